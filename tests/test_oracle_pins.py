@@ -1,0 +1,353 @@
+"""Pins of the CPU oracle to what the paper and the mathematics fix.
+
+None of these tests needs a GPU.  Each pin checks the oracle against
+something other than itself: values printed in the paper (tests/golden/),
+closed forms, invariants, brute force on tiny inputs, or a second
+independent route to the same quantity.  ``test_pins_catch_planted_mistakes``
+plants plausible mistakes in copies of the oracle's data and checks that the
+pins fail on each.
+"""
+
+import itertools
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def _golden_lines(golden_dir, name):
+    with open(os.path.join(golden_dir, name)) as f:
+        return [ln.strip() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def _printed_decimals(s):
+    return len(s.split(".")[1]) if "." in s else 0
+
+
+# ---------------------------------------------------------------- Sec. 2 ---
+def test_t_is_multiplierless_and_tt_diagonal():
+    assert set(np.unique(O.T)) <= {-1, 0, 1}
+    g = O.t_t_transpose()
+    assert np.all(g == np.diag(np.diag(g)))
+    # each diagonal entry is the number of non-zeros of that row
+    assert np.all(np.diag(g) == np.count_nonzero(O.T, axis=1))
+
+
+def test_s_matches_printed(golden_dir):
+    den = [int(v) for v in _golden_lines(golden_dir, "s_printed.txt")]
+    assert len(den) == 16
+    np.testing.assert_allclose(O.s_diag(), 1.0 / np.sqrt(den), rtol=0, atol=1e-15)
+    assert np.all(O.w_diag() * np.array(den) == 48)
+
+
+def test_c_hat_orthogonal():
+    c = O.c_hat()
+    np.testing.assert_allclose(c @ c.T, np.eye(16), atol=1e-14)
+
+
+def _cycles_to_row_source(text):
+    perm = list(range(16))
+    for grp in text.replace(")", "").split("(")[1:]:
+        elems = [int(t) for t in grp.split()]
+        if len(elems) > 1 and elems[0] == elems[-1]:
+            elems = elems[:-1]  # printed repetition of the cycle's first element
+        for a, b in zip(elems, elems[1:] + elems[:1]):
+            perm[a] = b
+    return tuple(perm)
+
+
+def test_factorisation_reproduces_t(golden_dir):
+    text = _golden_lines(golden_dir, "p2_cycles.txt")[0]
+    assert _cycles_to_row_source(text) == O.P2_ROW_SOURCE
+    m1, p1, m2, m3, m4, p2 = O.factors()
+    f = m4 @ m3 @ m2 @ p1 @ m1
+    assert np.array_equal(p2 @ f, O.T)
+    # rows of F are pairwise distinct, so no other row permutation gives T
+    assert len({tuple(r) for r in f}) == 16
+    # P1 and P2 are permutations
+    for p in (p1, p2):
+        assert np.array_equal(p @ p.T, np.eye(16, dtype=np.int64))
+
+
+def test_table1_addition_count(golden_dir):
+    mul, add, shift, total = [int(v) for v in _golden_lines(golden_dir, "table1_complexity.txt")[0].split()]
+    fs = O.factors()
+    assert sum(O.addition_count(m) for m in fs) == add == 60
+    assert sum(O.multiplication_count(m) for m in fs) == mul == 0
+    assert shift == 0 and total == add
+    # the transposed factors (the inverse T^T) need the same count
+    assert sum(O.addition_count(m.T) for m in fs) == 60
+    # the direct product needs many more: sum over rows of (nnz - 1)
+    assert O.addition_count(O.T) == 176
+
+
+# ---------------------------------------------------------------- Table 2 ---
+@pytest.mark.parametrize("name", ["DCT", "Proposed"])
+def test_table2_measures(golden_dir, name):
+    rows = {ln.split()[0]: ln.split()[1:] for ln in _golden_lines(golden_dir, "table2_measures.txt")}
+    printed = rows[name]
+    ct = O.dct_matrix() if name == "DCT" else O.c_hat()
+    got = O.table2_row(ct)
+    for key, text in zip(["d2", "eps", "mse", "cg", "eta"], printed):
+        nd = _printed_decimals(text)
+        assert round(got[key], nd) == pytest.approx(float(text), abs=10.0 ** -nd / 2 + 1e-12), key
+
+
+# ------------------------------------------------------- integer forward ---
+def _brute_forward(block):
+    y = [[0] * 16 for _ in range(16)]
+    for u in range(16):
+        for v in range(16):
+            s = 0
+            for m in range(16):
+                for n in range(16):
+                    s += int(O.T[u, m]) * int(block[m][n]) * int(O.T[v, n])
+            y[u][v] = s
+    return np.array(y, dtype=np.int64)
+
+
+def test_forward_brute_force_two_blocks():
+    rng = np.random.default_rng(7)
+    img = rng.integers(0, 256, size=(16, 32), dtype=np.int64)
+    y = O.forward_int(img)
+    for bx in range(2):
+        assert np.array_equal(y[0, bx], _brute_forward(img[:, 16 * bx:16 * bx + 16].tolist()))
+
+
+def test_forward_constant_block_is_dc_only():
+    for c in (0, 1, 128, 255):
+        y = O.forward_int(np.full((16, 16), c))
+        expect = np.zeros((16, 16), dtype=np.int64)
+        expect[0, 0] = 256 * c
+        assert np.array_equal(y[0, 0], expect)
+
+
+def test_forward_impulse_gives_outer_product():
+    for m, n in [(0, 0), (3, 11), (15, 15), (7, 2)]:
+        img = np.zeros((16, 16), dtype=np.int64)
+        img[m, n] = 1
+        assert np.array_equal(O.forward_int(img)[0, 0], np.outer(O.T[:, m], O.T[:, n]))
+
+
+def test_forward_linearity_and_range():
+    rng = np.random.default_rng(3)
+    a = rng.integers(-300, 300, size=(32, 48))
+    b = rng.integers(-300, 300, size=(32, 48))
+    assert np.array_equal(O.forward_int(5 * a + b), 5 * O.forward_int(a) + O.forward_int(b))
+    # u8 extremes: |Y| <= 256*255 for DC, <= 128*255 elsewhere
+    for c in (0, 255):
+        x = np.full((16, 16), c)
+        x[::2, ::3] = 255 - c
+        y = O.forward_int(x)[0, 0]
+        assert abs(y[0, 0]) <= 65280 and np.all(np.abs(y.ravel()[1:]) <= 32640)
+
+
+def test_one_d_unit_and_extreme_vectors_brute_force():
+    # the 1-D transform applied to unit vectors returns T's columns, and the
+    # extreme +-255 patterns hit the row bounds nnz_k * 255 exactly
+    for j in range(16):
+        e = np.zeros((16, 16), dtype=np.int64)
+        e[0, j] = 1  # row 0 only -> Y[u, v] = T[u, 0] T[v, j]
+        assert np.array_equal(O.forward_int(e)[0, 0][0], O.T[0, 0] * O.T[:, j])
+    x = np.where(O.T > 0, 255, -255)  # row k of x aligned with row k of T
+    for k in range(16):
+        assert int(O.T[k] @ x[k]) == 255 * int(np.count_nonzero(O.T[k]))
+
+
+# --------------------------------------------------------- exact inverse ---
+def test_inverse_exact_all_coefficients():
+    rng = np.random.default_rng(11)
+    img = rng.integers(0, 256, size=(48, 32), dtype=np.int64).astype(np.uint8)
+    y = O.forward_int(img)
+    z = O.inverse_numerator(y)
+    assert np.array_equal(z, 2304 * O.to_blocks(img.astype(np.int64)))
+    assert np.array_equal(O.inverse_exact(y), img)
+    res = O.compress_zonal_exact(img, 256)
+    assert res["sse"] == 0.0 and math.isinf(res["psnr"])
+    assert np.array_equal(res["recon_u8"], img)
+
+
+def test_round_half_away_div_matches_fractions():
+    vals = list(range(-5000, 5001, 7)) + [1152, -1152, 3456, -3456, 2304 * 3 + 1152]
+    got = O.round_half_away_div(np.array(vals), 2304)
+    for v, g in zip(vals, got):
+        f = Fraction(v, 2304)
+        q = math.floor(abs(f) + Fraction(1, 2))
+        assert g == (q if f >= 0 else -q)
+
+
+def _zonal_cases():
+    rng = np.random.default_rng(5)
+    img_a = rng.integers(0, 256, size=(32, 32)).astype(np.uint8)
+    from paper_1606_05562_gb300 import synth
+    img_b = synth.ar1_image(64, 48, 0.95, 9)
+    return [img_a, img_b]
+
+
+@pytest.mark.parametrize("r", [1, 6, 16, 36, 64, 100, 150, 255, 256])
+def test_exact_route_matches_fp64_definition(r):
+    for img in _zonal_cases():
+        ex = O.compress_zonal_exact(img, r)
+        fp = O.compress_zonal_fp64(img, r)
+        np.testing.assert_allclose(ex["numerator"] / 2304.0, O.to_blocks(fp["recon"]), atol=1e-9)
+        assert ex["sse"] == pytest.approx(fp["sse"], rel=1e-9, abs=1e-9)
+
+
+@pytest.mark.parametrize("r", [1, 16, 100, 200])
+def test_parseval_sse_equals_discarded_energy(r):
+    s = O.s_diag()
+    for img in _zonal_cases():
+        ex = O.compress_zonal_exact(img, r)
+        b = ex["coef"] * (s[:, None] * s[None, :])
+        dropped = np.where(O.zonal_mask(r)[None, None], 0.0, b)
+        assert ex["sse"] == pytest.approx(float(np.sum(dropped ** 2)), rel=1e-10)
+
+
+def test_psnr_monotone_in_r():
+    for img in _zonal_cases():
+        p = [O.compress_zonal_exact(img, r)["psnr"] for r in range(1, 257, 5)]
+        assert all(b >= a - 1e-12 for a, b in zip(p, p[1:]))
+
+
+def test_r1_keeps_block_mean_for_both_transforms():
+    for img in _zonal_cases():
+        a = O.compress_zonal_fp64(img, 1, "approx")
+        d = O.compress_zonal_fp64(img, 1, "dct")
+        mean = O.to_blocks(img.astype(np.float64)).mean(axis=(2, 3), keepdims=True)
+        np.testing.assert_allclose(O.to_blocks(a["recon"]), np.broadcast_to(mean, O.to_blocks(a["recon"]).shape), atol=1e-9)
+        assert a["psnr"] == pytest.approx(d["psnr"], rel=1e-12)
+
+
+def test_dct_matrix_orthonormal_and_exact_reconstruction():
+    c = O.dct_matrix()
+    np.testing.assert_allclose(c @ c.T, np.eye(16), atol=1e-14)
+    img = _zonal_cases()[1]
+    assert O.compress_zonal_fp64(img, 256, "dct")["sse"] < 1e-18 * img.size * 255 ** 2
+
+
+# -------------------------------------------------------------- zig-zag ---
+def _jpeg_walk(n):
+    """Zig-zag built by walking: up-right / down-left with boundary bounces."""
+    u = v = 0
+    out = [(0, 0)]
+    up = True  # moving towards row 0 (v increasing)
+    while len(out) < n * n:
+        if up:
+            if v == n - 1:
+                u += 1; up = False
+            elif u == 0:
+                v += 1; up = False
+            else:
+                u -= 1; v += 1
+        else:
+            if u == n - 1:
+                v += 1; up = True
+            elif v == 0:
+                u += 1; up = True
+            else:
+                u += 1; v -= 1
+        out.append((u, v))
+    return out
+
+
+def test_zigzag_matches_walk_and_invariants():
+    for n in (4, 8, 16):
+        assert O.zigzag_order(n) == _jpeg_walk(n)
+    z = O.zigzag_order(16)
+    assert z[:6] == [(0, 0), (0, 1), (1, 0), (2, 0), (1, 1), (0, 2)]
+    assert sorted(z) == [(u, v) for u in range(16) for v in range(16)]
+    for (a, b), (c, d) in zip(z, z[1:]):
+        assert max(abs(a - c), abs(b - d)) == 1
+    # triangular r keep whole anti-diagonals, whatever the orientation
+    for r, s in [(1, 0), (6, 2), (36, 7)]:
+        m = O.zonal_mask(r)
+        assert all(m[u, v] == (u + v <= s) for u in range(16) for v in range(16))
+    assert O.zonal_mask(256).all() and O.zonal_mask(150).sum() == 150
+
+
+# ---------------------------------------------------------- quantiser ---
+def test_quantiser_fp32_decision_close_to_fp64():
+    from paper_1606_05562_gb300 import synth
+    x = synth.laplacian_residual(64, 64, 21)
+    y = O.forward_int(x)
+    for qp in (22, 27, 32, 37):
+        l64 = O.quant_levels(y, qp, "fp64")
+        l32 = O.quant_levels(y, qp, "fp32")
+        diff = l64 != l32
+        assert np.all(np.abs(l64 - l32) <= 1)
+        assert diff.mean() < 1e-3
+
+
+def test_quantiser_closed_forms():
+    # QP = 0 -> Qstep = 1: level = round_half_away(B)
+    y = np.arange(-512, 512).reshape(4, 16, 16)[None]
+    s = O.s_diag()
+    b = y * (s[:, None] * s[None, :])
+    expect = np.sign(b) * np.floor(np.abs(b) + 0.5)
+    assert np.array_equal(O.quant_levels(y, 0, "fp64"), expect)
+    # very fine step reconstructs the residual to within the step
+    x = np.random.default_rng(2).integers(-255, 256, size=(32, 32)).astype(np.int16)
+    res = O.compress_quant(x, -60)
+    assert np.max(np.abs(res["recon"] - x)) < 2.0 ** -9
+    assert np.array_equal(res["recon_i16"], x)
+    # huge step zeroes everything
+    res = O.compress_quant(x, 120)
+    assert np.all(res["levels"] == 0) and np.all(res["recon"] == 0)
+
+
+# ------------------------------------------------------------------ PSNR ---
+def test_psnr_closed_forms():
+    a = np.zeros((16, 16), dtype=np.uint8)
+    b = np.full((16, 16), 255, dtype=np.uint8)
+    assert O.psnr_images(a, b) == pytest.approx(0.0, abs=1e-12)
+    c = a.copy(); c[0, 0] = 1
+    assert O.psnr_images(a, c) == pytest.approx(10 * math.log10(255 ** 2 * 256), rel=1e-15)
+    assert math.isinf(O.psnr_images(a, a))
+
+
+# ------------------------------------------------------ planted mistakes ---
+def _pins_pass(t, w, p2_source, zig):
+    """The pins above, as one predicate over (possibly mutated) oracle data."""
+    g = t @ t.T
+    if not np.all(g == np.diag(np.diag(g))):
+        return False
+    if np.any(np.diag(g) == 0) or np.any(48 % np.diag(g) != 0):
+        return False
+    if not np.array_equal(48 // np.diag(g), w):
+        return False
+    s = 1.0 / np.sqrt(np.diag(g))
+    ct = s[:, None] * t
+    got = O.table2_row(ct)
+    if abs(got["d2"] - 0.3405) > 5e-5 or abs(got["cg"] - 8.295) > 5e-4:
+        return False
+    m1, p1, m2, m3, m4, _ = O.factors()
+    f = m4 @ m3 @ m2 @ p1 @ m1
+    if not np.array_equal(f[list(p2_source)], t):
+        return False
+    if zig != _jpeg_walk(16):
+        return False
+    img = np.arange(256).reshape(16, 16) % 251
+    y = np.einsum("um,mn,vn->uv", t, img, t)
+    z = t.T @ (y * w[:, None] * w[None, :]) @ t
+    return np.array_equal(z, 2304 * img)
+
+
+def test_pins_catch_planted_mistakes():
+    t, w = O.T.copy(), O.w_diag().copy()
+    p2 = list(O.P2_ROW_SOURCE)
+    zig = O.zigzag_order(16)
+    assert _pins_pass(t, w, p2, zig)
+    mutants = []
+    t1 = t.copy(); t1[5, 3] *= -1; mutants.append((t1, w, p2, zig))          # sign flip
+    mutants.append((t.T.copy(), w, p2, zig))                                  # transposed T
+    t3 = t.copy(); t3[[2, 6]] = t3[[6, 2]]; mutants.append((t3, w, p2, zig))  # swapped rows
+    w4 = w.copy(); w4[3] = 4; mutants.append((t, w4, p2, zig))                # wrong weight
+    p5 = p2.copy(); p5[1], p5[8] = p5[8], p5[1]; mutants.append((t, w, p5, zig))  # P2 misread
+    z6 = zig.copy(); z6[1], z6[2] = z6[2], z6[1]; mutants.append((t, w, p2, z6))  # zig-zag orientation
+    t7 = t.copy(); t7[9, 4] = 1; mutants.append((t7, w, p2, zig))            # dropped zero
+    for i, m in enumerate(mutants):
+        assert not _pins_pass(*m), f"mutant {i} passed the pins"
