@@ -36,7 +36,8 @@ Readings of points the paper leaves open (each one is listed in the design doc):
   convention extended to 16x16.  Anti-diagonal s = u + v; on even s the scan
   runs with u decreasing, on odd s with v decreasing.
 * PSNR is computed on the unrounded, unclipped reconstruction; the stored
-  pixel is ``clamp(round_half_away_from_zero(x_hat))`` (C ``round``).
+  pixel is ``clamp(round_half_to_even(x_hat))``, decided exactly from the
+  integer numerator ``Z`` (ties at ``Z = 2304 k + 1152``).
 * Quantiser: ``level = sign(B) * floor(|B| / Qstep + 1/2)``,
   ``Qstep = 2^(QP/6)``, ``B = s_u s_v Y``; dequantised ``B' = level * Qstep``.
 """
@@ -280,11 +281,21 @@ def round_half_away_div(num: np.ndarray, den: int) -> np.ndarray:
     return np.sign(num) * q
 
 
+def round_half_even_div(num: np.ndarray, den: int) -> np.ndarray:
+    """Exact ``round_half_to_even(num / den)`` for integer arrays (den even)."""
+    num = np.asarray(num, dtype=np.int64)
+    shifted = num + den // 2
+    q = np.floor_divide(shifted, den)
+    tie = (shifted - q * den) == 0
+    return np.where(tie & (q % 2 == 1), q - 1, q)
+
+
 def inverse_exact(coef: np.ndarray, out_dtype=np.uint8) -> np.ndarray:
     """Reconstruct an image from integer coefficients (no coefficient dropped
-    unless ``coef`` already has zeros), exact rounding then clamping."""
+    unless ``coef`` already has zeros): exact round-half-to-even of
+    ``Z / 2304``, then clamping to the output type."""
     z = inverse_numerator(coef)
-    x = round_half_away_div(z, 2304)
+    x = round_half_even_div(z, 2304)
     info = np.iinfo(out_dtype)
     return from_blocks(np.clip(x, info.min, info.max).astype(out_dtype))
 
@@ -314,7 +325,7 @@ def compress_zonal_exact(img: np.ndarray, r: int) -> dict:
     blk_sse = np.sum(e * e, axis=(2, 3))  # int64 per block, scaled by 2304^2
     sse_num = sum(int(v) for v in blk_sse.ravel())
     sse = float(Fraction(sse_num, 2304 * 2304))
-    out = from_blocks(np.clip(round_half_away_div(z, 2304), 0, 255).astype(np.uint8))
+    out = from_blocks(np.clip(round_half_even_div(z, 2304), 0, 255).astype(np.uint8))
     return {
         "coef": y,
         "numerator": z,
@@ -373,8 +384,8 @@ def quant_levels(coef: np.ndarray, qp: float, precision: str = "fp64") -> np.nda
 
 def compress_quant(img: np.ndarray, qp: float, precision: str = "fp64") -> dict:
     """Forward, quantise with S absorbed, dequantise, inverse (FP64), for an
-    int16 residual plane.  Output plane: ``clamp(round_half_away(x_hat))`` as
-    int16; PSNR of the unrounded reconstruction with peak 255."""
+    int16 residual plane.  Output plane: ``clamp(round_half_to_even(x_hat))``
+    as int16; PSNR of the unrounded reconstruction with peak 255."""
     x = np.asarray(img)
     y = forward_int(x)
     lev = quant_levels(y, qp, precision)
@@ -384,8 +395,7 @@ def compress_quant(img: np.ndarray, qp: float, precision: str = "fp64") -> dict:
     a = to_blocks(x.astype(np.float64))
     diff = rec - a
     sse = float(np.sum(diff * diff))
-    r = np.sign(rec) * np.floor(np.abs(rec) + 0.5)
-    out = from_blocks(np.clip(r, -32768, 32767).astype(np.int16))
+    out = from_blocks(np.clip(np.rint(rec), -32768, 32767).astype(np.int16))
     return {"coef": y, "levels": lev, "recon": from_blocks(rec), "recon_i16": out,
             "sse": sse, "psnr": psnr_from_sse(sse, x.size)}
 

@@ -180,6 +180,14 @@ def test_round_half_away_div_matches_fractions():
         assert g == (q if f >= 0 else -q)
 
 
+def test_round_half_even_div_matches_python_round():
+    # Python's round() of a Fraction is exact round-half-to-even
+    vals = list(range(-7000, 7001, 5)) + [1152 * k for k in range(-9, 10, 2)]
+    got = O.round_half_even_div(np.array(vals), 2304)
+    for v, g in zip(vals, got):
+        assert g == round(Fraction(v, 2304))
+
+
 def _zonal_cases():
     rng = np.random.default_rng(5)
     img_a = rng.integers(0, 256, size=(32, 32)).astype(np.uint8)
