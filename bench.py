@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the fused forward + zonal + inverse + PSNR path on GB300.
+
+Workload (one step): 64 uint8 images of 512x512 (half AR(1) rho=0.95, half
+AR(1) rho=0.80 plus N(0, 8^2)), each compressed at every zonal r in
+{1, 6, 16, 36, 64, 100, 150, 256}: 512 image jobs, 134.2 Mpixel, in one
+persistent launch of the fused kernel plus the per-image PSNR finalize.
+Metric: Gpixel/s over the whole job (all ranks).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank compresses its own shard of images (weak
+scaling, no data-path collective); the step time is the max over ranks.
+``--impl reference`` times the CPU oracle on a bounded sample instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+R_SWEEP = (1, 6, 16, 36, 64, 100, 150, 256)
+N_IMAGES = 64
+SIDE = 512
+METRIC = "Gpixel/s fused fwd+zonal+inv+PSNR"
+UNIT = "Gpixel/s"
+WORKLOAD = "64x512x512 u8 AR(1) images x zonal r in {1,6,16,36,64,100,150,256}"
+N_SETS = 3  # rotating input/output sets: 3 x 268 MB per step-set > 4 x L2
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
+    ap.add_argument("--e2e-steps", type=int, default=30)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha256():
+    h = hashlib.sha256()
+    for f in ("atdct16_kernels.cu", "atdct16_butterfly.cuh", "atdct16_ops.cuh", "atdct16_internal.h"):
+        with open(os.path.join(ROOT, "paper_1606_05562_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the zonal kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "zonal_kernel_64x512x512.md")
+    try:
+        text = open(p).read()
+    except OSError:
+        return None
+    sha = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
+    tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.e+]+)", text)
+    if not sha or not tr or sha.group(1) != kernel_source_sha256():
+        return None
+    return float(tr.group(1))
+
+
+# --------------------------------------------------------------------------
+def cpu_baseline(batch, budget_s):
+    """The oracle as it stands, on a bounded sample of the workload."""
+    import numpy as np
+
+    import oracle as O
+
+    t0 = time.perf_counter()
+    px = 0
+    done = []
+    for i in range(len(batch)):
+        for r in R_SWEEP:
+            O.compress_zonal_exact(batch[i], r)
+            px += batch[i].size
+        done.append(i)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    threads = 1  # numpy int64 einsum runs on one core
+    return {"value": px / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(done)} of 64 images x 8 r ({px / 1e6:.1f} Mpx) with the exact-integer oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The CPU oracle on the same metric: each step compresses a strip of one
+    512x512 image at all eight r, the strip height chosen so that the whole
+    --steps/--warmup run stays within about two minutes."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1606_05562_gb300 import synth
+
+    import oracle as O
+
+    img = synth.ar1_image(SIDE, SIDE, 0.95, 100)
+    t0 = time.perf_counter()
+    for r in R_SWEEP:
+        O.compress_zonal_exact(img[:16], r)
+    per_row_s = (time.perf_counter() - t0) / 16
+    budget = 120.0 / max(1, args.steps + max(args.warmup, 0))
+    rows = int(min(SIDE, max(16, (budget / max(per_row_s, 1e-9)) // 16 * 16)))
+    strip = img[:rows]
+    px_step = strip.size * len(R_SWEEP)
+
+    def step():
+        for r in R_SWEEP:
+            O.compress_zonal_exact(strip, r)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = px_step * args.steps / dt / 1e9
+    sample = f"{rows}x{SIDE} strip of one AR(1) image x 8 r per step ({px_step / 1e6:.2f} Mpx), exact-integer oracle"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORKLOAD, "sample_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1606_05562_gb300 import atdct16, synth
+    from paper_1606_05562_gb300 import build as b
+
+    b.build()
+    batch = synth.image_batch_512(N_IMAGES, SIDE, first_seed=100 + 1000 * rank)
+    nr = len(R_SWEEP)
+    jobs = nr * N_IMAGES
+    px_step = jobs * SIDE * SIDE
+
+    # rotating sets of inputs (one copy per r) and outputs, > 4 x L2 in total
+    base = torch.from_numpy(batch).to(dev)
+    sets = []
+    for _ in range(N_SETS):
+        src = base.unsqueeze(0).repeat(nr, 1, 1, 1).contiguous()
+        dst = torch.empty_like(src)
+        descs = [atdct16.image(src[k, i], dst[k, i], r) for k, r in enumerate(R_SWEEP) for i in range(N_IMAGES)]
+        sets.append((src, dst, descs))
+    plan = atdct16.Plan(atdct16.U8, max_images=jobs)
+    psnr = torch.empty(jobs, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    for w in range(max(args.warmup, 3)):
+        plan.compress_zonal(sets[w % N_SETS][2], psnr)
+    torch.cuda.synchronize()
+    plan.set_profiling(True)
+    plan.profile()
+    gpu_id = "0"
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(gpu_id)
+    barrier()
+    clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        plan.compress_zonal(sets[k % N_SETS][2], psnr)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches, kernel_ms = plan.profile()
+    plan.set_profiling(False)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * px_step / (ms / 1e3) / 1e9
+    if plan.last_device_status() != atdct16.OK:
+        raise RuntimeError("device-side status error during the bench")
+
+    # roofline of the fused kernel: algorithmic bytes = 1 B in + 1 B out per
+    # pixel, the per-tile FP32 partials and the job descriptors
+    tiles = jobs * (SIDE // 16) * ((SIDE + 127) // 128)
+    algo_bytes = 2.0 * px_step + 4.0 * tiles + 64.0 * jobs
+    k_avg_s = (kernel_ms / launches) / 1e3 if launches else ms / 1e3
+    peak, peak_src = measured_peak_hbm()
+    achieved = algo_bytes / k_avg_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": recorded_traffic(), "peak_source": peak_src, "kernel": "zonal_kernel",
+            "kernel_ms": k_avg_s * 1e3, "algorithmic_bytes_per_launch": algo_bytes}
+
+    # end to end through the public API with host buffers: H2D of the 64
+    # images from pinned memory, the same 512-job call, D2H of every
+    # reconstruction and PSNR
+    h_src = torch.from_numpy(batch).pin_memory()
+    d_src = torch.empty_like(base)
+    d_dst = torch.empty((nr, N_IMAGES, SIDE, SIDE), dtype=torch.uint8, device=dev)
+    h_dst = torch.empty(d_dst.shape, dtype=torch.uint8).pin_memory()
+    h_psnr = torch.empty(jobs, dtype=torch.float64).pin_memory()
+    e2e_descs = [atdct16.image(d_src[i], d_dst[k, i], r) for k, r in enumerate(R_SWEEP) for i in range(N_IMAGES)]
+
+    def e2e_step():
+        d_src.copy_(h_src, non_blocking=True)
+        plan.compress_zonal(e2e_descs, psnr)
+        h_dst.copy_(d_dst, non_blocking=True)
+        h_psnr.copy_(psnr, non_blocking=True)
+
+    e2e = None
+    if args.e2e_steps > 0:
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+        if dist:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * px_step / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h_src.numel()), "d2h_bytes_per_step": int(h_dst.numel() + 8 * jobs),
+               "ms_per_step": e2e_ms}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "images": N_IMAGES, "side": SIDE, "r_sweep": list(R_SWEEP),
+                       "jobs_per_step": jobs, "pixels_per_step": px_step, "parallelism": f"dp{world} (image shards)",
+                       "l2": f"{N_SETS} rotating input/output sets of {2 * px_step / 1e6:.0f} MB (> 4 x L2)"},
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+        }
+        line["cpu_baseline"] = cpu_baseline(batch, args.cpu_seconds) if args.cpu_seconds > 0 else None
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * atdct16 -- GB300 (sm_103a) library for the orthogonal 16-point approximate
+ * DCT of da Silveira, Bayer, Cintra, Kulasekera, Madanayake and Kozakevicius
+ * (arXiv 1606.05562).
+ *
+ * The transform is the 16x16 matrix T with entries in {0, +-1} (Sec. 2),
+ * applied separably to every disjoint 16x16 block of an image,
+ *     Y = T X T^T,
+ * through the paper's 60-addition factorisation T = P2 M4 M3 M2 P1 M1
+ * (Sec. 2).  The orthogonal approximation is C_hat = S T with
+ * S = diag(T T^T)^(-1/2); S is folded into the quantisation step or the zonal
+ * retention (Sec. 2, last paragraph), so the inverse is
+ *     X_hat = T^T (S^2 Y' S^2) T.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers prefixed d_ are device pointers, h_ host pointers.  The caller
+ *   owns every buffer it passes; the library never frees them.  A plan owns
+ *   only its own workspace (tables, descriptors, per-tile partial sums).
+ * - Images are row-major with a pitch in bytes.  Width and height must be
+ *   positive multiples of 16.  Image base pointers and pitches must be
+ *   16-byte aligned (the kernels move 16-byte rows of a block).
+ * - Block (by, bx) covers rows 16*by..16*by+15 and columns 16*bx..16*bx+15.
+ *   Within a block the coefficient index is (u, v), u = vertical frequency
+ *   (row of T applied to the block's columns), v = horizontal frequency:
+ *       Y[u][v] = sum_m sum_n T[u][m] X[m][n] T[v][n].
+ * - Zig-zag order (Sec. 4, "adapting the zigzag sequence"): the JPEG
+ *   convention extended to 16x16: anti-diagonals s = u + v; on even s the
+ *   scan runs with u decreasing, on odd s with v decreasing.
+ * - Every compute call is asynchronous on the given stream and allocates
+ *   nothing.  Argument errors are detected on the host before any launch and
+ *   return ATDCT16_EINVAL; CUDA launch or copy errors return ATDCT16_ECUDA.
+ * - A plan is not thread-safe: use one plan per host thread (or serialise).
+ */
+#ifndef ATDCT16_H
+#define ATDCT16_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ATDCT16_OK = 0,
+  ATDCT16_EINVAL = 1,       /* bad argument: nothing was launched */
+  ATDCT16_ENOMEM = 2,       /* workspace or device memory exhausted */
+  ATDCT16_ECUDA = 3,        /* a CUDA runtime call failed */
+  ATDCT16_ETIMEOUT = 4,     /* a bounded device-side wait expired */
+  ATDCT16_EUNSUPPORTED = 5, /* valid request this build does not support */
+  ATDCT16_EDEVICE = 6       /* a kernel's own bounds checks rejected work */
+} atdct16_status;
+
+typedef enum { ATDCT16_U8 = 0, ATDCT16_I16 = 1 } atdct16_dtype;
+
+/* One image of a batch.  src/dst are device pointers (host pointers for the
+ * *_host entry points).  r_or_qp is the zonal r (0..256) for
+ * atdct16_compress_zonal and the quantisation point QP (0..63) for
+ * atdct16_compress_quant. */
+typedef struct {
+  const void* src;
+  void* dst;
+  int64_t src_pitch; /* bytes */
+  int64_t dst_pitch; /* bytes */
+  int32_t width;
+  int32_t height;
+  int32_t r_or_qp;
+  int32_t reserved; /* must be 0 */
+} atdct16_image;
+
+typedef struct atdct16_plan_st* atdct16_plan_t;
+typedef struct atdct16_batch_st* atdct16_batch_t;
+
+/* Library version string, e.g. "atdct16 1.0 sm_103a". */
+const char* atdct16_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char* atdct16_status_string(atdct16_status s);
+
+/* Create a plan on the current CUDA device.
+ *   dtype          pixel type of the images the plan will process (U8: zonal
+ *                  path, I16: quantisation path; forward/inverse accept both)
+ *   max_images     largest batch size any call will pass (>= 1)
+ *   workspace_budget_bytes  upper bound on device memory the plan may take
+ *                  (0 = a default of 256 MiB).  The plan sizes its per-tile
+ *                  partial-sum buffer from it; calls whose batches need more
+ *                  tiles than fit return ATDCT16_ENOMEM.
+ *   flags          0 (reserved)
+ * Allocates the plan's workspace (device tables, descriptor ring, partials)
+ * with cudaMalloc and pinned host staging with cudaHostAlloc. */
+atdct16_status atdct16_plan_create(atdct16_plan_t* plan, atdct16_dtype dtype, int32_t max_images,
+                                   size_t workspace_budget_bytes, uint32_t flags);
+
+/* Wait for the plan's outstanding work, then release its workspace. */
+atdct16_status atdct16_plan_destroy(atdct16_plan_t plan);
+
+/* Forward 2-D transform of every block (Sec. 2, Y = T X T^T; Sec. 4 splits
+ * the image into disjoint 16x16 blocks).  S is not applied.
+ *   d_src   image of `dtype` (U8 or I16) with pitch `pitch` bytes, w x h
+ *   d_coef  output, block-major: block b = by*(w/16)+bx occupies
+ *           d_coef[256*b .. 256*b+255], row-major in (u, v).  Exact int32
+ *           (|Y| <= 65280 for U8 input, <= 256*32768 for I16 input). */
+atdct16_status atdct16_forward(atdct16_plan_t plan, atdct16_dtype dtype, const void* d_src,
+                               int64_t pitch, int32_t w, int32_t h, int32_t* d_coef,
+                               cudaStream_t stream);
+
+/* Inverse 2-D transform (Sec. 4, A' = C_hat^T B' C_hat with S folded in),
+ * computed exactly: Z = T^T (W Y W) T with the integer W = 48 S^2, then
+ * X_hat = Z / 2304 rounded half to even (decided exactly from Z) and
+ * clamped to the range of `dtype`.  Coefficients produced by atdct16_forward reconstruct the input
+ * bit-exactly.  Layout of d_coef as for atdct16_forward.  Integer
+ * arithmetic is 64-bit, so any int32 coefficients are accepted. */
+atdct16_status atdct16_inverse(atdct16_plan_t plan, atdct16_dtype dtype, const int32_t* d_coef,
+                               int32_t w, int32_t h, void* d_dst, int64_t pitch,
+                               cudaStream_t stream);
+
+/* Fused zonal compression of a batch of uint8 images (Sec. 4 procedure):
+ * forward transform, keep the first r zig-zag coefficients of every block
+ * (images[i].r_or_qp = r, 0..256), scale by S^2 on both sides, inverse,
+ * store clamp(round_half_even(X_hat)) as uint8 in images[i].dst, and write
+ * the per-image PSNR (Sec. 4) to d_psnr[i]:
+ *     PSNR = 10 log10(255^2 * w * h / SSE),  +inf when SSE = 0,
+ * with SSE the squared error of the unrounded reconstruction X_hat against
+ * the input.  Every pixel crosses device memory once in and once out.
+ * The reconstruction numerator Z is exact, so the stored pixels are exact;
+ * SSE is accumulated in FP32 per block and FP64 per image.
+ *   h_images  host array of n descriptors (device src/dst pointers)
+ *   d_psnr    device array of n doubles
+ *   d_sse     optional device array of n doubles (may be NULL) */
+atdct16_status atdct16_compress_zonal(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n,
+                                      double* d_psnr, double* d_sse, cudaStream_t stream);
+
+/* Fused quantisation of a batch of int16 planes (Sec. 2: S absorbed into
+ * the quantiser; Sec. 5.3: HEVC quantisation points):
+ *     B = s_u s_v Y,  level = sign(B) floor(|B| / Qstep + 1/2),
+ *     Qstep = 2^(QP/6),  B' = level * Qstep,  X_hat = C_hat^T B' C_hat,
+ * stored as clamp(rint(X_hat)) int16 in images[i].dst.  The level decision
+ * is taken in FP32 as fp32(|Y| * fp32(s_u s_v / Qstep)) + 0.5 (no fused
+ * multiply-add).  The inverse runs in FP32.  PSNR (peak 255) of the
+ * unrounded reconstruction goes to d_psnr[i].
+ *   d_levels  optional (may be NULL): int16 levels, block-major as for
+ *             atdct16_forward, images concatenated in batch order. */
+atdct16_status atdct16_compress_quant(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n,
+                                      int16_t* d_levels, double* d_psnr, double* d_sse,
+                                      cudaStream_t stream);
+
+/* PSNR between two images of the same shape (Sec. 4), exact integer SSE.
+ * peak 255.  d_out: one device double.  Allocates nothing: the output slot
+ * doubles as the accumulator. */
+atdct16_status atdct16_psnr(atdct16_dtype dtype, const void* d_a, int64_t pitch_a, const void* d_b,
+                            int64_t pitch_b, int32_t w, int32_t h, double* d_out,
+                            cudaStream_t stream);
+
+/* Sticky device-side status of the plan (ATDCT16_OK unless a kernel's own
+ * checks rejected a descriptor).  Synchronises the plan's last stream. */
+atdct16_status atdct16_last_device_status(atdct16_plan_t plan);
+
+/* Kernel timing hook (tracing support; not part of the paper).  While
+ * enabled, every fused zonal / quantisation kernel launch of the plan is
+ * bracketed by CUDA events on the launch stream.  atdct16_plan_profile
+ * synchronises on those events and returns the number of timed launches and
+ * their summed device time in milliseconds, then clears the record.  At most
+ * 4096 launches are recorded between two queries; later ones are not timed. */
+atdct16_status atdct16_plan_set_profiling(atdct16_plan_t plan, int32_t enable);
+atdct16_status atdct16_plan_profile(atdct16_plan_t plan, int64_t* launches, double* kernel_ms);
+
+/* Runs the library's 1-D butterflies on the host, for tests:
+ * inverse = 0: out = T in;  inverse = 1: out = T^T in.  Same source code as
+ * the device kernels.  in/out: 16 int32 each. */
+atdct16_status atdct16_host_butterfly(const int32_t* in, int32_t* out, int32_t inverse);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ATDCT16_H */

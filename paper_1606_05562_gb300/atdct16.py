@@ -1,0 +1,190 @@
+"""Thin Python binding over the C ABI of ``libatdct16.so`` (include/atdct16.h).
+
+Argument marshalling only: every step of the transform runs in the CUDA
+library.  Tensors are torch CUDA tensors; their ``data_ptr()`` and the current
+torch stream are passed straight through.  If the library has not been built
+the first call raises -- there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+U8, I16 = 0, 1
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EDEVICE = range(7)
+
+
+class Atdct16Error(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+
+
+class Image(C.Structure):
+    """Mirror of ``atdct16_image``."""
+
+    _fields_ = [
+        ("src", C.c_void_p),
+        ("dst", C.c_void_p),
+        ("src_pitch", C.c_int64),
+        ("dst_pitch", C.c_int64),
+        ("width", C.c_int32),
+        ("height", C.c_int32),
+        ("r_or_qp", C.c_int32),
+        ("reserved", C.c_int32),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "atdct16_version": (C.c_char_p, []),
+    "atdct16_status_string": (C.c_char_p, [C.c_int]),
+    "atdct16_plan_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int32, C.c_size_t, C.c_uint32]),
+    "atdct16_plan_destroy": (C.c_int, [C.c_void_p]),
+    "atdct16_forward": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    "atdct16_inverse": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p]),
+    "atdct16_compress_zonal": (C.c_int, [C.c_void_p, C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "atdct16_compress_quant": (C.c_int, [C.c_void_p, C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "atdct16_psnr": (C.c_int, [C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    "atdct16_last_device_status": (C.c_int, [C.c_void_p]),
+    "atdct16_host_butterfly": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32]),
+    "atdct16_plan_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
+    "atdct16_plan_profile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib() -> C.CDLL:
+    """Load ``libatdct16.so`` (raises if it was never built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"atdct16 CUDA library missing at {path}; build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name, None)
+                if fn is None:
+                    continue
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return lib().atdct16_status_string(status).decode()
+    except RuntimeError:
+        return "library not loaded"
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise Atdct16Error(status, what)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def host_butterfly(values, inverse=False):
+    """Run the library's 1-D butterfly on the host (16 int32 values)."""
+    a = (C.c_int32 * 16)(*[int(v) for v in values])
+    o = (C.c_int32 * 16)()
+    _check(lib().atdct16_host_butterfly(a, o, 1 if inverse else 0), "host_butterfly")
+    return list(o)
+
+
+def image(src, dst, param, width=None, height=None):
+    """Descriptor for a 2-D (H, W) torch tensor pair (row pitch from strides)."""
+    h, w = src.shape[-2], src.shape[-1]
+    es = src.element_size()
+    return Image(src.data_ptr(), 0 if dst is None else dst.data_ptr(), src.stride(-2) * es,
+                 0 if dst is None else dst.stride(-2) * dst.element_size(),
+                 w if width is None else width, h if height is None else height, int(param), 0)
+
+
+class Plan:
+    """Owns an ``atdct16_plan_t`` (device workspace)."""
+
+    def __init__(self, dtype=U8, max_images=64, workspace_bytes=0):
+        self._h = C.c_void_p()
+        _check(lib().atdct16_plan_create(C.byref(self._h), dtype, max_images, workspace_bytes, 0), "plan_create")
+        self.dtype = dtype
+        self.max_images = max_images
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().atdct16_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, img, coef, dtype=U8, stream=None):
+        h, w = img.shape[-2], img.shape[-1]
+        _check(lib().atdct16_forward(self._h, dtype, _ptr(img), img.stride(-2) * img.element_size(), w, h,
+                                     _ptr(coef), _stream(stream)), "forward")
+
+    def inverse(self, coef, out, dtype=U8, stream=None):
+        h, w = out.shape[-2], out.shape[-1]
+        _check(lib().atdct16_inverse(self._h, dtype, _ptr(coef), w, h, _ptr(out),
+                                     out.stride(-2) * out.element_size(), _stream(stream)), "inverse")
+
+    def compress_zonal(self, images, psnr, sse=None, stream=None):
+        """``images``: list of Image descriptors (param = r)."""
+        arr = (Image * len(images))(*images)
+        _check(lib().atdct16_compress_zonal(self._h, arr, len(images), _ptr(psnr), _ptr(sse), _stream(stream)),
+               "compress_zonal")
+
+    def compress_quant(self, images, psnr, levels=None, sse=None, stream=None):
+        arr = (Image * len(images))(*images)
+        _check(lib().atdct16_compress_quant(self._h, arr, len(images), _ptr(levels), _ptr(psnr), _ptr(sse),
+                                            _stream(stream)), "compress_quant")
+
+    def set_profiling(self, on=True):
+        _check(lib().atdct16_plan_set_profiling(self._h, 1 if on else 0), "set_profiling")
+
+    def profile(self):
+        """(timed kernel launches, summed kernel milliseconds) since the last call."""
+        n, ms = C.c_int64(), C.c_double()
+        _check(lib().atdct16_plan_profile(self._h, C.byref(n), C.byref(ms)), "profile")
+        return n.value, ms.value
+
+    def last_device_status(self) -> int:
+        return lib().atdct16_last_device_status(self._h)
+
+
+def psnr(a, b, out, dtype=U8, stream=None):
+    h, w = a.shape[-2], a.shape[-1]
+    _check(lib().atdct16_psnr(dtype, _ptr(a), a.stride(-2) * a.element_size(), _ptr(b),
+                              b.stride(-2) * b.element_size(), w, h, _ptr(out), _stream(stream)), "psnr")

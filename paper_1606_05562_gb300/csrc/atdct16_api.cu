@@ -1,0 +1,351 @@
+// C-ABI layer: plans, argument validation, host-side constant tables, launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/atdct16.h"
+#include "atdct16_butterfly.cuh"
+#include "atdct16_internal.h"
+
+using namespace atdct16;
+
+struct atdct16_plan_st {
+  int device = 0;
+  atdct16_dtype dtype = ATDCT16_U8;
+  int max_images = 0;
+  long long max_tiles = 0;
+  int num_sms = 0;
+  int zonal_grid = 0;
+  int quant_grid = 0;
+  ImageJob* d_jobs = nullptr;
+  ImageJob* h_jobs = nullptr;           // pinned staging for the descriptor upload
+  float2* d_wtab = nullptr;             // zonal weights [r][c][u]
+  float4* d_qtab = nullptr;             // quantiser constants [QP][c][u]
+  float* d_tile_sse = nullptr;          // per-tile SSE partials
+  int* d_status = nullptr;
+  cudaEvent_t upload_done = nullptr;    // staging buffers may be rewritten after this
+  bool upload_pending = false;
+  cudaStream_t last_stream = nullptr;
+  // kernel timing hook
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_events;  // pairs (start, stop)
+  int prof_used = 0;                     // pairs recorded since the last query
+};
+
+namespace {
+
+// Zig-zag rank of (u, v) for 16x16 (Sec. 4, JPEG convention extended):
+// anti-diagonal s = u + v; even s scanned with u decreasing, odd s with v
+// decreasing.
+void zigzag_rank16(int rank[16][16]) {
+  int idx = 0;
+  for (int s = 0; s <= 30; ++s) {
+    const int lo = s > 15 ? s - 15 : 0, hi = s < 15 ? s : 15;
+    if (s % 2 == 0) {
+      for (int u = hi; u >= lo; --u) rank[u][s - u] = idx++;
+    } else {
+      for (int v = hi; v >= lo; --v) rank[s - v][v] = idx++;
+    }
+  }
+}
+
+// Number of non-zero entries in each row of T, read off the factorisation:
+// row i of T = row p(i) of M4 M3 M2 P1 M1, evaluated here by running the
+// library's own butterfly on unit vectors.
+void row_nonzeros(int nnz[16]) {
+  for (int i = 0; i < 16; ++i) nnz[i] = 0;
+  for (int j = 0; j < 16; ++j) {
+    int x[16] = {0}, y[16];
+    x[j] = 1;
+    fwd16(x, y);
+    for (int i = 0; i < 16; ++i) nnz[i] += (y[i] != 0);
+  }
+}
+
+constexpr int kProfPairs = 4096;
+
+// Start / stop events around one kernel launch when profiling is on.
+int prof_begin(atdct16_plan_t plan, cudaStream_t stream) {
+  if (!plan->profiling || plan->prof_used >= kProfPairs) return -1;
+  const int k = plan->prof_used++;
+  if (cudaEventRecord(plan->prof_events[2 * k], stream) != cudaSuccess) return -1;
+  return k;
+}
+void prof_end(atdct16_plan_t plan, int k, cudaStream_t stream) {
+  if (k >= 0) cudaEventRecord(plan->prof_events[2 * k + 1], stream);
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+atdct16_status from_cuda(cudaError_t e) { return e == cudaSuccess ? ATDCT16_OK : ATDCT16_ECUDA; }
+
+atdct16_status check_image(const atdct16_image& im, int elem, bool need_dst) {
+  if (!im.src || (need_dst && !im.dst)) return ATDCT16_EINVAL;
+  if (im.width <= 0 || im.height <= 0 || (im.width & 15) || (im.height & 15)) return ATDCT16_EINVAL;
+  if (im.src_pitch < (int64_t)im.width * elem || (im.src_pitch & 15)) return ATDCT16_EINVAL;
+  if (need_dst && (im.dst_pitch < (int64_t)im.width * elem || (im.dst_pitch & 15))) return ATDCT16_EINVAL;
+  if (!aligned16(im.src) || (need_dst && !aligned16(im.dst))) return ATDCT16_EINVAL;
+  if (im.reserved != 0) return ATDCT16_EINVAL;
+  return ATDCT16_OK;
+}
+
+// Fill the pinned descriptor staging buffer and upload it on `stream`.
+atdct16_status stage_jobs(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n, int elem,
+                          cudaStream_t stream, long long* ntiles_out, bool with_level_base) {
+  if (plan->upload_pending) {
+    // the previous upload must have left the staging buffers before reuse
+    if (cudaEventSynchronize(plan->upload_done) != cudaSuccess) return ATDCT16_ECUDA;
+    plan->upload_pending = false;
+  }
+  long long tiles = 0, blocks = 0;
+  for (int i = 0; i < n; ++i) {
+    const atdct16_image& im = h_images[i];
+    ImageJob& J = plan->h_jobs[i];
+    J.src = static_cast<const uint8_t*>(im.src);
+    J.dst = static_cast<uint8_t*>(im.dst);
+    J.src_pitch = im.src_pitch;
+    J.dst_pitch = im.dst_pitch;
+    J.width = im.width;
+    J.height = im.height;
+    J.tiles_x = (im.width + kTileW - 1) / kTileW;
+    J.param = im.r_or_qp;
+    J.tile_begin = tiles;
+    tiles += (long long)J.tiles_x * (im.height / kTileH);
+    J.level_base = with_level_base ? blocks * 256 : 0;
+    blocks += (long long)(im.width / 16) * (im.height / 16);
+  }
+  if (tiles > plan->max_tiles) return ATDCT16_ENOMEM;
+  cudaError_t e = cudaMemcpyAsync(plan->d_jobs, plan->h_jobs, sizeof(ImageJob) * n, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaEventRecord(plan->upload_done, stream);
+  if (e != cudaSuccess) return ATDCT16_ECUDA;
+  plan->upload_pending = true;
+  plan->last_stream = stream;
+  *ntiles_out = tiles;
+  (void)elem;
+  return ATDCT16_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* atdct16_version(void) { return "atdct16 1.0 sm_103a"; }
+
+const char* atdct16_status_string(atdct16_status s) {
+  switch (s) {
+    case ATDCT16_OK: return "ok";
+    case ATDCT16_EINVAL: return "invalid argument";
+    case ATDCT16_ENOMEM: return "out of workspace or device memory";
+    case ATDCT16_ECUDA: return "CUDA runtime error";
+    case ATDCT16_ETIMEOUT: return "device-side wait timed out";
+    case ATDCT16_EUNSUPPORTED: return "unsupported request";
+    case ATDCT16_EDEVICE: return "kernel rejected a descriptor";
+  }
+  return "unknown status";
+}
+
+atdct16_status atdct16_host_butterfly(const int32_t* in, int32_t* out, int32_t inverse) {
+  if (!in || !out) return ATDCT16_EINVAL;
+  int x[16], y[16];
+  for (int i = 0; i < 16; ++i) x[i] = in[i];
+  if (inverse) inv16(x, y); else fwd16(x, y);
+  for (int i = 0; i < 16; ++i) out[i] = y[i];
+  return ATDCT16_OK;
+}
+
+atdct16_status atdct16_plan_destroy(atdct16_plan_t plan) {
+  if (!plan) return ATDCT16_EINVAL;
+  cudaSetDevice(plan->device);
+  if (plan->upload_done) cudaEventSynchronize(plan->upload_done);
+  if (plan->last_stream) cudaStreamSynchronize(plan->last_stream);
+  cudaFree(plan->d_jobs);
+  cudaFree(plan->d_wtab);
+  cudaFree(plan->d_qtab);
+  cudaFree(plan->d_tile_sse);
+  cudaFree(plan->d_status);
+  cudaFreeHost(plan->h_jobs);
+  if (plan->upload_done) cudaEventDestroy(plan->upload_done);
+  for (cudaEvent_t ev : plan->prof_events) cudaEventDestroy(ev);
+  delete plan;
+  return ATDCT16_OK;
+}
+
+atdct16_status atdct16_plan_create(atdct16_plan_t* out, atdct16_dtype dtype, int32_t max_images,
+                                   size_t workspace_budget_bytes, uint32_t flags) {
+  if (!out || max_images < 1 || flags != 0 || (dtype != ATDCT16_U8 && dtype != ATDCT16_I16)) return ATDCT16_EINVAL;
+  *out = nullptr;
+  atdct16_plan_st* plan = new (std::nothrow) atdct16_plan_st();
+  if (!plan) return ATDCT16_ENOMEM;
+  plan->dtype = dtype;
+  plan->max_images = max_images;
+  if (cudaGetDevice(&plan->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device) != cudaSuccess) {
+    delete plan;
+    return ATDCT16_ECUDA;
+  }
+  const size_t budget = workspace_budget_bytes ? workspace_budget_bytes : (size_t)256 << 20;
+  const size_t fixed = sizeof(ImageJob) * max_images +
+                       sizeof(float2) * kZonalTableEntries + sizeof(float4) * kQuantTableEntries + 256;
+  if (budget <= fixed + 1024 * sizeof(float)) {
+    delete plan;
+    return ATDCT16_ENOMEM;
+  }
+  plan->max_tiles = (long long)((budget - fixed) / sizeof(float));
+
+  // Host tables.  S^2 = 1 / nnz(row of T) (T T^T is diagonal with the row
+  // non-zero counts, Sec. 2), so W = 48 S^2 = 48 / nnz.
+  int nnz[16], rank[16][16];
+  row_nonzeros(nnz);
+  zigzag_rank16(rank);
+  std::vector<float2> wtab(kZonalTableEntries);
+  for (int r = 0; r <= 256; ++r)
+    for (int c = 0; c < 16; ++c)
+      for (int u = 0; u < 16; ++u) {
+        const double wgt = (48.0 / nnz[u]) * (48.0 / nnz[c]) / 256.0;  // exact in FP32
+        const bool keep = rank[u][c] < r;
+        wtab[(r * 16 + c) * 16 + u] = make_float2(keep ? (float)wgt : 0.f, keep ? 0.f : (float)wgt);
+      }
+  std::vector<float4> qtab(kQuantTableEntries);
+  for (int qp = 0; qp <= kMaxQP; ++qp) {
+    const double qs = std::pow(2.0, qp / 6.0);
+    for (int c = 0; c < 16; ++c)
+      for (int u = 0; u < 16; ++u) {
+        // s_u s_v as the product of the two FP64 diagonal entries of S
+        const double s = (1.0 / std::sqrt((double)nnz[u])) * (1.0 / std::sqrt((double)nnz[c]));
+        qtab[(qp * 16 + c) * 16 + u] = make_float4((float)(s / qs), (float)s, (float)(s * qs), (float)qs);
+      }
+  }
+
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_jobs, sizeof(ImageJob) * max_images);
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_wtab, sizeof(float2) * kZonalTableEntries);
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_qtab, sizeof(float4) * kQuantTableEntries);
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_tile_sse, sizeof(float) * plan->max_tiles);
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaHostAlloc(&plan->h_jobs, sizeof(ImageJob) * max_images, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->upload_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemcpy(plan->d_wtab, wtab.data(), sizeof(float2) * kZonalTableEntries, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(plan->d_qtab, qtab.data(), sizeof(float4) * kQuantTableEntries, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(plan->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    atdct16_plan_destroy(plan);
+    return e == cudaErrorMemoryAllocation ? ATDCT16_ENOMEM : ATDCT16_ECUDA;
+  }
+  plan->zonal_grid = plan->num_sms * zonal_ctas_per_sm();
+  plan->quant_grid = plan->num_sms * quant_ctas_per_sm();
+  *out = plan;
+  return ATDCT16_OK;
+}
+
+atdct16_status atdct16_forward(atdct16_plan_t plan, atdct16_dtype dtype, const void* d_src, int64_t pitch,
+                               int32_t w, int32_t h, int32_t* d_coef, cudaStream_t stream) {
+  if (!plan || !d_src || !d_coef || (dtype != ATDCT16_U8 && dtype != ATDCT16_I16)) return ATDCT16_EINVAL;
+  const int elem = dtype == ATDCT16_U8 ? 1 : 2;
+  if (w <= 0 || h <= 0 || (w & 15) || (h & 15) || pitch < (int64_t)w * elem || (pitch & 15)) return ATDCT16_EINVAL;
+  if (!aligned16(d_src) || !aligned16(d_coef)) return ATDCT16_EINVAL;
+  plan->last_stream = stream;
+  return from_cuda(launch_forward(dtype, d_src, pitch, w, h, d_coef, stream));
+}
+
+atdct16_status atdct16_inverse(atdct16_plan_t plan, atdct16_dtype dtype, const int32_t* d_coef, int32_t w,
+                               int32_t h, void* d_dst, int64_t pitch, cudaStream_t stream) {
+  if (!plan || !d_dst || !d_coef || (dtype != ATDCT16_U8 && dtype != ATDCT16_I16)) return ATDCT16_EINVAL;
+  const int elem = dtype == ATDCT16_U8 ? 1 : 2;
+  if (w <= 0 || h <= 0 || (w & 15) || (h & 15) || pitch < (int64_t)w * elem) return ATDCT16_EINVAL;
+  if (dtype == ATDCT16_I16 && ((pitch & 1) || (reinterpret_cast<uintptr_t>(d_dst) & 1))) return ATDCT16_EINVAL;
+  plan->last_stream = stream;
+  return from_cuda(launch_inverse(dtype, d_coef, w, h, d_dst, pitch, stream));
+}
+
+atdct16_status atdct16_compress_zonal(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n,
+                                      double* d_psnr, double* d_sse, cudaStream_t stream) {
+  if (!plan || !h_images || !d_psnr || n < 1 || n > plan->max_images) return ATDCT16_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    const atdct16_status s = check_image(h_images[i], 1, true);
+    if (s != ATDCT16_OK) return s;
+    if (h_images[i].r_or_qp < 0 || h_images[i].r_or_qp > 256) return ATDCT16_EINVAL;
+  }
+  long long ntiles = 0;
+  atdct16_status s = stage_jobs(plan, h_images, n, 1, stream, &ntiles, false);
+  if (s != ATDCT16_OK) return s;
+  const int grid = (int)std::min<long long>(plan->zonal_grid, (ntiles + kWarpsPerCta - 1) / kWarpsPerCta);
+  const int pk = prof_begin(plan, stream);
+  cudaError_t e = launch_zonal(plan->d_jobs, n, ntiles, plan->d_wtab, plan->d_tile_sse, plan->d_status, grid, stream);
+  prof_end(plan, pk, stream);
+  if (e == cudaSuccess)
+    e = launch_psnr_finalize(plan->d_jobs, n, ntiles, plan->d_tile_sse, 255.0, d_psnr, d_sse, stream);
+  return from_cuda(e);
+}
+
+atdct16_status atdct16_compress_quant(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n,
+                                      int16_t* d_levels, double* d_psnr, double* d_sse, cudaStream_t stream) {
+  if (!plan || !h_images || !d_psnr || n < 1 || n > plan->max_images) return ATDCT16_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    const atdct16_status s = check_image(h_images[i], 2, true);
+    if (s != ATDCT16_OK) return s;
+    if (h_images[i].r_or_qp < 0 || h_images[i].r_or_qp > kMaxQP) return ATDCT16_EINVAL;
+  }
+  if (d_levels && !aligned16(d_levels)) return ATDCT16_EINVAL;
+  long long ntiles = 0;
+  atdct16_status s = stage_jobs(plan, h_images, n, 2, stream, &ntiles, d_levels != nullptr);
+  if (s != ATDCT16_OK) return s;
+  const int grid = (int)std::min<long long>(plan->quant_grid, (ntiles + kWarpsPerCta - 1) / kWarpsPerCta);
+  const int pk = prof_begin(plan, stream);
+  cudaError_t e = launch_quant(plan->d_jobs, n, ntiles, plan->d_qtab, d_levels, plan->d_tile_sse,
+                               plan->d_status, grid, stream);
+  prof_end(plan, pk, stream);
+  if (e == cudaSuccess)
+    e = launch_psnr_finalize(plan->d_jobs, n, ntiles, plan->d_tile_sse, 255.0, d_psnr, d_sse, stream);
+  return from_cuda(e);
+}
+
+atdct16_status atdct16_psnr(atdct16_dtype dtype, const void* d_a, int64_t pitch_a, const void* d_b,
+                            int64_t pitch_b, int32_t w, int32_t h, double* d_out, cudaStream_t stream) {
+  if (!d_a || !d_b || !d_out || (dtype != ATDCT16_U8 && dtype != ATDCT16_I16)) return ATDCT16_EINVAL;
+  const int elem = dtype == ATDCT16_U8 ? 1 : 2;
+  if (w <= 0 || h <= 0 || pitch_a < (int64_t)w * elem || pitch_b < (int64_t)w * elem) return ATDCT16_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_out) & 7) != 0) return ATDCT16_EINVAL;
+  if (elem == 2 && ((pitch_a | pitch_b) & 1)) return ATDCT16_EINVAL;
+  return from_cuda(launch_psnr_pair(dtype, d_a, pitch_a, d_b, pitch_b, w, h, d_out, stream));
+}
+
+atdct16_status atdct16_plan_set_profiling(atdct16_plan_t plan, int32_t enable) {
+  if (!plan) return ATDCT16_EINVAL;
+  if (enable && plan->prof_events.empty()) {
+    plan->prof_events.resize(2 * kProfPairs, nullptr);
+    for (auto& ev : plan->prof_events)
+      if (cudaEventCreate(&ev) != cudaSuccess) return ATDCT16_ECUDA;
+  }
+  plan->profiling = enable != 0;
+  plan->prof_used = 0;
+  return ATDCT16_OK;
+}
+
+atdct16_status atdct16_plan_profile(atdct16_plan_t plan, int64_t* launches, double* kernel_ms) {
+  if (!plan || !launches || !kernel_ms) return ATDCT16_EINVAL;
+  double total = 0.0;
+  for (int k = 0; k < plan->prof_used; ++k) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(plan->prof_events[2 * k + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, plan->prof_events[2 * k], plan->prof_events[2 * k + 1]) != cudaSuccess)
+      return ATDCT16_ECUDA;
+    total += ms;
+  }
+  *launches = plan->prof_used;
+  *kernel_ms = total;
+  plan->prof_used = 0;
+  return ATDCT16_OK;
+}
+
+atdct16_status atdct16_last_device_status(atdct16_plan_t plan) {
+  if (!plan) return ATDCT16_EINVAL;
+  if (plan->last_stream && cudaStreamSynchronize(plan->last_stream) != cudaSuccess) return ATDCT16_ECUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return ATDCT16_ECUDA;
+  return v == kDevOk ? ATDCT16_OK : ATDCT16_EDEVICE;
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// Internal declarations shared by the kernels and the C-ABI layer.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace atdct16 {
+
+// A tile is 16 image rows x 128 columns (eight 16x16 blocks).  One warp
+// processes one tile at a time; the last tile of a row may hold fewer blocks.
+constexpr int kTileW = 128;
+constexpr int kTileH = 16;
+constexpr int kWarpsPerCta = 8;
+constexpr int kThreadsPerCta = 32 * kWarpsPerCta;
+
+// One image of a batch, as the kernels see it (64 bytes).
+struct ImageJob {
+  const uint8_t* src;
+  uint8_t* dst;
+  long long src_pitch;   // bytes
+  long long dst_pitch;   // bytes
+  long long tile_begin;  // first global tile index of this image
+  long long level_base;  // quantisation path: first int16 level of this image
+  int width;
+  int height;
+  int tiles_x;           // tiles per tile row = ceil(width / 128)
+  int param;             // zonal r (0..256) or quantisation point QP (0..63)
+};
+static_assert(sizeof(ImageJob) == 64, "ImageJob layout");
+
+// Zonal weights, one entry per (r, column c, row-frequency u):
+// (kw, dw) = (keep, 1 - keep) * W_u * W_c / 256, W = 48 S^2 = 48 / diag(T T^T).
+constexpr int kZonalTableEntries = 257 * 256;
+// Quantiser constants per (QP, c, u): (k, s, g, Qstep) with s = s_u s_c,
+// k = fp32(s / Qstep), g = fp32(s * Qstep).
+constexpr int kMaxQP = 63;
+constexpr int kQuantTableEntries = (kMaxQP + 1) * 256;
+
+// Device status codes written by kernels' own checks (sticky, first wins).
+constexpr int kDevOk = 0;
+constexpr int kDevBadJob = 1;
+
+// Kernel launchers (atdct16_kernels.cu).  All asynchronous on `stream`.
+cudaError_t launch_zonal(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
+                         float* d_tile_sse, int* d_status, int grid, cudaStream_t stream);
+cudaError_t launch_quant(const ImageJob* d_jobs, int njobs, long long ntiles, const float4* d_qtab,
+                         int16_t* d_levels, float* d_tile_sse, int* d_status, int grid,
+                         cudaStream_t stream);
+cudaError_t launch_psnr_finalize(const ImageJob* d_jobs, int njobs, long long ntiles,
+                                 const float* d_tile_sse, double peak, double* d_psnr,
+                                 double* d_sse, cudaStream_t stream);
+cudaError_t launch_forward(int dtype, const void* d_src, long long pitch, int w, int h,
+                           int32_t* d_coef, cudaStream_t stream);
+cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void* d_dst,
+                           long long pitch, cudaStream_t stream);
+cudaError_t launch_psnr_pair(int dtype, const void* d_a, long long pitch_a, const void* d_b,
+                             long long pitch_b, int w, int h, double* d_out, cudaStream_t stream);
+int zonal_ctas_per_sm();
+int quant_ctas_per_sm();
+
+}  // namespace atdct16

@@ -1,0 +1,675 @@
+// sm_103a kernels for the 16x16 multiplierless transform of arXiv 1606.05562.
+//
+// Work decomposition shared by the fused kernels
+// ----------------------------------------------
+// A warp owns one 16 x 128 tile (eight 16x16 blocks) at a time and walks the
+// tiles of a whole batch in a persistent loop.  Inside the warp, lane
+// l = 8 p + j works on the block pair (A, B) = (block p, block p + 4) of the
+// tile.  Every value is a packed float2 holding the same position of blocks A
+// and B, so each f32x2 instruction advances both blocks.
+//   row pass      : lane j holds image rows 2j, 2j+1 of A and B
+//   transpose     : through a warp-private 8 KB shared-memory buffer,
+//                   XOR-swizzled on 16-byte chunks (conflict-free both ways)
+//   column pass   : lane j holds columns 2j, 2j+1 of A and B
+//   scale / mask  : per coefficient, weights from a per-r table
+//   inverse column, transpose back, inverse row, round, store.
+//
+// Exactness.  u8 pixels enter as 2^23 + 256 x (one byte permute builds the
+// float); every forward node is then a multiple of 256 below 2^32, so the
+// integer transform Y = T X T^T is exact in FP32.  The zonal inverse works on
+// the integers D = keep * W_u W_v Y (W = 48 S^2 in {3, 4, 6}) and produces the
+// integer numerator Z = T^T D T of X_hat = Z / 2304; every intermediate stays
+// below 2^24 for all zig-zag prefixes and u8 input, so Z is exact too.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "atdct16_butterfly.cuh"
+#include "atdct16_internal.h"
+
+namespace atdct16 {
+
+// --------------------------------------------------------------------------
+// Value types for the generic butterflies.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2mul(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
+
+__device__ __forceinline__ unsigned word_of(const uint4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// 2^23 + 256 * (byte k of w): exact float built by one byte permute.
+__device__ __forceinline__ float u8_scaled(unsigned w, int k) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7404u | ((unsigned)k << 4)));
+}
+
+// d = (c << 16) | (sat_u8(a) << 8) | sat_u8(b)   (PTX cvt.pack semantics)
+__device__ __forceinline__ unsigned pack_u8(unsigned a, unsigned b, unsigned c) {
+  unsigned d;
+  asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+// d = (sat_s16(a) << 16) | sat_s16(b)
+__device__ __forceinline__ unsigned pack_s16(int a, int b) {
+  unsigned d;
+  asm("cvt.pack.sat.s16.s32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// Round half to even of x, clamped to 0..255, as the raw bits of a denormal:
+// fl(x * 2^-149) lands on the denormal grid, whose spacing is 2^-149, so its
+// bit pattern is rne(|x|) with the sign in bit 31.  As a signed 32-bit integer
+// that saturates to 0 for negative x and to 255 above 255 in cvt.pack.sat.
+__device__ __forceinline__ float2 rne_denormal(float2 x) {
+  return __fmul2_rn(x, make_float2(__uint_as_float(1u), __uint_as_float(1u)));
+}
+
+// fp32(1/2304): with it, fl(Z * c) equals Z / 2304 exactly whenever Z / 2304 is
+// a half-integer (Z is then a multiple of 9 and 9 * fp32(1/9) = 1 + 2^-27), and
+// is within 6e-5 of Z / 2304 otherwise, far inside the 1/2304 gap to any .5.
+__constant__ float kInv2304 = 1.0f / 2304.0f;
+
+__device__ __forceinline__ void warp_find_job(const ImageJob* __restrict__ jobs, int njobs,
+                                              long long t, int& job) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&jobs[mid].tile_begin) <= t) lo = mid; else hi = mid - 1;
+  }
+  job = lo;
+}
+
+__device__ __forceinline__ void set_status(int* status, int code) {
+  atomicCAS(status, kDevOk, code);
+}
+
+// Warp-private transpose buffer: 4 block pairs x 16 lines x 8 chunks of 16 B.
+struct alignas(16) WarpBuf {
+  float4 c[4 * 16 * 8];
+};
+
+// Row-stage values (rows 2j, 2j+1, all 16 positions) -> column-stage values
+// (columns 2j, 2j+1, all 16 positions).  Chunk (line, q) holds two float2
+// entries of one line; the chunk slot is XOR-swizzled by (line >> 1) & 7.
+__device__ __forceinline__ void transpose_rows_to_cols(float4* buf, int p, int j,
+                                                       const float2 (&r0)[16], const float2 (&r1)[16],
+                                                       float2 (&c0)[16], float2 (&c1)[16]) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+    buf[(p * 16 + k) * 8 + (j ^ ((k >> 1) & 7))] = make_float4(r0[k].x, r0[k].y, r1[k].x, r1[k].y);
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 v0 = buf[(p * 16 + 2 * j) * 8 + (q ^ j)];
+    const float4 v1 = buf[(p * 16 + 2 * j + 1) * 8 + (q ^ j)];
+    c0[2 * q] = make_float2(v0.x, v0.y);
+    c0[2 * q + 1] = make_float2(v0.z, v0.w);
+    c1[2 * q] = make_float2(v1.x, v1.y);
+    c1[2 * q + 1] = make_float2(v1.z, v1.w);
+  }
+  __syncwarp();
+}
+
+// Column-stage values (columns 2j, 2j+1 over all rows m) -> row-stage values
+// (rows 2j, 2j+1 over all columns).
+__device__ __forceinline__ void transpose_cols_to_rows(float4* buf, int p, int j,
+                                                       const float2 (&u0)[16], const float2 (&u1)[16],
+                                                       float2 (&v0)[16], float2 (&v1)[16]) {
+#pragma unroll
+  for (int m = 0; m < 16; ++m)
+    buf[(p * 16 + m) * 8 + (j ^ ((m >> 1) & 7))] = make_float4(u0[m].x, u0[m].y, u1[m].x, u1[m].y);
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 a = buf[(p * 16 + 2 * j) * 8 + (q ^ j)];
+    const float4 b = buf[(p * 16 + 2 * j + 1) * 8 + (q ^ j)];
+    v0[2 * q] = make_float2(a.x, a.y);
+    v0[2 * q + 1] = make_float2(a.z, a.w);
+    v1[2 * q] = make_float2(b.x, b.y);
+    v1[2 * q + 1] = make_float2(b.z, b.w);
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// --------------------------------------------------------------------------
+// Fused zonal compression: forward, keep the first r zig-zag coefficients,
+// S^2 scaling, inverse, round, store u8, per-tile SSE (Sec. 4 procedure).
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreadsPerCta, 1)
+zonal_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
+             const float2* __restrict__ wtab, float* __restrict__ tile_sse, int* __restrict__ status) {
+  __shared__ WarpBuf sbuf[kWarpsPerCta];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = lane >> 3, j = lane & 7;
+  float4* buf = sbuf[warp].c;
+  const long long nwarps = (long long)gridDim.x * kWarpsPerCta;
+
+  int job = -1;
+  long long jb = 0, je = 0;
+  ImageJob J;
+  for (long long t = (long long)blockIdx.x * kWarpsPerCta + warp; t < ntiles; t += nwarps) {
+    if (t < jb || t >= je) {
+      warp_find_job(jobs, njobs, t, job);
+      J = jobs[job];
+      jb = J.tile_begin;
+      je = jb + (long long)J.tiles_x * (J.height >> 4);
+      if (t < jb || t >= je) {  // descriptor table inconsistent with ntiles
+        if (lane == 0) set_status(status, kDevBadJob);
+        continue;
+      }
+    }
+    const long long lt = t - jb;
+    const int ty = (int)(lt / J.tiles_x);
+    const int tx = (int)(lt - (long long)ty * J.tiles_x);
+    const int x0 = tx * kTileW, y0 = ty * kTileH;
+    const int nb = min(8, (J.width - x0) >> 4);
+    const bool va = p < nb, vb = p + 4 < nb;
+
+    // ---- load rows 2j, 2j+1 of blocks A and B (16 B each)
+    const uint8_t* s = J.src + (long long)(y0 + 2 * j) * J.src_pitch + x0 + 16 * p;
+    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
+    if (va) {
+      a0 = __ldcs(reinterpret_cast<const uint4*>(s));
+      a1 = __ldcs(reinterpret_cast<const uint4*>(s + J.src_pitch));
+    }
+    if (vb) {
+      b0 = __ldcs(reinterpret_cast<const uint4*>(s + 64));
+      b1 = __ldcs(reinterpret_cast<const uint4*>(s + 64 + J.src_pitch));
+    }
+
+    // ---- row pass (Sec. 2 factorisation) on 2^23 + 256 x
+    float2 x0v[16], x1v[16], r0[16], r1[16];
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+      x0v[n] = make_float2(u8_scaled(word_of(a0, n >> 2), n & 3), u8_scaled(word_of(b0, n >> 2), n & 3));
+      x1v[n] = make_float2(u8_scaled(word_of(a1, n >> 2), n & 3), u8_scaled(word_of(b1, n >> 2), n & 3));
+    }
+    fwd16(x0v, r0);
+    fwd16(x1v, r1);
+    // row 0 of T sums all 16 inputs: remove 16 * 2^23 (exact)
+    r0[0] = bsub(r0[0], make_float2(134217728.0f, 134217728.0f));
+    r1[0] = bsub(r1[0], make_float2(134217728.0f, 134217728.0f));
+
+    // ---- transpose, column pass: y = 256 Y (exact)
+    float2 c0[16], c1[16];
+    transpose_rows_to_cols(buf, p, j, r0, r1, c0, c1);
+    float2 ya[16], yb[16];
+    fwd16(c0, ya);
+    fwd16(c1, yb);
+
+    // ---- zonal mask and S^2 weights; dropped energy (Parseval) for the SSE
+    const float4* w0 = reinterpret_cast<const float4*>(wtab + ((long long)J.param * 16 + 2 * j) * 16);
+    const float4* w1 = w0 + 8;
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int h = 0; h < 8; ++h) {
+      const float4 wa = __ldg(w0 + h);
+      const float4 wb = __ldg(w1 + h);
+      acc = __ffma2_rn(f2mul(ya[2 * h], wa.y), ya[2 * h], acc);
+      acc = __ffma2_rn(f2mul(ya[2 * h + 1], wa.w), ya[2 * h + 1], acc);
+      acc = __ffma2_rn(f2mul(yb[2 * h], wb.y), yb[2 * h], acc);
+      acc = __ffma2_rn(f2mul(yb[2 * h + 1], wb.w), yb[2 * h + 1], acc);
+      ya[2 * h] = f2mul(ya[2 * h], wa.x);
+      ya[2 * h + 1] = f2mul(ya[2 * h + 1], wa.z);
+      yb[2 * h] = f2mul(yb[2 * h], wb.x);
+      yb[2 * h + 1] = f2mul(yb[2 * h + 1], wb.z);
+    }
+
+    // ---- inverse: column pass, transpose back, row pass -> exact Z
+    float2 u0[16], u1[16];
+    inv16(ya, u0);
+    inv16(yb, u1);
+    float2 v0[16], v1[16];
+    transpose_cols_to_rows(buf, p, j, u0, u1, v0, v1);
+    float2 z0[16], z1[16];
+    inv16(v0, z0);
+    inv16(v1, z1);
+
+    // ---- round half to even, clamp, pack, store
+    uint4 oa0, oa1, ob0, ob1;
+    unsigned qa0[16], qa1[16], qb0[16], qb1[16];
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+      const float2 e0 = rne_denormal(f2mul(z0[n], kInv2304));
+      const float2 e1 = rne_denormal(f2mul(z1[n], kInv2304));
+      qa0[n] = __float_as_uint(e0.x);
+      qb0[n] = __float_as_uint(e0.y);
+      qa1[n] = __float_as_uint(e1.x);
+      qb1[n] = __float_as_uint(e1.y);
+    }
+#define ATDCT16_PACK4(q, i) pack_u8(q[4 * (i) + 1], q[4 * (i)], pack_u8(q[4 * (i) + 3], q[4 * (i) + 2], 0u))
+    oa0 = make_uint4(ATDCT16_PACK4(qa0, 0), ATDCT16_PACK4(qa0, 1), ATDCT16_PACK4(qa0, 2), ATDCT16_PACK4(qa0, 3));
+    oa1 = make_uint4(ATDCT16_PACK4(qa1, 0), ATDCT16_PACK4(qa1, 1), ATDCT16_PACK4(qa1, 2), ATDCT16_PACK4(qa1, 3));
+    ob0 = make_uint4(ATDCT16_PACK4(qb0, 0), ATDCT16_PACK4(qb0, 1), ATDCT16_PACK4(qb0, 2), ATDCT16_PACK4(qb0, 3));
+    ob1 = make_uint4(ATDCT16_PACK4(qb1, 0), ATDCT16_PACK4(qb1, 1), ATDCT16_PACK4(qb1, 2), ATDCT16_PACK4(qb1, 3));
+#undef ATDCT16_PACK4
+    uint8_t* d = J.dst + (long long)(y0 + 2 * j) * J.dst_pitch + x0 + 16 * p;
+    if (va) {
+      __stcs(reinterpret_cast<uint4*>(d), oa0);
+      __stcs(reinterpret_cast<uint4*>(d + J.dst_pitch), oa1);
+    }
+    if (vb) {
+      __stcs(reinterpret_cast<uint4*>(d + 64), ob0);
+      __stcs(reinterpret_cast<uint4*>(d + 64 + J.dst_pitch), ob1);
+    }
+
+    // ---- tile SSE: dropped energy / (256 * 2304), summed over valid blocks
+    const float tot = warp_sum((va ? acc.x : 0.f) + (vb ? acc.y : 0.f));
+    if (lane == 0) tile_sse[t] = tot * (1.0f / (256.0f * 2304.0f));
+  }
+}
+
+// --------------------------------------------------------------------------
+// Fused quantisation (S absorbed into the quantiser) for int16 planes.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ float i16_lo(unsigned w) { return (float)(short)(w & 0xffffu); }
+__device__ __forceinline__ float i16_hi(unsigned w) { return (float)(short)(w >> 16); }
+
+__global__ void __launch_bounds__(kThreadsPerCta, 1)
+quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
+             const float4* __restrict__ qtab, int16_t* __restrict__ levels, float* __restrict__ tile_sse,
+             int* __restrict__ status) {
+  __shared__ WarpBuf sbuf[kWarpsPerCta];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = lane >> 3, j = lane & 7;
+  float4* buf = sbuf[warp].c;
+  const long long nwarps = (long long)gridDim.x * kWarpsPerCta;
+
+  int job = -1;
+  long long jb = 0, je = 0;
+  ImageJob J;
+  for (long long t = (long long)blockIdx.x * kWarpsPerCta + warp; t < ntiles; t += nwarps) {
+    if (t < jb || t >= je) {
+      warp_find_job(jobs, njobs, t, job);
+      J = jobs[job];
+      jb = J.tile_begin;
+      je = jb + (long long)J.tiles_x * (J.height >> 4);
+      if (t < jb || t >= je) {
+        if (lane == 0) set_status(status, kDevBadJob);
+        continue;
+      }
+    }
+    const long long lt = t - jb;
+    const int ty = (int)(lt / J.tiles_x);
+    const int tx = (int)(lt - (long long)ty * J.tiles_x);
+    const int x0 = tx * kTileW, y0 = ty * kTileH;
+    const int nb = min(8, (J.width - x0) >> 4);
+    const bool va = p < nb, vb = p + 4 < nb;
+
+    // ---- load rows 2j, 2j+1 of A and B: 32 B each
+    const uint8_t* s = J.src + (long long)(y0 + 2 * j) * J.src_pitch + 2 * (x0 + 16 * p);
+    uint4 a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = b[i] = make_uint4(0, 0, 0, 0);
+    if (va) {
+      a[0] = __ldcs(reinterpret_cast<const uint4*>(s));
+      a[1] = __ldcs(reinterpret_cast<const uint4*>(s + 16));
+      a[2] = __ldcs(reinterpret_cast<const uint4*>(s + J.src_pitch));
+      a[3] = __ldcs(reinterpret_cast<const uint4*>(s + J.src_pitch + 16));
+    }
+    if (vb) {
+      b[0] = __ldcs(reinterpret_cast<const uint4*>(s + 128));
+      b[1] = __ldcs(reinterpret_cast<const uint4*>(s + 144));
+      b[2] = __ldcs(reinterpret_cast<const uint4*>(s + J.src_pitch + 128));
+      b[3] = __ldcs(reinterpret_cast<const uint4*>(s + J.src_pitch + 144));
+    }
+    float2 x0v[16], x1v[16], r0[16], r1[16];
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+      const int wi = (n >> 1) & 3, hi = n & 1, part = n >> 3;
+      const unsigned wa0 = word_of(a[part], wi), wb0 = word_of(b[part], wi);
+      const unsigned wa1 = word_of(a[2 + part], wi), wb1 = word_of(b[2 + part], wi);
+      x0v[n] = make_float2(hi ? i16_hi(wa0) : i16_lo(wa0), hi ? i16_hi(wb0) : i16_lo(wb0));
+      x1v[n] = make_float2(hi ? i16_hi(wa1) : i16_lo(wa1), hi ? i16_hi(wb1) : i16_lo(wb1));
+    }
+    fwd16(x0v, r0);
+    fwd16(x1v, r1);
+    float2 c0[16], c1[16];
+    transpose_rows_to_cols(buf, p, j, r0, r1, c0, c1);
+    float2 ya[16], yb[16];
+    fwd16(c0, ya);  // exact integers Y
+    fwd16(c1, yb);
+
+    // ---- quantise: level = sign(Y) floor(fp32(|Y| k) + 0.5), k = fp32(s/Qstep)
+    const float4* q0 = qtab + ((long long)J.param * 16 + 2 * j) * 16;
+    const float4* q1 = q0 + 16;
+    float2 acc = make_float2(0.f, 0.f);
+    const long long lbase = J.level_base;
+    const int bpr = J.width >> 4;
+    const long long blk_a = (long long)(y0 >> 4) * bpr + (x0 >> 4) + p;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const float4 qa = __ldg(q0 + u), qb = __ldg(q1 + u);  // (k, s, g, Qstep)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        float2& y = i ? yb[u] : ya[u];
+        const float4& q = i ? qb : qa;
+        const float la = copysignf(floorf(__fadd_rn(__fmul_rn(fabsf(y.x), q.x), 0.5f)), y.x);
+        const float lb = copysignf(floorf(__fadd_rn(__fmul_rn(fabsf(y.y), q.x), 0.5f)), y.y);
+        // Parseval: error energy of B - B' in the orthonormal domain
+        const float ea = fmaf(la, -q.w, __fmul_rn(y.x, q.y));
+        const float eb = fmaf(lb, -q.w, __fmul_rn(y.y, q.y));
+        acc.x = fmaf(ea, ea, acc.x);
+        acc.y = fmaf(eb, eb, acc.y);
+        if (levels) {
+          const int col = 2 * j + i;
+          if (va) levels[lbase + blk_a * 256 + u * 16 + col] = (int16_t)la;
+          if (vb) levels[lbase + (blk_a + 4) * 256 + u * 16 + col] = (int16_t)lb;
+        }
+        y = make_float2(la * q.z, lb * q.z);  // S B' S entry
+      }
+    }
+    float2 u0[16], u1[16];
+    inv16(ya, u0);
+    inv16(yb, u1);
+    float2 v0[16], v1[16];
+    transpose_cols_to_rows(buf, p, j, u0, u1, v0, v1);
+    float2 z0[16], z1[16];
+    inv16(v0, z0);
+    inv16(v1, z1);
+
+    // ---- rint, clamp to int16, store
+    uint4 oa[4], ob[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      // words 2i, 2i+1 of each 16-sample row hold samples 4i .. 4i+3
+      const int n = 4 * i;
+      const int row_part = 0;
+      (void)row_part;
+      unsigned a00 = pack_s16(__float2int_rn(z0[n + 1].x), __float2int_rn(z0[n].x));
+      unsigned a01 = pack_s16(__float2int_rn(z0[n + 3].x), __float2int_rn(z0[n + 2].x));
+      unsigned b00 = pack_s16(__float2int_rn(z0[n + 1].y), __float2int_rn(z0[n].y));
+      unsigned b01 = pack_s16(__float2int_rn(z0[n + 3].y), __float2int_rn(z0[n + 2].y));
+      unsigned a10 = pack_s16(__float2int_rn(z1[n + 1].x), __float2int_rn(z1[n].x));
+      unsigned a11 = pack_s16(__float2int_rn(z1[n + 3].x), __float2int_rn(z1[n + 2].x));
+      unsigned b10 = pack_s16(__float2int_rn(z1[n + 1].y), __float2int_rn(z1[n].y));
+      unsigned b11 = pack_s16(__float2int_rn(z1[n + 3].y), __float2int_rn(z1[n + 2].y));
+      // oa[0..1]: row 2j (32 B), oa[2..3]: row 2j+1
+      unsigned* pa0 = reinterpret_cast<unsigned*>(&oa[i >> 1]);
+      unsigned* pa1 = reinterpret_cast<unsigned*>(&oa[2 + (i >> 1)]);
+      unsigned* pb0 = reinterpret_cast<unsigned*>(&ob[i >> 1]);
+      unsigned* pb1 = reinterpret_cast<unsigned*>(&ob[2 + (i >> 1)]);
+      const int o = 2 * (i & 1);
+      pa0[o] = a00; pa0[o + 1] = a01;
+      pa1[o] = a10; pa1[o + 1] = a11;
+      pb0[o] = b00; pb0[o + 1] = b01;
+      pb1[o] = b10; pb1[o + 1] = b11;
+    }
+    uint8_t* d = J.dst + (long long)(y0 + 2 * j) * J.dst_pitch + 2 * (x0 + 16 * p);
+    if (va) {
+      __stcs(reinterpret_cast<uint4*>(d), oa[0]);
+      __stcs(reinterpret_cast<uint4*>(d + 16), oa[1]);
+      __stcs(reinterpret_cast<uint4*>(d + J.dst_pitch), oa[2]);
+      __stcs(reinterpret_cast<uint4*>(d + J.dst_pitch + 16), oa[3]);
+    }
+    if (vb) {
+      __stcs(reinterpret_cast<uint4*>(d + 128), ob[0]);
+      __stcs(reinterpret_cast<uint4*>(d + 144), ob[1]);
+      __stcs(reinterpret_cast<uint4*>(d + J.dst_pitch + 128), ob[2]);
+      __stcs(reinterpret_cast<uint4*>(d + J.dst_pitch + 144), ob[3]);
+    }
+    const float tot = warp_sum((va ? acc.x : 0.f) + (vb ? acc.y : 0.f));
+    if (lane == 0) tile_sse[t] = tot;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Per-image PSNR from the per-tile SSE partials (FP64, fixed summation order).
+// --------------------------------------------------------------------------
+__global__ void psnr_finalize_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
+                                     const float* __restrict__ tile_sse, double peak,
+                                     double* __restrict__ psnr, double* __restrict__ sse_out) {
+  const int lane = threadIdx.x & 31;
+  const int job = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (job >= njobs) return;
+  const long long b = jobs[job].tile_begin;
+  const long long e = (job + 1 < njobs) ? jobs[job + 1].tile_begin : ntiles;
+  double s = 0.0;
+  for (long long t = b + lane; t < e; t += 32) s += (double)tile_sse[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    const double npx = (double)jobs[job].width * (double)jobs[job].height;
+    psnr[job] = s > 0.0 ? 10.0 * log10(peak * peak * npx / s) : CUDART_INF;
+    if (sse_out) sse_out[job] = s;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Forward transform to exact int32 coefficients (block-major, (u, v) row-major).
+// --------------------------------------------------------------------------
+template <int kDtype>  // 0: u8, 1: i16
+__global__ void __launch_bounds__(kThreadsPerCta)
+forward_kernel(const uint8_t* __restrict__ src, long long pitch, int w, int h, int32_t* __restrict__ coef) {
+  __shared__ WarpBuf sbuf[kWarpsPerCta];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = lane >> 3, j = lane & 7;
+  float4* buf = sbuf[warp].c;
+  const int tiles_x = (w + kTileW - 1) / kTileW;
+  const long long t = (long long)blockIdx.x * kWarpsPerCta + warp;
+  if (t >= (long long)tiles_x * (h >> 4)) return;
+  const int ty = (int)(t / tiles_x), tx = (int)(t - (long long)ty * tiles_x);
+  const int x0 = tx * kTileW, y0 = ty * kTileH;
+  const int nb = min(8, (w - x0) >> 4);
+  const bool va = p < nb, vb = p + 4 < nb;
+  float2 x0v[16], x1v[16], r0[16], r1[16];
+  if (kDtype == 0) {
+    const uint8_t* s = src + (long long)(y0 + 2 * j) * pitch + x0 + 16 * p;
+    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
+    if (va) { a0 = *reinterpret_cast<const uint4*>(s); a1 = *reinterpret_cast<const uint4*>(s + pitch); }
+    if (vb) { b0 = *reinterpret_cast<const uint4*>(s + 64); b1 = *reinterpret_cast<const uint4*>(s + 64 + pitch); }
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+      x0v[n] = make_float2(u8_scaled(word_of(a0, n >> 2), n & 3), u8_scaled(word_of(b0, n >> 2), n & 3));
+      x1v[n] = make_float2(u8_scaled(word_of(a1, n >> 2), n & 3), u8_scaled(word_of(b1, n >> 2), n & 3));
+    }
+  } else {
+    const uint8_t* s = src + (long long)(y0 + 2 * j) * pitch + 2 * (x0 + 16 * p);
+    uint4 a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = b[i] = make_uint4(0, 0, 0, 0);
+    if (va) {
+      a[0] = *reinterpret_cast<const uint4*>(s); a[1] = *reinterpret_cast<const uint4*>(s + 16);
+      a[2] = *reinterpret_cast<const uint4*>(s + pitch); a[3] = *reinterpret_cast<const uint4*>(s + pitch + 16);
+    }
+    if (vb) {
+      b[0] = *reinterpret_cast<const uint4*>(s + 128); b[1] = *reinterpret_cast<const uint4*>(s + 144);
+      b[2] = *reinterpret_cast<const uint4*>(s + pitch + 128); b[3] = *reinterpret_cast<const uint4*>(s + pitch + 144);
+    }
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+      const int wi = (n >> 1) & 3, hi = n & 1, part = n >> 3;
+      const unsigned wa0 = word_of(a[part], wi), wb0 = word_of(b[part], wi);
+      const unsigned wa1 = word_of(a[2 + part], wi), wb1 = word_of(b[2 + part], wi);
+      x0v[n] = make_float2(hi ? i16_hi(wa0) : i16_lo(wa0), hi ? i16_hi(wb0) : i16_lo(wb0));
+      x1v[n] = make_float2(hi ? i16_hi(wa1) : i16_lo(wa1), hi ? i16_hi(wb1) : i16_lo(wb1));
+    }
+  }
+  fwd16(x0v, r0);
+  fwd16(x1v, r1);
+  if (kDtype == 0) {
+    r0[0] = bsub(r0[0], make_float2(134217728.0f, 134217728.0f));
+    r1[0] = bsub(r1[0], make_float2(134217728.0f, 134217728.0f));
+  }
+  float2 c0[16], c1[16], y0v[16], y1v[16];
+  transpose_rows_to_cols(buf, p, j, r0, r1, c0, c1);
+  fwd16(c0, y0v);
+  fwd16(c1, y1v);
+  const float sc = kDtype == 0 ? (1.0f / 256.0f) : 1.0f;
+  const int bpr = w >> 4;
+  const long long blk = (long long)(y0 >> 4) * bpr + (x0 >> 4) + p;
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    if (va)
+      *reinterpret_cast<int2*>(coef + blk * 256 + u * 16 + 2 * j) =
+          make_int2(__float2int_rn(y0v[u].x * sc), __float2int_rn(y1v[u].x * sc));
+    if (vb)
+      *reinterpret_cast<int2*>(coef + (blk + 4) * 256 + u * 16 + 2 * j) =
+          make_int2(__float2int_rn(y0v[u].y * sc), __float2int_rn(y1v[u].y * sc));
+  }
+}
+
+// --------------------------------------------------------------------------
+// Exact inverse in 64-bit integers: Z = T^T (W Y W) T, X_hat = Z / 2304,
+// round half to even, clamp.  16 threads per block, 16 blocks per CTA.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ long long rne_div(long long z, long long d) {
+  // floor((z + d/2) / d), then ties (remainder 0 after the shift) to even
+  const long long n = z + d / 2;
+  long long q = n >= 0 ? n / d : -((-n + d - 1) / d);
+  if (n - q * d == 0 && (q & 1)) q -= 1;
+  return q;
+}
+
+template <int kDtype>
+__global__ void __launch_bounds__(256)
+inverse_exact_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __restrict__ dst, long long pitch) {
+  __shared__ long long su[16][16][17];
+  // W = 48 S^2 from the printed S of Sec. 2: S^2 = 1/16, 1/12 or 1/8.
+  const int Wd[16] = {3, 3, 4, 6, 6, 3, 4, 4, 3, 4, 4, 6, 6, 4, 4, 4};
+  const int bl = threadIdx.x >> 4, t = threadIdx.x & 15;
+  const int bpr = w >> 4;
+  const long long nblk = (long long)bpr * (h >> 4);
+  const long long b = (long long)blockIdx.x * 16 + bl;
+  const bool valid = b < nblk;
+  long long d[16], u[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+    d[k] = valid ? (long long)Wd[k] * Wd[t] * (long long)coef[b * 256 + k * 16 + t] : 0;
+  inv16(d, u);  // column t: U[m][t]
+#pragma unroll
+  for (int m = 0; m < 16; ++m) su[bl][m][t] = u[m];
+  __syncthreads();
+  long long v[16], z[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) v[c] = su[bl][t][c];
+  inv16(v, z);  // row t: Z[t][n]
+  if (!valid) return;
+  const long long by = b / bpr, bx = b - by * bpr;
+  uint8_t* o = dst + (by * 16 + t) * pitch;
+  if (kDtype == 0) {
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+      const long long q = rne_div(z[n], 2304);
+      o[bx * 16 + n] = (uint8_t)(q < 0 ? 0 : (q > 255 ? 255 : q));
+    }
+  } else {
+    int16_t* o16 = reinterpret_cast<int16_t*>(o);
+#pragma unroll
+    for (int n = 0; n < 16; ++n) {
+      const long long q = rne_div(z[n], 2304);
+      o16[bx * 16 + n] = (int16_t)(q < -32768 ? -32768 : (q > 32767 ? 32767 : q));
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// PSNR of two images, exact integer SSE accumulated in the output slot.
+// --------------------------------------------------------------------------
+template <int kDtype>
+__global__ void psnr_pair_kernel(const uint8_t* __restrict__ a, long long pa, const uint8_t* __restrict__ b,
+                                 long long pb, int w, int h, unsigned long long* __restrict__ acc) {
+  unsigned long long s = 0;
+  const long long n = (long long)w * h;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long y = i / w, x = i - y * w;
+    long long d;
+    if (kDtype == 0) d = (long long)a[y * pa + x] - (long long)b[y * pb + x];
+    else d = (long long)reinterpret_cast<const int16_t*>(a + y * pa)[x] - (long long)reinterpret_cast<const int16_t*>(b + y * pb)[x];
+    s += (unsigned long long)(d * d);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(acc, s);
+}
+
+__global__ void psnr_pair_finish(unsigned long long* slot, double npx, double peak) {
+  const unsigned long long s = *slot;
+  *reinterpret_cast<double*>(slot) = s ? 10.0 * log10(peak * peak * npx / (double)s) : CUDART_INF;
+}
+
+// --------------------------------------------------------------------------
+// Launchers
+// --------------------------------------------------------------------------
+cudaError_t launch_zonal(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
+                         float* d_tile_sse, int* d_status, int grid, cudaStream_t stream) {
+  if (ntiles <= 0) return cudaSuccess;
+  zonal_kernel<<<grid, kThreadsPerCta, 0, stream>>>(d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quant(const ImageJob* d_jobs, int njobs, long long ntiles, const float4* d_qtab,
+                         int16_t* d_levels, float* d_tile_sse, int* d_status, int grid,
+                         cudaStream_t stream) {
+  if (ntiles <= 0) return cudaSuccess;
+  quant_kernel<<<grid, kThreadsPerCta, 0, stream>>>(d_jobs, njobs, ntiles, d_qtab, d_levels, d_tile_sse,
+                                                      d_status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_psnr_finalize(const ImageJob* d_jobs, int njobs, long long ntiles, const float* d_tile_sse,
+                                 double peak, double* d_psnr, double* d_sse, cudaStream_t stream) {
+  if (njobs <= 0) return cudaSuccess;
+  const int warps = 8;
+  psnr_finalize_kernel<<<(njobs + warps - 1) / warps, 32 * warps, 0, stream>>>(d_jobs, njobs, ntiles, d_tile_sse,
+                                                                               peak, d_psnr, d_sse);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward(int dtype, const void* d_src, long long pitch, int w, int h, int32_t* d_coef,
+                           cudaStream_t stream) {
+  const long long tiles = (long long)((w + kTileW - 1) / kTileW) * (h >> 4);
+  const int grid = (int)((tiles + kWarpsPerCta - 1) / kWarpsPerCta);
+  if (dtype == 0)
+    forward_kernel<0><<<grid, kThreadsPerCta, 0, stream>>>((const uint8_t*)d_src, pitch, w, h, d_coef);
+  else
+    forward_kernel<1><<<grid, kThreadsPerCta, 0, stream>>>((const uint8_t*)d_src, pitch, w, h, d_coef);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void* d_dst, long long pitch,
+                           cudaStream_t stream) {
+  const long long nblk = (long long)(w >> 4) * (h >> 4);
+  const int grid = (int)((nblk + 15) / 16);
+  if (dtype == 0)
+    inverse_exact_kernel<0><<<grid, 256, 0, stream>>>(d_coef, w, h, (uint8_t*)d_dst, pitch);
+  else
+    inverse_exact_kernel<1><<<grid, 256, 0, stream>>>(d_coef, w, h, (uint8_t*)d_dst, pitch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_psnr_pair(int dtype, const void* d_a, long long pitch_a, const void* d_b, long long pitch_b,
+                             int w, int h, double* d_out, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double), stream);
+  if (e != cudaSuccess) return e;
+  unsigned long long* slot = reinterpret_cast<unsigned long long*>(d_out);
+  const long long n = (long long)w * h;
+  int grid = (int)((n + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  if (dtype == 0)
+    psnr_pair_kernel<0><<<grid, 256, 0, stream>>>((const uint8_t*)d_a, pitch_a, (const uint8_t*)d_b, pitch_b, w, h, slot);
+  else
+    psnr_pair_kernel<1><<<grid, 256, 0, stream>>>((const uint8_t*)d_a, pitch_a, (const uint8_t*)d_b, pitch_b, w, h, slot);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  psnr_pair_finish<<<1, 1, 0, stream>>>(slot, (double)n, 255.0);
+  return cudaGetLastError();
+}
+
+int zonal_ctas_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_kernel, kThreadsPerCta, 0) != cudaSuccess || n < 1) n = 1;
+  return n;
+}
+int quant_ctas_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, quant_kernel, kThreadsPerCta, 0) != cudaSuccess || n < 1) n = 1;
+  return n;
+}
+
+}  // namespace atdct16

@@ -1,0 +1,37 @@
+// Value-type operations used by the generic butterflies: badd(a, b) = a + b,
+// bsub(a, b) = a - b.  Integers for host-side tests and the exact inverse;
+// float and packed float2 (one f32x2 instruction per pair) on the device.
+#pragma once
+
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+#define ATDCT16_OPS_HD __host__ __device__ __forceinline__
+#else
+#define ATDCT16_OPS_HD inline
+#endif
+
+namespace atdct16 {
+
+ATDCT16_OPS_HD int badd(int a, int b) { return a + b; }
+ATDCT16_OPS_HD int bsub(int a, int b) { return a - b; }
+ATDCT16_OPS_HD long long badd(long long a, long long b) { return a + b; }
+ATDCT16_OPS_HD long long bsub(long long a, long long b) { return a - b; }
+
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned long long f2_bits(float2 v) {
+  return (unsigned long long)__float_as_uint(v.x) | ((unsigned long long)__float_as_uint(v.y) << 32);
+}
+__device__ __forceinline__ float2 bits_f2(unsigned long long u) {
+  return make_float2(__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32)));
+}
+__device__ __forceinline__ float2 badd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 bsub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(d);
+}
+__device__ __forceinline__ float badd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float bsub(float a, float b) { return __fsub_rn(a, b); }
+#endif
+
+}  // namespace atdct16

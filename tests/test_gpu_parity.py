@@ -1,0 +1,293 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer work (coefficients, stored pixels, quantisation levels) must match
+bit for bit; FP32 results (PSNR, int16 reconstructions of the quantisation
+path) are held to the stated tolerances.  Sizes span several tiles and
+ragged tails; the last tests run the full 64 x 512 x 512 batch and check
+sampled images one by one.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1606_05562_gb300 import atdct16, build, synth
+
+pytestmark = pytest.mark.gpu
+
+PSNR_RTOL = 1e-5
+R_SWEEP = synth.ZONAL_R_SWEEP
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    atdct16.lib()
+    return t
+
+
+@pytest.fixture(scope="module")
+def plan(torch):
+    p = atdct16.Plan(atdct16.U8, max_images=1024, workspace_bytes=256 << 20)
+    yield p
+    assert p.last_device_status() == atdct16.OK
+    p.close()
+
+
+@pytest.fixture(scope="module")
+def qplan(torch):
+    p = atdct16.Plan(atdct16.I16, max_images=64)
+    yield p
+    assert p.last_device_status() == atdct16.OK
+    p.close()
+
+
+def dev_image(torch, arr, pitch_extra=0):
+    """Device copy of a 2-D array; optional padding makes the pitch differ
+    from the width.  Returns the (H, W) view."""
+    h, w = arr.shape
+    base = torch.zeros((h, w + pitch_extra), dtype=torch.uint8 if arr.dtype == np.uint8 else torch.int16,
+                       device="cuda")
+    view = base[:, :w]
+    view.copy_(torch.from_numpy(np.ascontiguousarray(arr)))
+    return view
+
+
+def empty_like_img(torch, h, w, dtype, pitch_extra=0):
+    base = torch.full((h, w + pitch_extra), 77, dtype=dtype, device="cuda")
+    return base[:, :w]
+
+
+def run_zonal(torch, plan, imgs, rs, pitch_extra=0):
+    srcs = [dev_image(torch, im, pitch_extra) for im in imgs]
+    dsts = [empty_like_img(torch, im.shape[0], im.shape[1], torch.uint8, pitch_extra) for im in imgs]
+    descs = [atdct16.image(s, d, r) for s, d, r in zip(srcs, dsts, rs)]
+    psnr = torch.empty(len(imgs), dtype=torch.float64, device="cuda")
+    sse = torch.empty(len(imgs), dtype=torch.float64, device="cuda")
+    plan.compress_zonal(descs, psnr, sse)
+    torch.cuda.synchronize()
+    return [d.cpu().numpy() for d in dsts], psnr.cpu().numpy(), sse.cpu().numpy()
+
+
+def check_zonal(img, r, out, psnr, sse):
+    ref = O.compress_zonal_exact(img, r)
+    assert np.array_equal(out, ref["recon_u8"]), f"r={r}: {np.count_nonzero(out != ref['recon_u8'])} pixels differ"
+    if math.isinf(ref["psnr"]):
+        assert math.isinf(psnr) and sse == 0.0
+    else:
+        assert psnr == pytest.approx(ref["psnr"], rel=PSNR_RTOL)
+        assert sse == pytest.approx(ref["sse"], rel=1e-4, abs=1e-3)
+
+
+# ------------------------------------------------------------- config 1 ---
+def test_forward_256_bit_exact(torch, plan):
+    img = synth.single_image_256()
+    x = dev_image(torch, img)
+    coef = torch.empty(256 * 256, dtype=torch.int32, device="cuda")
+    plan.forward(x, coef)
+    torch.cuda.synchronize()
+    ref = O.forward_int(img).reshape(-1)
+    assert np.array_equal(coef.cpu().numpy(), ref)
+
+
+def test_inverse_256_reconstructs_exactly(torch, plan):
+    img = synth.single_image_256()
+    x = dev_image(torch, img)
+    coef = torch.empty(256 * 256, dtype=torch.int32, device="cuda")
+    plan.forward(x, coef)
+    out = empty_like_img(torch, 256, 256, torch.uint8)
+    plan.inverse(coef, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), img)
+
+
+@pytest.mark.parametrize("shape", [(16, 16), (48, 272), (64, 96)])
+def test_forward_inverse_i16_bit_exact(torch, plan, shape):
+    x = synth.laplacian_residual(*shape, seed=11)
+    x[0, :16] = 32767
+    x[1, :16] = -32768
+    xd = dev_image(torch, x)
+    nblk = (shape[0] // 16) * (shape[1] // 16)
+    coef = torch.empty(nblk * 256, dtype=torch.int32, device="cuda")
+    plan.forward(xd, coef, dtype=atdct16.I16)
+    out = empty_like_img(torch, *shape, torch.int16)
+    plan.inverse(coef, out, dtype=atdct16.I16)
+    torch.cuda.synchronize()
+    assert np.array_equal(coef.cpu().numpy(), O.forward_int(x).reshape(-1))
+    assert np.array_equal(out.cpu().numpy(), x)
+
+
+@pytest.mark.parametrize("r", [0, 1, 7, 36, 150])
+def test_inverse_of_masked_coefficients_exact(torch, plan, r):
+    img = synth.ar1_image(48, 80, 0.9, 5)
+    y = O.forward_int(img)
+    yk = np.where(O.zonal_mask(r)[None, None], y, 0)
+    coef = torch.from_numpy(np.ascontiguousarray(yk.reshape(-1).astype(np.int32))).cuda()
+    out = empty_like_img(torch, 48, 80, torch.uint8)
+    plan.inverse(coef, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), O.inverse_exact(yk))
+
+
+# ------------------------------------------------------ zonal, small ---
+def _small_images():
+    rng = np.random.default_rng(42)
+    imgs = [
+        synth.ar1_image(96, 80, 0.95, 1),                         # ragged tile: 5 blocks wide
+        synth.ar1_image(16, 16, 0.95, 2),                         # one block
+        synth.ar1_image(32, 272, 0.8, 3, noise_sigma=8.0),        # 17 blocks: tiles of 8, 8, 1
+        rng.integers(0, 256, size=(48, 128)).astype(np.uint8),    # white noise
+        np.zeros((16, 48), np.uint8),
+        np.full((32, 32), 255, np.uint8),
+        (np.indices((32, 144)).sum(axis=0) % 2 * 255).astype(np.uint8),  # checkerboard
+    ]
+    g = np.zeros((64, 64), np.uint8)
+    g[:, ::2] = 255
+    imgs.append(g)
+    return imgs
+
+
+@pytest.mark.parametrize("r", [0, 1, 2, 6, 16, 36, 64, 100, 136, 150, 255, 256])
+def test_zonal_small_images_exact(torch, plan, r):
+    imgs = _small_images()
+    outs, psnr, sse = run_zonal(torch, plan, imgs, [r] * len(imgs))
+    for img, out, p, s in zip(imgs, outs, psnr, sse):
+        check_zonal(img, r, out, p, s)
+
+
+def test_zonal_mixed_r_in_one_call_and_pitch(torch, plan):
+    imgs = _small_images() * 3
+    rs = [int(v) for v in np.random.default_rng(3).choice(R_SWEEP, size=len(imgs))]
+    outs, psnr, sse = run_zonal(torch, plan, imgs, rs, pitch_extra=48)
+    for img, r, out, p, s in zip(imgs, rs, outs, psnr, sse):
+        check_zonal(img, r, out, p, s)
+
+
+def test_zonal_random_sizes(torch, plan):
+    rng = np.random.default_rng(9)
+    sizes = [(16 * int(rng.integers(1, 20)), 16 * int(rng.integers(1, 40))) for _ in range(20)]
+    imgs = [synth.ar1_image(h, w, 0.9, 100 + i) for i, (h, w) in enumerate(sizes)]
+    rs = [int(v) for v in rng.integers(0, 257, size=len(imgs))]
+    outs, psnr, sse = run_zonal(torch, plan, imgs, rs)
+    for img, r, out, p, s in zip(imgs, rs, outs, psnr, sse):
+        check_zonal(img, r, out, p, s)
+
+
+# ------------------------------------------- zonal, full 64 x 512 x 512 ---
+def test_zonal_full_batch_sampled(torch, plan):
+    batch = synth.image_batch_512(64)
+    src = torch.from_numpy(batch).cuda()
+    dst = torch.empty((len(R_SWEEP), 64, 512, 512), dtype=torch.uint8, device="cuda")
+    descs = [atdct16.image(src[i], dst[k, i], r) for k, r in enumerate(R_SWEEP) for i in range(64)]
+    psnr = torch.empty(len(descs), dtype=torch.float64, device="cuda")
+    plan.compress_zonal(descs, psnr)
+    torch.cuda.synchronize()
+    ps = psnr.cpu().numpy().reshape(len(R_SWEEP), 64)
+    # PSNR non-decreasing in r for every image, +inf at r = 256
+    assert np.all(np.diff(ps[:-1], axis=0) >= -1e-9)
+    assert np.all(np.isinf(ps[-1]))
+    assert np.array_equal(dst[-1].cpu().numpy(), batch)
+    # sampled images against the oracle, both halves of the batch
+    for k, r in enumerate(R_SWEEP):
+        for i in (0, 31, 32, 63):
+            ref = O.compress_zonal_exact(batch[i], r)
+            assert np.array_equal(dst[k, i].cpu().numpy(), ref["recon_u8"])
+            if not math.isinf(ref["psnr"]):
+                assert ps[k, i] == pytest.approx(ref["psnr"], rel=PSNR_RTOL)
+
+
+# ---------------------------------------------------------- quantiser ---
+def run_quant(torch, qplan, planes, qps, with_levels=True):
+    srcs = [dev_image(torch, p) for p in planes]
+    dsts = [empty_like_img(torch, p.shape[0], p.shape[1], torch.int16) for p in planes]
+    descs = [atdct16.image(s, d, q) for s, d, q in zip(srcs, dsts, qps)]
+    nlev = sum(p.size for p in planes)
+    levels = torch.empty(nlev, dtype=torch.int16, device="cuda") if with_levels else None
+    psnr = torch.empty(len(planes), dtype=torch.float64, device="cuda")
+    qplan.compress_quant(descs, psnr, levels=levels)
+    torch.cuda.synchronize()
+    return [d.cpu().numpy() for d in dsts], psnr.cpu().numpy(), (levels.cpu().numpy() if with_levels else None)
+
+
+def check_quant_plane(plane, qp, out, psnr, lev):
+    ref = O.compress_quant(plane, qp, precision="fp32")
+    assert np.array_equal(lev, ref["levels"].reshape(-1)), "levels differ"
+    rec = ref["recon"]
+    diff = out.astype(np.int64) - ref["recon_i16"].astype(np.int64)
+    near_tie = np.abs(np.abs(rec - np.floor(rec)) - 0.5) < 2e-3
+    assert np.all(np.abs(diff) <= 1)
+    assert np.all(diff[~near_tie] == 0)
+    assert psnr == pytest.approx(ref["psnr"], rel=PSNR_RTOL)
+
+
+@pytest.mark.parametrize("qp", [0, 22, 27, 32, 37, 51])
+def test_quant_planes(torch, qplan, qp):
+    planes = [synth.laplacian_residual(64, 96, 30 + qp), synth.laplacian_residual(32, 48, 31 + qp),
+              synth.laplacian_residual(16, 272, 32 + qp)]
+    outs, psnr, lev = run_quant(torch, qplan, planes, [qp] * 3)
+    off = 0
+    for plane, out, p in zip(planes, outs, psnr):
+        check_quant_plane(plane, qp, out, p, lev[off:off + plane.size])
+        off += plane.size
+
+
+def test_quant_video_frame_full_size(torch, qplan):
+    (yp, cb, cr), = synth.residual_frames(1)
+    planes = [yp, cb, cr]
+    outs, psnr, lev = run_quant(torch, qplan, planes, [27, 27, 27])
+    off = 0
+    for plane, out, p in zip(planes, outs, psnr):
+        check_quant_plane(plane, 27, out, p, lev[off:off + plane.size])
+        off += plane.size
+
+
+# --------------------------------------------------------------- PSNR ---
+def test_psnr_pair(torch):
+    a = synth.ar1_image(64, 80, 0.9, 1)
+    b = synth.ar1_image(64, 80, 0.9, 2)
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    atdct16.psnr(dev_image(torch, a), dev_image(torch, b, 16), out)
+    torch.cuda.synchronize()
+    assert out.item() == pytest.approx(O.psnr_images(a, b), rel=1e-12)
+    atdct16.psnr(dev_image(torch, a), dev_image(torch, a), out)
+    torch.cuda.synchronize()
+    assert math.isinf(out.item())
+    x = synth.laplacian_residual(32, 48, 1)
+    y = synth.laplacian_residual(32, 48, 2)
+    atdct16.psnr(dev_image(torch, x), dev_image(torch, y), out, dtype=atdct16.I16)
+    torch.cuda.synchronize()
+    assert out.item() == pytest.approx(O.psnr_images(x, y), rel=1e-12)
+
+
+# ------------------------------------------------------- argument checks ---
+def test_invalid_arguments_rejected(torch, plan):
+    img = dev_image(torch, synth.ar1_image(32, 32, 0.9, 1))
+    out = empty_like_img(torch, 32, 32, torch.uint8)
+    psnr = torch.empty(1, dtype=torch.float64, device="cuda")
+    bad = [
+        atdct16.Image(img.data_ptr(), out.data_ptr(), 32, 32, 24, 32, 16, 0),      # width not /16
+        atdct16.Image(img.data_ptr(), out.data_ptr(), 32, 32, 32, 32, 257, 0),     # r > 256
+        atdct16.Image(img.data_ptr() + 1, out.data_ptr(), 32, 32, 32, 32, 16, 0),  # misaligned
+        atdct16.Image(img.data_ptr(), out.data_ptr(), 24, 32, 32, 32, 16, 0),      # pitch < width
+        atdct16.Image(0, out.data_ptr(), 32, 32, 32, 32, 16, 0),                   # null src
+    ]
+    for d in bad:
+        with pytest.raises(atdct16.Atdct16Error) as e:
+            plan.compress_zonal([d], psnr)
+        assert e.value.status == atdct16.EINVAL
+    with pytest.raises(atdct16.Atdct16Error):
+        plan.compress_zonal([], psnr)
+    assert plan.last_device_status() == atdct16.OK
+
+
+def test_in_tree_library_loaded(torch):
+    import os
+    path = atdct16.library_path()
+    assert os.path.dirname(path) == os.path.dirname(os.path.abspath(atdct16.__file__))
+    maps = open("/proc/self/maps").read()
+    assert path in maps
