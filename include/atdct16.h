@@ -146,6 +146,31 @@ atdct16_status atdct16_compress_quant(atdct16_plan_t plan, const atdct16_image* 
                                       int16_t* d_levels, double* d_psnr, double* d_sse,
                                       cudaStream_t stream);
 
+/* Zonal compression that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * while they compress -- programs running on a memory budget fixed at
+ * start-up, latency-critical paths that cannot afford cudaMalloc's implicit
+ * synchronisation, applications whose own allocator owns all device memory.
+ * It computes exactly what atdct16_compress_zonal computes, without a plan.
+ * Besides the caller's images and outputs it uses only a scratch area of
+ * about 1 MiB that is part of the library image itself: every GPU that loads
+ * the library holds it until the process exits.
+ *   n <= ATDCT16_NOALLOC_MAX_IMAGES, and the batch must fit in
+ *   ATDCT16_NOALLOC_MAX_TILES tiles of 16 x 128 pixels (each image takes
+ *   ceil(w/128) * h/16 tiles, e.g. 128 per 512x512 image); larger requests
+ *   return ATDCT16_ENOMEM and launch nothing.  Other argument rules and the
+ *   meaning of d_psnr / d_sse are those of atdct16_compress_zonal.
+ * The first call on each device sets that device up (looks up the scratch
+ * area's device address and fills its weight table on `stream`); make that
+ * first call before any stream capture.  All calls share the scratch area and
+ * it keeps the last call's contents: calls that may overlap on the GPU
+ * (other streams, other host threads) race on it and must be serialised by
+ * the caller. */
+#define ATDCT16_NOALLOC_MAX_IMAGES 64
+#define ATDCT16_NOALLOC_MAX_TILES 131072
+atdct16_status atdct16_compress_zonal_noalloc(const atdct16_image* h_images, int32_t n, double* d_psnr,
+                                              double* d_sse, cudaStream_t stream);
+
 /* PSNR between two images of the same shape (Sec. 4), exact integer SSE.
  * peak 255.  d_out: one device double.  Allocates nothing: the output slot
  * doubles as the accumulator. */

@@ -54,6 +54,7 @@ _SIGS = {
     "atdct16_psnr": (C.c_int, [C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "atdct16_last_device_status": (C.c_int, [C.c_void_p]),
     "atdct16_host_butterfly": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32]),
+    "atdct16_compress_zonal_noalloc": (C.c_int, [C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "atdct16_plan_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "atdct16_plan_profile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
 }
@@ -182,6 +183,14 @@ class Plan:
 
     def last_device_status(self) -> int:
         return lib().atdct16_last_device_status(self._h)
+
+
+def compress_zonal_noalloc(images, psnr, sse=None, stream=None):
+    """Zonal compression through the entry point that allocates nothing (no
+    plan; at most 64 images and 131072 tiles per call)."""
+    arr = (Image * len(images))(*images)
+    _check(lib().atdct16_compress_zonal_noalloc(arr, len(images), _ptr(psnr), _ptr(sse), _stream(stream)),
+           "compress_zonal_noalloc")
 
 
 def psnr(a, b, out, dtype=U8, stream=None):
