@@ -19,7 +19,8 @@
  *   only its own workspace (tables, descriptors, per-tile partial sums).
  * - Images are row-major with a pitch in bytes.  Width and height must be
  *   positive multiples of 16.  Image base pointers and pitches must be
- *   16-byte aligned (the kernels move 16-byte rows of a block).
+ *   16-byte aligned (the kernels move 16-byte rows of a block), and pitches
+ *   of batched images must be below 2^31 bytes.
  * - Block (by, bx) covers rows 16*by..16*by+15 and columns 16*bx..16*bx+15.
  *   Within a block the coefficient index is (u, v), u = vertical frequency
  *   (row of T applied to the block's columns), v = horizontal frequency:

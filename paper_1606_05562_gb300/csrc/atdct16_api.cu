@@ -89,6 +89,7 @@ atdct16_status check_image(const atdct16_image& im, int elem, bool need_dst) {
   if (need_dst && (im.dst_pitch < (int64_t)im.width * elem || (im.dst_pitch & 15))) return ATDCT16_EINVAL;
   if (!aligned16(im.src) || (need_dst && !aligned16(im.dst))) return ATDCT16_EINVAL;
   if (im.reserved != 0) return ATDCT16_EINVAL;
+  if (im.src_pitch >= ((int64_t)1 << 31) || im.dst_pitch >= ((int64_t)1 << 31)) return ATDCT16_EINVAL;
   return ATDCT16_OK;
 }
 
@@ -271,7 +272,7 @@ atdct16_status atdct16_compress_zonal(atdct16_plan_t plan, const atdct16_image* 
   long long ntiles = 0;
   atdct16_status s = stage_jobs(plan, h_images, n, 1, stream, &ntiles, false);
   if (s != ATDCT16_OK) return s;
-  const int grid = (int)std::min<long long>(plan->zonal_grid, (ntiles + kWarpsPerCta - 1) / kWarpsPerCta);
+  const int grid = (int)std::min<long long>(plan->zonal_grid, (ntiles + kZonalWarps - 1) / kZonalWarps);
   const int pk = prof_begin(plan, stream);
   cudaError_t e = launch_zonal(plan->d_jobs, n, ntiles, plan->d_wtab, plan->d_tile_sse, plan->d_status, grid, stream);
   prof_end(plan, pk, stream);

@@ -12,6 +12,7 @@ constexpr int kTileW = 128;
 constexpr int kTileH = 16;
 constexpr int kWarpsPerCta = 8;
 constexpr int kThreadsPerCta = 32 * kWarpsPerCta;
+constexpr int kZonalWarps = 4;  // warps per CTA of the fused zonal kernel
 
 // One image of a batch, as the kernels see it (64 bytes).
 struct ImageJob {
@@ -43,6 +44,13 @@ constexpr int kDevBadJob = 1;
 // Kernel launchers (atdct16_kernels.cu).  All asynchronous on `stream`.
 cudaError_t launch_zonal(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
                          float* d_tile_sse, int* d_status, int grid, cudaStream_t stream);
+// Zonal kernel variants: all-FP32 butterflies (default) or the forward
+// transform in 16-bit SWAR lanes.
+constexpr int kZonalF32 = 0;
+constexpr int kZonalSwar = 1;
+cudaError_t launch_zonal_variant(int variant, const ImageJob* d_jobs, int njobs, long long ntiles,
+                                 const float2* d_wtab, float* d_tile_sse, int* d_status, int grid,
+                                 cudaStream_t stream);
 cudaError_t launch_quant(const ImageJob* d_jobs, int njobs, long long ntiles, const float4* d_qtab,
                          int16_t* d_levels, float* d_tile_sse, int* d_status, int grid,
                          cudaStream_t stream);

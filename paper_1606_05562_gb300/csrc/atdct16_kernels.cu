@@ -139,128 +139,465 @@ __device__ __forceinline__ float warp_sum(float v) {
 // --------------------------------------------------------------------------
 // Fused zonal compression: forward, keep the first r zig-zag coefficients,
 // S^2 scaling, inverse, round, store u8, per-tile SSE (Sec. 4 procedure).
+//
+// Shared memory per warp: the transpose buffer (lines = block columns, slots
+// = row pairs, 16-byte chunks XOR-swizzled by (line >> 1) & 7) and a copy of
+// the weight table of the warp's current r (chunks swizzled the same way).
+// The back-transpose uses the same line-per-column layout, so a lane only
+// overwrites the two lines it alone has read.  The next tile's input rows
+// are loaded while the current tile is computed.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreadsPerCta, 1)
-zonal_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
+struct alignas(16) ZonalWarpSmem {
+  float4 t[4 * 16 * 8];  // 8 KB transpose buffer
+  float4 w[16 * 8];      // 2 KB weights (kw_u, dw_u, kw_u+1, dw_u+1) per column
+};
+
+struct TileRef {
+  const uint8_t* src;  // row 2j of block A of this lane
+  uint8_t* dst;
+  long long t;
+  int src_pitch, dst_pitch;  // bytes (host checks they fit in 31 bits)
+  int r;
+  int nb;
+};
+
+template <int kWarps>
+__global__ void __launch_bounds__(32 * kWarps, 16 / kWarps)
+zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
              const float2* __restrict__ wtab, float* __restrict__ tile_sse, int* __restrict__ status) {
-  __shared__ WarpBuf sbuf[kWarpsPerCta];
+  __shared__ ZonalWarpSmem smem[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int p = lane >> 3, j = lane & 7;
-  float4* buf = sbuf[warp].c;
-  const long long nwarps = (long long)gridDim.x * kWarpsPerCta;
+  float4* buf = smem[warp].t;
+  float4* wsm = smem[warp].w;
+  const long long nwarps = (long long)gridDim.x * kWarps;
 
   int job = -1;
   long long jb = 0, je = 0;
-  ImageJob J;
-  for (long long t = (long long)blockIdx.x * kWarpsPerCta + warp; t < ntiles; t += nwarps) {
+  // Locate tile t: warp-uniform job lookup and this lane's row pointers.  The
+  // descriptor is re-read (it stays in L1) instead of being kept in registers.
+  auto locate = [&](long long t, TileRef& ref) -> bool {
     if (t < jb || t >= je) {
       warp_find_job(jobs, njobs, t, job);
-      J = jobs[job];
-      jb = J.tile_begin;
-      je = jb + (long long)J.tiles_x * (J.height >> 4);
-      if (t < jb || t >= je) {  // descriptor table inconsistent with ntiles
-        if (lane == 0) set_status(status, kDevBadJob);
-        continue;
+      jb = __ldg(&jobs[job].tile_begin);
+      je = jb + (long long)__ldg(&jobs[job].tiles_x) * (__ldg(&jobs[job].height) >> 4);
+      if (t < jb || t >= je) return false;
+    }
+    const ImageJob* J = jobs + job;
+    const int tiles_x = __ldg(&J->tiles_x);
+    const long long lt = t - jb;
+    const int ty = (int)(lt / tiles_x);
+    const int tx = (int)(lt - (long long)ty * tiles_x);
+    const int x0 = tx * kTileW;
+    const long long row = (long long)(ty * kTileH + 2 * j);
+    ref.src_pitch = (int)__ldg(&J->src_pitch);
+    ref.dst_pitch = (int)__ldg(&J->dst_pitch);
+    ref.src = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->src))) +
+              row * ref.src_pitch + x0 + 16 * p;
+    ref.dst = reinterpret_cast<uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->dst))) +
+              row * ref.dst_pitch + x0 + 16 * p;
+    ref.t = t;
+    ref.r = __ldg(&J->param);
+    ref.nb = min(8, (__ldg(&J->width) - x0) >> 4);
+    return true;
+  };
+  auto load = [&](const TileRef& ref, uint4& a0, uint4& a1, uint4& b0, uint4& b1) {
+    a0 = a1 = b0 = b1 = make_uint4(0, 0, 0, 0);
+    if (p < ref.nb) {
+      a0 = __ldcs(reinterpret_cast<const uint4*>(ref.src));
+      a1 = __ldcs(reinterpret_cast<const uint4*>(ref.src + ref.src_pitch));
+    }
+    if (p + 4 < ref.nb) {
+      b0 = __ldcs(reinterpret_cast<const uint4*>(ref.src + 64));
+      b1 = __ldcs(reinterpret_cast<const uint4*>(ref.src + 64 + ref.src_pitch));
+    }
+  };
+
+  // Each warp takes a contiguous range of tiles, so consecutive tiles of a
+  // warp mostly belong to the same image (one descriptor lookup, one weight
+  // refresh per image rather than per tile).
+  const long long per_warp = (ntiles + nwarps - 1) / nwarps;
+  const long long gw = (long long)blockIdx.x * kWarps + warp;
+  const long long t_end = min(ntiles, (gw + 1) * per_warp);
+  long long t = gw * per_warp;
+  TileRef cur;
+  uint4 a0, a1, b0, b1;
+  while (t < t_end && !locate(t, cur)) {
+    if (lane == 0) set_status(status, kDevBadJob);
+    ++t;
+  }
+  if (t >= t_end) return;
+  load(cur, a0, a1, b0, b1);
+  int wr = -1;  // r whose weights are in wsm
+
+  while (true) {
+    // ---- prefetch the next tile
+    long long tn = cur.t + 1;
+    TileRef nxt;
+    bool have_next = false;
+    while (tn < t_end) {
+      if (locate(tn, nxt)) { have_next = true; break; }
+      if (lane == 0) set_status(status, kDevBadJob);
+      ++tn;
+    }
+    uint4 na0, na1, nb0, nb1;
+    if (have_next) load(nxt, na0, na1, nb0, nb1);
+
+    const bool va = p < cur.nb, vb = p + 4 < cur.nb;
+    if (cur.r != wr) {  // warp-uniform: refresh the weight copy
+      __syncwarp();
+      const float4* src = reinterpret_cast<const float4*>(wtab) + (long long)cur.r * 128;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int g = lane * 4 + q, c = g >> 3, h = g & 7;
+        wsm[c * 8 + (h ^ ((c >> 1) & 7))] = __ldg(src + g);
+      }
+      __syncwarp();
+      wr = cur.r;
+    }
+
+    // ---- row pass (Sec. 2 factorisation) on 2^23 + 256 x, one image row at
+    // a time; each row fills one half of its 16-byte chunks
+    {
+      float2* half = reinterpret_cast<float2*>(buf);
+#pragma unroll
+      for (int tr = 0; tr < 2; ++tr) {
+        const uint4& wa = tr ? a1 : a0;
+        const uint4& wb = tr ? b1 : b0;
+        float2 xv[16], rv[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n)
+          xv[n] = make_float2(u8_scaled(word_of(wa, n >> 2), n & 3), u8_scaled(word_of(wb, n >> 2), n & 3));
+        fwd16(xv, rv);
+        // row 0 of T sums all 16 inputs: remove 16 * 2^23 (exact)
+        rv[0] = bsub(rv[0], make_float2(134217728.0f, 134217728.0f));
+#pragma unroll
+        for (int k = 0; k < 16; ++k) half[2 * ((p * 16 + k) * 8 + (j ^ ((k >> 1) & 7))) + tr] = rv[k];
       }
     }
-    const long long lt = t - jb;
-    const int ty = (int)(lt / J.tiles_x);
-    const int tx = (int)(lt - (long long)ty * J.tiles_x);
-    const int x0 = tx * kTileW, y0 = ty * kTileH;
-    const int nb = min(8, (J.width - x0) >> 4);
-    const bool va = p < nb, vb = p + 4 < nb;
+    __syncwarp();
 
-    // ---- load rows 2j, 2j+1 of blocks A and B (16 B each)
-    const uint8_t* s = J.src + (long long)(y0 + 2 * j) * J.src_pitch + x0 + 16 * p;
-    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
-    if (va) {
-      a0 = __ldcs(reinterpret_cast<const uint4*>(s));
-      a1 = __ldcs(reinterpret_cast<const uint4*>(s + J.src_pitch));
-    }
-    if (vb) {
-      b0 = __ldcs(reinterpret_cast<const uint4*>(s + 64));
-      b1 = __ldcs(reinterpret_cast<const uint4*>(s + 64 + J.src_pitch));
-    }
-
-    // ---- row pass (Sec. 2 factorisation) on 2^23 + 256 x
-    float2 x0v[16], x1v[16], r0[16], r1[16];
-#pragma unroll
-    for (int n = 0; n < 16; ++n) {
-      x0v[n] = make_float2(u8_scaled(word_of(a0, n >> 2), n & 3), u8_scaled(word_of(b0, n >> 2), n & 3));
-      x1v[n] = make_float2(u8_scaled(word_of(a1, n >> 2), n & 3), u8_scaled(word_of(b1, n >> 2), n & 3));
-    }
-    fwd16(x0v, r0);
-    fwd16(x1v, r1);
-    // row 0 of T sums all 16 inputs: remove 16 * 2^23 (exact)
-    r0[0] = bsub(r0[0], make_float2(134217728.0f, 134217728.0f));
-    r1[0] = bsub(r1[0], make_float2(134217728.0f, 134217728.0f));
-
-    // ---- transpose, column pass: y = 256 Y (exact)
-    float2 c0[16], c1[16];
-    transpose_rows_to_cols(buf, p, j, r0, r1, c0, c1);
-    float2 ya[16], yb[16];
-    fwd16(c0, ya);
-    fwd16(c1, yb);
-
-    // ---- zonal mask and S^2 weights; dropped energy (Parseval) for the SSE
-    const float4* w0 = reinterpret_cast<const float4*>(wtab + ((long long)J.param * 16 + 2 * j) * 16);
-    const float4* w1 = w0 + 8;
+    // ---- per column c = 2j + i: column pass (y = 256 Y, exact), zonal mask
+    // and S^2 weights, dropped energy (Parseval), inverse column pass; the
+    // result goes back into the same line of the buffer.
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int h = 0; h < 8; ++h) {
-      const float4 wa = __ldg(w0 + h);
-      const float4 wb = __ldg(w1 + h);
-      acc = __ffma2_rn(f2mul(ya[2 * h], wa.y), ya[2 * h], acc);
-      acc = __ffma2_rn(f2mul(ya[2 * h + 1], wa.w), ya[2 * h + 1], acc);
-      acc = __ffma2_rn(f2mul(yb[2 * h], wb.y), yb[2 * h], acc);
-      acc = __ffma2_rn(f2mul(yb[2 * h + 1], wb.w), yb[2 * h + 1], acc);
-      ya[2 * h] = f2mul(ya[2 * h], wa.x);
-      ya[2 * h + 1] = f2mul(ya[2 * h + 1], wa.z);
-      yb[2 * h] = f2mul(yb[2 * h], wb.x);
-      yb[2 * h + 1] = f2mul(yb[2 * h + 1], wb.z);
-    }
-
-    // ---- inverse: column pass, transpose back, row pass -> exact Z
-    float2 u0[16], u1[16];
-    inv16(ya, u0);
-    inv16(yb, u1);
-    float2 v0[16], v1[16];
-    transpose_cols_to_rows(buf, p, j, u0, u1, v0, v1);
-    float2 z0[16], z1[16];
-    inv16(v0, z0);
-    inv16(v1, z1);
-
-    // ---- round half to even, clamp, pack, store
-    uint4 oa0, oa1, ob0, ob1;
-    unsigned qa0[16], qa1[16], qb0[16], qb1[16];
+    for (int i = 0; i < 2; ++i) {
+      const int line = p * 16 + 2 * j + i;
+      float2 cv[16], y[16];
 #pragma unroll
-    for (int n = 0; n < 16; ++n) {
-      const float2 e0 = rne_denormal(f2mul(z0[n], kInv2304));
-      const float2 e1 = rne_denormal(f2mul(z1[n], kInv2304));
-      qa0[n] = __float_as_uint(e0.x);
-      qb0[n] = __float_as_uint(e0.y);
-      qa1[n] = __float_as_uint(e1.x);
-      qb1[n] = __float_as_uint(e1.y);
+      for (int q = 0; q < 8; ++q) {
+        const float4 v = buf[line * 8 + (q ^ j)];
+        cv[2 * q] = make_float2(v.x, v.y);
+        cv[2 * q + 1] = make_float2(v.z, v.w);
+      }
+      fwd16(cv, y);
+      const int wc = (2 * j + i) * 8;
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        const float4 w = wsm[wc + (h ^ j)];
+        acc = __ffma2_rn(f2mul(y[2 * h], w.y), y[2 * h], acc);
+        acc = __ffma2_rn(f2mul(y[2 * h + 1], w.w), y[2 * h + 1], acc);
+        y[2 * h] = f2mul(y[2 * h], w.x);
+        y[2 * h + 1] = f2mul(y[2 * h + 1], w.z);
+      }
+      float2 uo[16];
+      inv16(y, uo);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        buf[line * 8 + (q ^ j)] = make_float4(uo[2 * q].x, uo[2 * q].y, uo[2 * q + 1].x, uo[2 * q + 1].y);
     }
-#define ATDCT16_PACK4(q, i) pack_u8(q[4 * (i) + 1], q[4 * (i)], pack_u8(q[4 * (i) + 3], q[4 * (i) + 2], 0u))
-    oa0 = make_uint4(ATDCT16_PACK4(qa0, 0), ATDCT16_PACK4(qa0, 1), ATDCT16_PACK4(qa0, 2), ATDCT16_PACK4(qa0, 3));
-    oa1 = make_uint4(ATDCT16_PACK4(qa1, 0), ATDCT16_PACK4(qa1, 1), ATDCT16_PACK4(qa1, 2), ATDCT16_PACK4(qa1, 3));
-    ob0 = make_uint4(ATDCT16_PACK4(qb0, 0), ATDCT16_PACK4(qb0, 1), ATDCT16_PACK4(qb0, 2), ATDCT16_PACK4(qb0, 3));
-    ob1 = make_uint4(ATDCT16_PACK4(qb1, 0), ATDCT16_PACK4(qb1, 1), ATDCT16_PACK4(qb1, 2), ATDCT16_PACK4(qb1, 3));
-#undef ATDCT16_PACK4
-    uint8_t* d = J.dst + (long long)(y0 + 2 * j) * J.dst_pitch + x0 + 16 * p;
-    if (va) {
-      __stcs(reinterpret_cast<uint4*>(d), oa0);
-      __stcs(reinterpret_cast<uint4*>(d + J.dst_pitch), oa1);
-    }
-    if (vb) {
-      __stcs(reinterpret_cast<uint4*>(d + 64), ob0);
-      __stcs(reinterpret_cast<uint4*>(d + 64 + J.dst_pitch), ob1);
+    __syncwarp();
+
+    // ---- per row 2j + t: gather the row, inverse row pass -> exact Z,
+    // round half to even, clamp, pack, store
+#pragma unroll
+    for (int tr = 0; tr < 2; ++tr) {
+      float2 v[16], z[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const float4 q4 = buf[(p * 16 + c) * 8 + (j ^ ((c >> 1) & 7))];
+        v[c] = tr ? make_float2(q4.z, q4.w) : make_float2(q4.x, q4.y);
+      }
+      inv16(v, z);
+      unsigned oa[4], ob[4];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        unsigned qa[4], qb[4];
+#pragma unroll
+        for (int e4 = 0; e4 < 4; ++e4) {
+          const float2 e = rne_denormal(f2mul(z[4 * g + e4], kInv2304));
+          qa[e4] = __float_as_uint(e.x);
+          qb[e4] = __float_as_uint(e.y);
+        }
+        oa[g] = pack_u8(qa[1], qa[0], pack_u8(qa[3], qa[2], 0u));
+        ob[g] = pack_u8(qb[1], qb[0], pack_u8(qb[3], qb[2], 0u));
+      }
+      uint8_t* d = cur.dst + tr * cur.dst_pitch;
+      if (va) __stcs(reinterpret_cast<uint4*>(d), make_uint4(oa[0], oa[1], oa[2], oa[3]));
+      if (vb) __stcs(reinterpret_cast<uint4*>(d + 64), make_uint4(ob[0], ob[1], ob[2], ob[3]));
     }
 
     // ---- tile SSE: dropped energy / (256 * 2304), summed over valid blocks
     const float tot = warp_sum((va ? acc.x : 0.f) + (vb ? acc.y : 0.f));
-    if (lane == 0) tile_sse[t] = tot * (1.0f / (256.0f * 2304.0f));
+    if (lane == 0) tile_sse[cur.t] = tot * (1.0f / (256.0f * 2304.0f));
+    __syncwarp();  // buffer reads done before the next tile's writes
+
+    if (!have_next) break;
+    cur = nxt;
+    a0 = na0; a1 = na1; b0 = nb0; b1 = nb1;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Fused zonal compression with the forward transform in 16-bit SWAR lanes.
+//
+// The forward transform is exact integer work whose every node fits int16
+// once the DC column is centred (row-pass outputs of T's all-ones row minus
+// 2048): it runs on two blocks per 32-bit register (offset-binary lanes, one
+// 3-input integer add per butterfly addition) on the integer pipe, leaving
+// the FP32 pipe to the inverse.  Conversion to FP32 happens once per
+// coefficient, fused with the zonal mask and the row weight W_u:
+//   word -> (mask ? word : bias) -> two magic floats 2^23 + 32768 + Y
+//   -> D = f W_u - (2^23 + 32768) W_u   (one f32x2 FMA, exact).
+// The column weight W_c is applied in the inverse row stage, where c is a
+// compile-time index.  SSE is accumulated from e = Z - 2304 x with the input
+// rows re-read (they are still in L1/L2).
+//
+// Shared memory per warp (13 KB): T1 (SWAR words, 4 KB), T2 (float2 pairs,
+// 8 KB) and the keep-masks of the warp's current r (1 KB), each with a
+// 16-byte-chunk XOR swizzle that is conflict-free for its writers and readers.
+// Lanes with odd p handle their two rows in the opposite order, so their
+// 8-byte reads of T2 fall in the other half of each chunk.
+// --------------------------------------------------------------------------
+constexpr int kSwarWarpSmem = 4096 + 8192 + 1024;
+
+// W = 48 S^2 for rows 0..15 of T (S printed in Sec. 2: 1/4, 1/sqrt(12), 1/sqrt(8))
+__host__ __device__ constexpr float w48(int i) {
+  return (i == 0 || i == 1 || i == 5 || i == 8) ? 3.f : ((i == 3 || i == 4 || i == 11 || i == 12) ? 6.f : 4.f);
+}
+
+__device__ __forceinline__ unsigned lop_select(unsigned w, unsigned m, unsigned other) {
+  return (w & m) | (~m & other);
+}
+
+template <int kWarps>
+__global__ void __launch_bounds__(32 * kWarps, 16 / kWarps)
+zonal_swar_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
+                  const float2* __restrict__ wtab, float* __restrict__ tile_sse, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char dsmem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = lane >> 3, j = lane & 7, po = p & 1;
+  unsigned char* wbase = dsmem + warp * kSwarWarpSmem;
+  uint4* t1 = reinterpret_cast<uint4*>(wbase);            // 256 chunks
+  float4* t2 = reinterpret_cast<float4*>(wbase + 4096);   // 512 chunks
+  uint4* msk = reinterpret_cast<uint4*>(wbase + 12288);   // 64 chunks
+  const long long nwarps = (long long)gridDim.x * kWarps;
+
+  int job = -1;
+  long long jb = 0, je = 0;
+  auto locate = [&](long long t, TileRef& ref) -> bool {
+    if (t < jb || t >= je) {
+      warp_find_job(jobs, njobs, t, job);
+      jb = __ldg(&jobs[job].tile_begin);
+      je = jb + (long long)__ldg(&jobs[job].tiles_x) * (__ldg(&jobs[job].height) >> 4);
+      if (t < jb || t >= je) return false;
+    }
+    const ImageJob* J = jobs + job;
+    const int tiles_x = __ldg(&J->tiles_x);
+    const long long lt = t - jb;
+    const int ty = (int)(lt / tiles_x);
+    const int tx = (int)(lt - (long long)ty * tiles_x);
+    const int x0 = tx * kTileW;
+    const long long row = (long long)(ty * kTileH + 2 * j);
+    ref.src_pitch = (int)__ldg(&J->src_pitch);
+    ref.dst_pitch = (int)__ldg(&J->dst_pitch);
+    ref.src = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->src))) +
+              row * ref.src_pitch + x0 + 16 * p;
+    ref.dst = reinterpret_cast<uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->dst))) +
+              row * ref.dst_pitch + x0 + 16 * p;
+    ref.t = t;
+    ref.r = __ldg(&J->param);
+    ref.nb = min(8, (__ldg(&J->width) - x0) >> 4);
+    return true;
+  };
+  auto load = [&](const TileRef& ref, uint4& a0, uint4& a1, uint4& b0, uint4& b1) {
+    a0 = a1 = b0 = b1 = make_uint4(0, 0, 0, 0);
+    if (p < ref.nb) {
+      a0 = __ldg(reinterpret_cast<const uint4*>(ref.src));
+      a1 = __ldg(reinterpret_cast<const uint4*>(ref.src + ref.src_pitch));
+    }
+    if (p + 4 < ref.nb) {
+      b0 = __ldg(reinterpret_cast<const uint4*>(ref.src + 64));
+      b1 = __ldg(reinterpret_cast<const uint4*>(ref.src + 64 + ref.src_pitch));
+    }
+  };
+
+  const long long per_warp = (ntiles + nwarps - 1) / nwarps;
+  const long long gw = (long long)blockIdx.x * kWarps + warp;
+  const long long t_end = min(ntiles, (gw + 1) * per_warp);
+  long long t = gw * per_warp;
+  TileRef cur;
+  uint4 a0, a1, b0, b1;
+  while (t < t_end && !locate(t, cur)) {
+    if (lane == 0) set_status(status, kDevBadJob);
+    ++t;
+  }
+  if (t >= t_end) return;
+  load(cur, a0, a1, b0, b1);
+  int mr = -1;  // r whose keep-masks are in msk
+
+  while (true) {
+    long long tn = cur.t + 1;
+    TileRef nxt;
+    bool have_next = false;
+    while (tn < t_end) {
+      if (locate(tn, nxt)) { have_next = true; break; }
+      if (lane == 0) set_status(status, kDevBadJob);
+      ++tn;
+    }
+    uint4 na0, na1, nb0, nb1;
+    if (have_next) load(nxt, na0, na1, nb0, nb1);
+
+    const bool va = p < cur.nb, vb = p + 4 < cur.nb;
+    if (cur.r != mr) {  // warp-uniform: rebuild the keep-mask words of this r
+      __syncwarp();
+      const float4* wr4 = reinterpret_cast<const float4*>(wtab) + (long long)cur.r * 128;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e0 = lane * 8 + 4 * h;  // coefficients e0..e0+3: c = e0 >> 4, u = e0 & 15
+        const float4 k01 = __ldg(wr4 + (e0 >> 1));
+        const float4 k23 = __ldg(wr4 + (e0 >> 1) + 1);
+        const int c = e0 >> 4, q = (e0 & 15) >> 2;
+        msk[(c >> 1) * 8 + (((c & 1) * 4 + q) ^ (c >> 1))] =
+            make_uint4(k01.x != 0.f ? ~0u : 0u, k01.z != 0.f ? ~0u : 0u, k23.x != 0.f ? ~0u : 0u, k23.z != 0.f ? ~0u : 0u);
+      }
+      __syncwarp();
+      mr = cur.r;
+    }
+
+    // ---- row pass in SWAR lanes (A, B) for rows 2j, 2j+1; DC centring
+    {
+      Swar16 x0v[16], x1v[16], r0[16], r1[16];
+#pragma unroll
+      for (int k = 0; k < 16; k += 2) {
+        const int wi = k >> 2, bi = k & 3;
+        const unsigned sel0 = (unsigned)(bi | ((bi + 1) << 4) | ((4 + bi) << 8) | ((5 + bi) << 12));
+        const unsigned t0 = __byte_perm(word_of(a0, wi), word_of(b0, wi), sel0);
+        const unsigned t1w = __byte_perm(word_of(a1, wi), word_of(b1, wi), sel0);
+        const unsigned sel1 = (unsigned)((bi + 1) | (bi << 4) | ((5 + bi) << 8) | ((4 + bi) << 12));
+        const unsigned u0 = __byte_perm(word_of(a0, wi), word_of(b0, wi), sel1);
+        const unsigned u1 = __byte_perm(word_of(a1, wi), word_of(b1, wi), sel1);
+        x0v[k].v = lop_select(t0, 0x00FF00FFu, kSwarBias);
+        x1v[k].v = lop_select(t1w, 0x00FF00FFu, kSwarBias);
+        x0v[k + 1].v = lop_select(u0, 0x00FF00FFu, kSwarBias);
+        x1v[k + 1].v = lop_select(u1, 0x00FF00FFu, kSwarBias);
+      }
+      fwd16(x0v, r0);
+      fwd16(x1v, r1);
+      r0[0].v -= 0x08000800u;  // centre the DC column: R[m][0] - 2048 in both lanes
+      r1[0].v -= 0x08000800u;
+      uint2* t1h = reinterpret_cast<uint2*>(t1);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int chunk = ((p >> 1) * 16 + k) * 8 + (((j >> 1) + 4 * po) ^ ((k >> 1) & 7));
+        t1h[2 * chunk + (j & 1)] = make_uint2(r0[k].v, r1[k].v);
+      }
+    }
+    __syncwarp();
+
+    // ---- per column c = 2j + i: SWAR column pass, mask + W_u + FP32
+    // conversion, FP32 inverse column pass, into T2 line c
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int c = 2 * j + i;
+      Swar16 cv[16], y[16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint4 v = t1[((p >> 1) * 16 + c) * 8 + ((q + 4 * po) ^ j)];
+        cv[4 * q].v = v.x;
+        cv[4 * q + 1].v = v.y;
+        cv[4 * q + 2].v = v.z;
+        cv[4 * q + 3].v = v.w;
+      }
+      fwd16(cv, y);
+      // Y[0][0] came out of the centred DC column 32768 low: its lane value
+      // already equals Y + 0, so it converts with offset 2^23 instead.
+      const float k00 = (c == 0) ? -8388608.0f * w48(0) : -8421376.0f * w48(0);
+      const unsigned zero00 = (c == 0) ? 0u : kSwarBias;  // word that converts to 0
+      float2 d[16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint4 m4 = msk[j * 8 + ((i * 4 + q) ^ j)];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int u = 4 * q + e;
+          const unsigned mw = e == 0 ? m4.x : (e == 1 ? m4.y : (e == 2 ? m4.z : m4.w));
+          const unsigned w = lop_select(y[u].v, mw, u == 0 ? zero00 : kSwarBias);
+          const float flo = __uint_as_float((w & 0xFFFFu) | 0x4B000000u);
+          const float fhi = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7432u));
+          const float wu = w48(u);
+          const float kk = u == 0 ? k00 : -8421376.0f * wu;  // -(2^23 + 32768) W_u
+          d[u] = __ffma2_rn(make_float2(flo, fhi), make_float2(wu, wu), make_float2(kk, kk));
+        }
+      }
+      float2 uo[16];
+      inv16(d, uo);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        t2[(p * 16 + c) * 8 + (q ^ j)] = make_float4(uo[2 * q].x, uo[2 * q].y, uo[2 * q + 1].x, uo[2 * q + 1].y);
+    }
+    __syncwarp();
+
+    // ---- per row ar (odd p: rows in reverse order): W_c, inverse row pass,
+    // round half to even, clamp, pack, store; SSE from Z - 2304 x
+    float2 acc = make_float2(0.f, 0.f);
+    const float2* t2h = reinterpret_cast<const float2*>(t2);
+#pragma unroll
+    for (int tr = 0; tr < 2; ++tr) {
+      const int h = tr ^ po;  // row 2j + h
+      float2 v[16], z[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const float wc = w48(c);
+        v[c] = f2mul(t2h[2 * ((p * 16 + c) * 8 + (j ^ ((c >> 1) & 7))) + h], wc);
+      }
+      inv16(v, z);
+      const uint8_t* srow = cur.src + h * cur.src_pitch;
+      const uint4 xa = va ? __ldg(reinterpret_cast<const uint4*>(srow)) : make_uint4(0, 0, 0, 0);
+      const uint4 xb = vb ? __ldg(reinterpret_cast<const uint4*>(srow + 64)) : make_uint4(0, 0, 0, 0);
+      unsigned oa[4], ob[4];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        unsigned qa[4], qb[4];
+        const unsigned wxa = word_of(xa, g), wxb = word_of(xb, g);
+#pragma unroll
+        for (int e4 = 0; e4 < 4; ++e4) {
+          const float2 zz = z[4 * g + e4];
+          const float2 e = rne_denormal(f2mul(zz, kInv2304));
+          qa[e4] = __float_as_uint(e.x);
+          qb[e4] = __float_as_uint(e.y);
+          const float2 xf = make_float2(__uint2float_rn((wxa >> (8 * e4)) & 0xFFu),
+                                        __uint2float_rn((wxb >> (8 * e4)) & 0xFFu));
+          const float2 err = __ffma2_rn(xf, make_float2(-2304.f, -2304.f), zz);
+          acc = __ffma2_rn(err, err, acc);
+        }
+        oa[g] = pack_u8(qa[1], qa[0], pack_u8(qa[3], qa[2], 0u));
+        ob[g] = pack_u8(qb[1], qb[0], pack_u8(qb[3], qb[2], 0u));
+      }
+      uint8_t* dd = cur.dst + h * cur.dst_pitch;
+      if (va) __stcs(reinterpret_cast<uint4*>(dd), make_uint4(oa[0], oa[1], oa[2], oa[3]));
+      if (vb) __stcs(reinterpret_cast<uint4*>(dd + 64), make_uint4(ob[0], ob[1], ob[2], ob[3]));
+    }
+
+    // ---- tile SSE: sum of e^2 / 2304^2 over valid blocks
+    const float tot = warp_sum((va ? acc.x : 0.f) + (vb ? acc.y : 0.f));
+    if (lane == 0) tile_sse[cur.t] = tot * (1.0f / (2304.0f * 2304.0f));
+    __syncwarp();
+
+    if (!have_next) break;
+    cur = nxt;
+    a0 = na0; a1 = na1; b0 = nb0; b1 = nb1;
   }
 }
 
@@ -596,11 +933,27 @@ __global__ void psnr_pair_finish(unsigned long long* slot, double npx, double pe
 // --------------------------------------------------------------------------
 // Launchers
 // --------------------------------------------------------------------------
+cudaError_t launch_zonal_variant(int variant, const ImageJob* d_jobs, int njobs, long long ntiles,
+                                 const float2* d_wtab, float* d_tile_sse, int* d_status, int grid,
+                                 cudaStream_t stream) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (variant == kZonalSwar) {
+    // dynamic shared memory above 48 KB must be enabled per device
+    cudaError_t e = cudaFuncSetAttribute(zonal_swar_kernel<kZonalWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSwarWarpSmem * kZonalWarps);
+    if (e != cudaSuccess) return e;
+    zonal_swar_kernel<kZonalWarps><<<grid, 32 * kZonalWarps, kSwarWarpSmem * kZonalWarps, stream>>>(
+        d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
+  } else {
+    zonal_f32_kernel<kZonalWarps><<<grid, 32 * kZonalWarps, 0, stream>>>(d_jobs, njobs, ntiles, d_wtab, d_tile_sse,
+                                                                         d_status);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_zonal(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
                          float* d_tile_sse, int* d_status, int grid, cudaStream_t stream) {
-  if (ntiles <= 0) return cudaSuccess;
-  zonal_kernel<<<grid, kThreadsPerCta, 0, stream>>>(d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
-  return cudaGetLastError();
+  return launch_zonal_variant(kZonalF32, d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, grid, stream);
 }
 
 cudaError_t launch_quant(const ImageJob* d_jobs, int njobs, long long ntiles, const float4* d_qtab,
@@ -663,7 +1016,10 @@ cudaError_t launch_psnr_pair(int dtype, const void* d_a, long long pitch_a, cons
 
 int zonal_ctas_per_sm() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_kernel, kThreadsPerCta, 0) != cudaSuccess || n < 1) n = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_f32_kernel<kZonalWarps>, 32 * kZonalWarps, 0) !=
+          cudaSuccess ||
+      n < 1)
+    n = 1;
   return n;
 }
 int quant_ctas_per_sm() {

@@ -135,7 +135,8 @@ extern "C" atdct16_status atdct16_compress_zonal_noalloc(const atdct16_image* h_
     if (!im.src || !im.dst || im.width <= 0 || im.height <= 0 || (im.width & 15) || (im.height & 15) ||
         im.src_pitch < im.width || im.dst_pitch < im.width || (im.src_pitch & 15) || (im.dst_pitch & 15) ||
         (reinterpret_cast<uintptr_t>(im.src) & 15) || (reinterpret_cast<uintptr_t>(im.dst) & 15) ||
-        im.reserved != 0 || im.r_or_qp < 0 || im.r_or_qp > 256)
+        im.reserved != 0 || im.r_or_qp < 0 || im.r_or_qp > 256 || im.src_pitch >= ((int64_t)1 << 31) ||
+        im.dst_pitch >= ((int64_t)1 << 31))
       return ATDCT16_EINVAL;
     ImageJob& J = pack.jobs[i];
     J.src = static_cast<const uint8_t*>(im.src);
@@ -161,7 +162,7 @@ extern "C" atdct16_status atdct16_compress_zonal_noalloc(const atdct16_image* h_
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return ATDCT16_ECUDA;
   const ImageJob* jobs = reinterpret_cast<const ImageJob*>(p + kOffJobs);
-  const int grid = (int)std::min<long long>(s->grid, (tiles + kWarpsPerCta - 1) / kWarpsPerCta);
+  const int grid = (int)std::min<long long>(s->grid, (tiles + kZonalWarps - 1) / kZonalWarps);
   e = launch_zonal(jobs, n, tiles, reinterpret_cast<const float2*>(p + kOffWtab),
                    reinterpret_cast<float*>(p + kOffTiles), reinterpret_cast<int*>(p + kOffStatus), grid, stream);
   if (e == cudaSuccess)

@@ -17,6 +17,18 @@ ATDCT16_OPS_HD int bsub(int a, int b) { return a - b; }
 ATDCT16_OPS_HD long long badd(long long a, long long b) { return a + b; }
 ATDCT16_OPS_HD long long bsub(long long a, long long b) { return a - b; }
 
+// Two exact int16 lanes in one 32-bit word, offset-binary: each 16-bit field
+// holds value + 32768, so the word for lanes (lo, hi) is
+// (lo + 32768) + 65536 (hi + 32768).  One 32-bit add of three operands adds
+// or subtracts both lanes and re-biases them; no carry crosses lanes while
+// every true lane value stays in [-32768, 32767].
+struct Swar16 {
+  unsigned v;
+};
+constexpr unsigned kSwarBias = 0x80008000u;
+ATDCT16_OPS_HD Swar16 badd(Swar16 a, Swar16 b) { return Swar16{a.v + b.v - kSwarBias}; }
+ATDCT16_OPS_HD Swar16 bsub(Swar16 a, Swar16 b) { return Swar16{a.v - b.v + kSwarBias}; }
+
 #ifdef __CUDACC__
 __device__ __forceinline__ unsigned long long f2_bits(float2 v) {
   return (unsigned long long)__float_as_uint(v.x) | ((unsigned long long)__float_as_uint(v.y) << 32);

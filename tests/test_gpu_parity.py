@@ -17,7 +17,10 @@ from paper_1606_05562_gb300 import atdct16, build, synth
 
 pytestmark = pytest.mark.gpu
 
+# FP32 results within 1e-5 of FP64: relative for PSNR, with a 1e-5 dB floor
+# where the PSNR itself is 0 dB (SSE equal to the signal energy).
 PSNR_RTOL = 1e-5
+PSNR_ATOL = 1e-5
 R_SWEEP = synth.ZONAL_R_SWEEP
 
 
@@ -80,7 +83,7 @@ def check_zonal(img, r, out, psnr, sse):
     if math.isinf(ref["psnr"]):
         assert math.isinf(psnr) and sse == 0.0
     else:
-        assert psnr == pytest.approx(ref["psnr"], rel=PSNR_RTOL)
+        assert psnr == pytest.approx(ref["psnr"], rel=PSNR_RTOL, abs=PSNR_ATOL)
         assert sse == pytest.approx(ref["sse"], rel=1e-4, abs=1e-3)
 
 
@@ -198,7 +201,7 @@ def test_zonal_full_batch_sampled(torch, plan):
             ref = O.compress_zonal_exact(batch[i], r)
             assert np.array_equal(dst[k, i].cpu().numpy(), ref["recon_u8"])
             if not math.isinf(ref["psnr"]):
-                assert ps[k, i] == pytest.approx(ref["psnr"], rel=PSNR_RTOL)
+                assert ps[k, i] == pytest.approx(ref["psnr"], rel=PSNR_RTOL, abs=PSNR_ATOL)
 
 
 # ---------------------------------------------------------- quantiser ---
@@ -222,7 +225,7 @@ def check_quant_plane(plane, qp, out, psnr, lev):
     near_tie = np.abs(np.abs(rec - np.floor(rec)) - 0.5) < 2e-3
     assert np.all(np.abs(diff) <= 1)
     assert np.all(diff[~near_tie] == 0)
-    assert psnr == pytest.approx(ref["psnr"], rel=PSNR_RTOL)
+    assert psnr == pytest.approx(ref["psnr"], rel=PSNR_RTOL, abs=PSNR_ATOL)
 
 
 @pytest.mark.parametrize("qp", [0, 22, 27, 32, 37, 51])
