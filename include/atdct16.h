@@ -179,6 +179,86 @@ atdct16_status atdct16_psnr(atdct16_dtype dtype, const void* d_a, int64_t pitch_
                             int64_t pitch_b, int32_t w, int32_t h, double* d_out,
                             cudaStream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Resident mixed-size batches (a fixed set of images compressed repeatedly).
+ * atdct16_batch_create uploads the descriptors once, sizes the batch's own
+ * per-tile partials, optionally autotunes the launch shape of the fused
+ * zonal kernel on the batch itself (kernel variant, warps per CTA, prefetch
+ * depth and CTAs per SM, i.e. tiles per CTA), and optionally captures the
+ * fused kernel and the PSNR finalize into one CUDA graph.  Each
+ * atdct16_batch_launch then re-runs the whole batch (Sec. 4 procedure on
+ * every image) with one graph launch.
+ * --------------------------------------------------------------------------- */
+#define ATDCT16_BATCH_AUTOTUNE 1u /* time the candidate launch shapes, keep the fastest */
+#define ATDCT16_BATCH_GRAPH 2u    /* capture the launches into a CUDA graph */
+
+/* h_images: n zonal descriptors (device src/dst, r in 0..256).  d_psnr /
+ * d_sse: caller-owned device outputs (d_sse may be NULL), written by every
+ * launch.  Creation allocates the batch's device memory, copies the
+ * descriptors synchronously and, with ATDCT16_BATCH_AUTOTUNE, runs the batch
+ * several times on `stream` (so dst must not overlap any src: EINVAL).  The
+ * tuning result is cached per (GPU, batch shape) in the plan; when the
+ * environment variable ATDCT16_TUNE_CACHE names a file, results are also
+ * read from and appended to it (one JSON object per line). */
+atdct16_status atdct16_batch_create(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n,
+                                    double* d_psnr, double* d_sse, uint32_t flags, cudaStream_t stream,
+                                    atdct16_batch_t* batch);
+/* Re-run the batch on `stream` (asynchronous). */
+atdct16_status atdct16_batch_launch(atdct16_batch_t batch, cudaStream_t stream);
+/* Chosen launch shape: variant (0 FP32, 1 SWAR), warps per CTA, prefetch,
+ * grid size, tile count and the tuned time per launch in ms (0 if untuned).
+ * Any pointer may be NULL. */
+atdct16_status atdct16_batch_info(atdct16_batch_t batch, int32_t* variant, int32_t* warps, int32_t* prefetch,
+                                  int32_t* grid, int64_t* tiles, float* tuned_ms);
+/* Waits for the batch's last launch stream, then frees it. */
+atdct16_status atdct16_batch_destroy(atdct16_batch_t batch);
+
+/* ---------------------------------------------------------------------------
+ * Continuous-batching compression server (zonal path).  A scheduler thread
+ * admits submitted requests in arrival order as soon as their buffers fit in
+ * a device arena of memory_budget_bytes (allocated once at creation), uploads
+ * them while earlier batches compute, puts every uploaded request into the
+ * next fused-kernel launch on a free compute slot (up to max_batch requests
+ * per launch; slots run concurrently), downloads the reconstruction and the
+ * PSNR, and frees the buffers.  A request's result does not depend on the
+ * batch it rode in.
+ * --------------------------------------------------------------------------- */
+typedef struct atdct16_server_st* atdct16_server_t;
+typedef struct {
+  size_t memory_budget_bytes; /* device arena for request buffers (2 bytes per pixel) */
+  int32_t max_batch;          /* requests per launch, >= 1 */
+  int32_t compute_slots;      /* launches that may be in flight at once, 1..16 */
+  int32_t reserved;           /* 0 */
+} atdct16_server_config;
+/* One compression request: uint8 image in host memory (pinned memory makes
+ * the copies asynchronous), reconstruction written to h_dst; r in 0..256. */
+typedef struct {
+  const void* h_src;
+  void* h_dst;
+  int64_t src_pitch; /* bytes */
+  int64_t dst_pitch; /* bytes */
+  int32_t width;     /* multiple of 16 */
+  int32_t height;    /* multiple of 16 */
+  int32_t r;
+  int32_t reserved; /* 0 */
+} atdct16_request;
+
+atdct16_status atdct16_server_create(const atdct16_server_config* cfg, atdct16_server_t* server);
+/* Queue a request (never blocks).  The host buffers must stay valid until the
+ * request completes.  ATDCT16_ENOMEM if it can never fit in the arena. */
+atdct16_status atdct16_server_submit(atdct16_server_t server, const atdct16_request* req, uint64_t* ticket);
+/* Wait for a request (timeout_us < 0: no limit; ATDCT16_ETIMEOUT when it
+ * expires).  On completion returns its PSNR (Sec. 4) and its latency from
+ * submission to completion in seconds, and forgets the ticket. */
+atdct16_status atdct16_server_wait(atdct16_server_t server, uint64_t ticket, double* psnr, double* latency_s,
+                                   int64_t timeout_us);
+/* Completed requests, kernel launches, pixels completed, seconds from the
+ * first submission to the last completion, arena bytes in use. */
+atdct16_status atdct16_server_stats(atdct16_server_t server, uint64_t* completed, uint64_t* launches,
+                                    double* pixels, double* busy_s, size_t* arena_used);
+/* Stops the scheduler after the work in flight, frees everything. */
+atdct16_status atdct16_server_destroy(atdct16_server_t server);
+
 /* Sticky device-side status of the plan (ATDCT16_OK unless a kernel's own
  * checks rejected a descriptor).  Synchronises the plan's last stream. */
 atdct16_status atdct16_last_device_status(atdct16_plan_t plan);

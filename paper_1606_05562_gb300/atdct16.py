@@ -39,6 +39,32 @@ class Image(C.Structure):
     ]
 
 
+class ServerConfig(C.Structure):
+    """Mirror of ``atdct16_server_config``."""
+
+    _fields_ = [
+        ("memory_budget_bytes", C.c_size_t),
+        ("max_batch", C.c_int32),
+        ("compute_slots", C.c_int32),
+        ("reserved", C.c_int32),
+    ]
+
+
+class Request(C.Structure):
+    """Mirror of ``atdct16_request``."""
+
+    _fields_ = [
+        ("h_src", C.c_void_p),
+        ("h_dst", C.c_void_p),
+        ("src_pitch", C.c_int64),
+        ("dst_pitch", C.c_int64),
+        ("width", C.c_int32),
+        ("height", C.c_int32),
+        ("r", C.c_int32),
+        ("reserved", C.c_int32),
+    ]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -55,6 +81,19 @@ _SIGS = {
     "atdct16_last_device_status": (C.c_int, [C.c_void_p]),
     "atdct16_host_butterfly": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32]),
     "atdct16_compress_zonal_noalloc": (C.c_int, [C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "atdct16_batch_create": (C.c_int, [C.c_void_p, C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p, C.c_uint32,
+                                       C.c_void_p, C.POINTER(C.c_void_p)]),
+    "atdct16_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "atdct16_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_float)]),
+    "atdct16_batch_destroy": (C.c_int, [C.c_void_p]),
+    "atdct16_server_create": (C.c_int, [C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]),
+    "atdct16_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "atdct16_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.c_int64]),
+    "atdct16_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_size_t)]),
+    "atdct16_server_destroy": (C.c_int, [C.c_void_p]),
     "atdct16_plan_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "atdct16_plan_profile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
 }
@@ -183,6 +222,93 @@ class Plan:
 
     def last_device_status(self) -> int:
         return lib().atdct16_last_device_status(self._h)
+
+
+BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2
+
+
+class Batch:
+    """A resident zonal batch (``atdct16_batch_*``): descriptors on the device,
+    optional autotuned launch shape and CUDA-graph capture."""
+
+    def __init__(self, plan, images, psnr, sse=None, flags=BATCH_AUTOTUNE | BATCH_GRAPH, stream=None):
+        self._h = C.c_void_p()
+        self.plan = plan  # keeps the plan alive
+        arr = (Image * len(images))(*images)
+        _check(lib().atdct16_batch_create(plan.handle, arr, len(images), _ptr(psnr), _ptr(sse), flags,
+                                          _stream(stream), C.byref(self._h)), "batch_create")
+
+    def launch(self, stream=None):
+        _check(lib().atdct16_batch_launch(self._h, _stream(stream)), "batch_launch")
+
+    def info(self):
+        v, w, p, g = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        t, ms = C.c_int64(), C.c_float()
+        _check(lib().atdct16_batch_info(self._h, C.byref(v), C.byref(w), C.byref(p), C.byref(g), C.byref(t),
+                                        C.byref(ms)), "batch_info")
+        return {"variant": ("f32", "swar")[v.value], "warps": w.value, "prefetch": p.value, "grid": g.value,
+                "tiles": t.value, "tuned_ms": ms.value}
+
+    def close(self):
+        if self._h:
+            lib().atdct16_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_ptr(a):
+    """Address of a host buffer: a CPU torch tensor or a numpy array."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr(), a.stride(-2) * a.element_size()
+    return a.ctypes.data, a.strides[-2]
+
+
+class Server:
+    """Continuous-batching compression server (``atdct16_server_*``)."""
+
+    def __init__(self, memory_budget_bytes=1 << 30, max_batch=64, compute_slots=2):
+        self._h = C.c_void_p()
+        cfg = ServerConfig(memory_budget_bytes, max_batch, compute_slots, 0)
+        _check(lib().atdct16_server_create(C.byref(cfg), C.byref(self._h)), "server_create")
+
+    def submit(self, src, dst, r):
+        """Queue ``src`` (H, W uint8, host) -> ``dst`` (host); returns a ticket."""
+        sp, spitch = _host_ptr(src)
+        dp, dpitch = _host_ptr(dst)
+        h, w = src.shape[-2], src.shape[-1]
+        req = Request(sp, dp, spitch, dpitch, w, h, int(r), 0)
+        t = C.c_uint64()
+        _check(lib().atdct16_server_submit(self._h, C.byref(req), C.byref(t)), "server_submit")
+        return t.value
+
+    def wait(self, ticket, timeout_us=-1):
+        """(PSNR, latency in seconds) of a request; forgets the ticket."""
+        p, lat = C.c_double(), C.c_double()
+        _check(lib().atdct16_server_wait(self._h, ticket, C.byref(p), C.byref(lat), timeout_us), "server_wait")
+        return p.value, lat.value
+
+    def stats(self):
+        c, l, px, b, a = C.c_uint64(), C.c_uint64(), C.c_double(), C.c_double(), C.c_size_t()
+        _check(lib().atdct16_server_stats(self._h, C.byref(c), C.byref(l), C.byref(px), C.byref(b), C.byref(a)),
+               "server_stats")
+        return {"completed": c.value, "launches": l.value, "pixels": px.value, "busy_s": b.value,
+                "arena_used": a.value}
+
+    def close(self):
+        if self._h:
+            lib().atdct16_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def compress_zonal_noalloc(images, psnr, sse=None, stream=None):

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -29,6 +30,13 @@ struct atdct16_plan_st {
   cudaEvent_t upload_done = nullptr;    // staging buffers may be rewritten after this
   bool upload_pending = false;
   cudaStream_t last_stream = nullptr;
+  // autotuner results for this plan: batch-shape key -> (config, CTAs per SM, ms)
+  struct Tuned {
+    ZonalConfig cfg;
+    int ctas;
+    float ms;
+  };
+  std::map<unsigned long long, Tuned> tuned;
   // kernel timing hook
   bool profiling = false;
   std::vector<cudaEvent_t> prof_events;  // pairs (start, stop)
@@ -130,6 +138,23 @@ atdct16_status stage_jobs(atdct16_plan_t plan, const atdct16_image* h_images, in
 }
 
 }  // namespace
+
+namespace atdct16 {
+const float2* plan_zonal_table(const atdct16_plan_st* plan) { return plan->d_wtab; }
+int plan_num_sms(const atdct16_plan_st* plan) { return plan->num_sms; }
+int plan_device(const atdct16_plan_st* plan) { return plan->device; }
+bool plan_tune_lookup(atdct16_plan_st* plan, unsigned long long key, ZonalConfig* cfg, int* ctas, float* ms) {
+  auto it = plan->tuned.find(key);
+  if (it == plan->tuned.end()) return false;
+  *cfg = it->second.cfg;
+  *ctas = it->second.ctas;
+  *ms = it->second.ms;
+  return true;
+}
+void plan_tune_store(atdct16_plan_st* plan, unsigned long long key, const ZonalConfig& cfg, int ctas, float ms) {
+  plan->tuned[key] = atdct16_plan_st::Tuned{cfg, ctas, ms};
+}
+}  // namespace atdct16
 
 extern "C" {
 

@@ -1,0 +1,338 @@
+// Resident batches: descriptors uploaded once, launch shape autotuned on the
+// batch itself, fused zonal kernel + PSNR finalize captured in a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/atdct16.h"
+#include "atdct16_internal.h"
+
+using namespace atdct16;
+
+struct atdct16_batch_st {
+  atdct16_plan_t plan = nullptr;
+  int device = 0;
+  int n = 0;
+  long long ntiles = 0;
+  ImageJob* d_jobs = nullptr;
+  float* d_tile_sse = nullptr;
+  int* d_status = nullptr;
+  double* d_psnr = nullptr;
+  double* d_sse = nullptr;
+  ZonalConfig cfg{};
+  int ctas = 1;
+  int grid = 1;
+  float tuned_ms = 0.f;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+atdct16_status check_zonal_image(const atdct16_image& im) {
+  if (!im.src || !im.dst || im.width <= 0 || im.height <= 0 || (im.width & 15) || (im.height & 15))
+    return ATDCT16_EINVAL;
+  if (im.src_pitch < im.width || im.dst_pitch < im.width || (im.src_pitch & 15) || (im.dst_pitch & 15))
+    return ATDCT16_EINVAL;
+  if (im.src_pitch >= ((int64_t)1 << 31) || im.dst_pitch >= ((int64_t)1 << 31)) return ATDCT16_EINVAL;
+  if (!aligned16(im.src) || !aligned16(im.dst) || im.reserved != 0 || im.r_or_qp < 0 || im.r_or_qp > 256)
+    return ATDCT16_EINVAL;
+  return ATDCT16_OK;
+}
+
+// Does any destination byte range overlap any source byte range?
+bool dst_overlaps_src(const atdct16_image* im, int n) {
+  struct Range {
+    uintptr_t lo, hi;
+    int kind;  // 0 src, 1 dst
+  };
+  std::vector<Range> r;
+  r.reserve(2 * n);
+  for (int i = 0; i < n; ++i) {
+    const uintptr_t s = reinterpret_cast<uintptr_t>(im[i].src), d = reinterpret_cast<uintptr_t>(im[i].dst);
+    r.push_back({s, s + (uintptr_t)im[i].src_pitch * (im[i].height - 1) + im[i].width, 0});
+    r.push_back({d, d + (uintptr_t)im[i].dst_pitch * (im[i].height - 1) + im[i].width, 1});
+  }
+  std::sort(r.begin(), r.end(), [](const Range& a, const Range& b) { return a.lo < b.lo; });
+  // sweep: any open range of the other kind reaching past this start overlaps
+  uintptr_t max_hi[2] = {0, 0};
+  for (const Range& x : r) {
+    if (max_hi[1 - x.kind] > x.lo) return true;
+    max_hi[x.kind] = std::max(max_hi[x.kind], x.hi);
+  }
+  return false;
+}
+
+// FNV-1a over the batch shape: sizes, r and the device's SM count.
+unsigned long long shape_key(const atdct16_image* im, int n, int sms) {
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](unsigned long long v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (v >> (8 * b)) & 0xff;
+      h *= 1099511628211ull;
+    }
+  };
+  mix((unsigned long long)n);
+  mix((unsigned long long)sms);
+  for (int i = 0; i < n; ++i) {
+    mix((unsigned long long)im[i].width << 32 | (unsigned)im[i].height);
+    mix((unsigned long long)im[i].r_or_qp);
+  }
+  return h;
+}
+
+int grid_for(const ZonalConfig& cfg, int ctas, int sms, long long ntiles) {
+  const long long need = (ntiles + cfg.warps - 1) / cfg.warps;
+  return (int)std::max<long long>(1, std::min<long long>((long long)sms * ctas, need));
+}
+
+// Tuning-cache file (ATDCT16_TUNE_CACHE): one JSON object per line,
+// {"key": "<hex>", "variant": v, "warps": w, "prefetch": p, "ctas": c, "ms": t}
+bool file_lookup(unsigned long long key, ZonalConfig* cfg, int* ctas, float* ms) {
+  const char* path = std::getenv("ATDCT16_TUNE_CACHE");
+  if (!path || !*path) return false;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  while (std::fgets(line, sizeof line, f)) {
+    unsigned long long k = 0;
+    int v, w, p, c;
+    float t;
+    if (std::sscanf(line, " {\"key\": \"%llx\", \"variant\": %d, \"warps\": %d, \"prefetch\": %d, \"ctas\": %d, \"ms\": %f",
+                    &k, &v, &w, &p, &c, &t) == 6 &&
+        k == key) {
+      const ZonalConfig z{v, w, p};
+      if (zonal_config_supported(z) && c >= 1) {
+        *cfg = z;
+        *ctas = c;
+        *ms = t;
+        found = true;  // the last matching line wins
+      }
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+void file_store(unsigned long long key, const ZonalConfig& cfg, int ctas, float ms) {
+  const char* path = std::getenv("ATDCT16_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "{\"key\": \"%016llx\", \"variant\": %d, \"warps\": %d, \"prefetch\": %d, \"ctas\": %d, \"ms\": %.6f}\n",
+               key, cfg.variant, cfg.warps, cfg.prefetch, ctas, ms);
+  std::fclose(f);
+}
+
+cudaError_t launch_batch_once(atdct16_batch_st* b, const ZonalConfig& cfg, int grid, cudaStream_t stream) {
+  cudaError_t e = launch_zonal_config(cfg, b->d_jobs, b->n, b->ntiles, plan_zonal_table(b->plan), b->d_tile_sse,
+                                      b->d_status, grid, stream);
+  if (e == cudaSuccess)
+    e = launch_psnr_finalize(b->d_jobs, b->n, b->ntiles, b->d_tile_sse, 255.0, b->d_psnr, b->d_sse, stream);
+  return e;
+}
+
+// Time every candidate launch shape on the batch (min of 3 after a warm-up).
+atdct16_status autotune(atdct16_batch_st* b, int sms, cudaStream_t stream) {
+  const ZonalConfig cands[] = {
+      {kZonalF32, 4, 1}, {kZonalF32, 2, 1}, {kZonalF32, 8, 1}, {kZonalF32, 4, 0}, {kZonalSwar, 4, 1},
+  };
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return ATDCT16_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return ATDCT16_ECUDA;
+  }
+  float best = 1e30f;
+  ZonalConfig best_cfg = default_zonal_config();
+  int best_ctas = 1;
+  atdct16_status st = ATDCT16_OK;
+  for (const ZonalConfig& c : cands) {
+    const int maxc = zonal_config_max_ctas_per_sm(c);
+    const int opts[2] = {maxc, std::max(1, maxc / 2)};
+    for (int oi = 0; oi < (maxc > 1 ? 2 : 1) && st == ATDCT16_OK; ++oi) {
+      const int grid = grid_for(c, opts[oi], sms, b->ntiles);
+      if (launch_batch_once(b, c, grid, stream) != cudaSuccess) {
+        st = ATDCT16_ECUDA;
+        break;
+      }
+      float t = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        float ms = 0.f;
+        if (cudaEventRecord(e0, stream) != cudaSuccess || launch_batch_once(b, c, grid, stream) != cudaSuccess ||
+            cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          st = ATDCT16_ECUDA;
+          break;
+        }
+        t = std::min(t, ms);
+      }
+      if (st == ATDCT16_OK && t < best) {
+        best = t;
+        best_cfg = c;
+        best_ctas = opts[oi];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != ATDCT16_OK) return st;
+  b->cfg = best_cfg;
+  b->ctas = best_ctas;
+  b->tuned_ms = best;
+  return ATDCT16_OK;
+}
+
+void free_batch(atdct16_batch_st* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(b->d_jobs);
+  cudaFree(b->d_tile_sse);
+  cudaFree(b->d_status);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+atdct16_status atdct16_batch_create(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n, double* d_psnr,
+                                    double* d_sse, uint32_t flags, cudaStream_t stream, atdct16_batch_t* out) {
+  if (!out) return ATDCT16_EINVAL;
+  *out = nullptr;
+  if (!plan || !h_images || !d_psnr || n < 1 || (flags & ~(ATDCT16_BATCH_AUTOTUNE | ATDCT16_BATCH_GRAPH)))
+    return ATDCT16_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    const atdct16_status s = check_zonal_image(h_images[i]);
+    if (s != ATDCT16_OK) return s;
+  }
+  if ((flags & ATDCT16_BATCH_AUTOTUNE) && dst_overlaps_src(h_images, n)) return ATDCT16_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ATDCT16_ECUDA;
+  if (dev != plan_device(plan)) return ATDCT16_EINVAL;
+
+  std::vector<ImageJob> jobs(n);
+  long long tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    const atdct16_image& im = h_images[i];
+    ImageJob& J = jobs[i];
+    J.src = static_cast<const uint8_t*>(im.src);
+    J.dst = static_cast<uint8_t*>(im.dst);
+    J.src_pitch = im.src_pitch;
+    J.dst_pitch = im.dst_pitch;
+    J.width = im.width;
+    J.height = im.height;
+    J.tiles_x = (im.width + kTileW - 1) / kTileW;
+    J.param = im.r_or_qp;
+    J.tile_begin = tiles;
+    J.level_base = 0;
+    tiles += (long long)J.tiles_x * (im.height / kTileH);
+  }
+
+  atdct16_batch_st* b = new (std::nothrow) atdct16_batch_st();
+  if (!b) return ATDCT16_ENOMEM;
+  b->plan = plan;
+  b->device = dev;
+  b->n = n;
+  b->ntiles = tiles;
+  b->d_psnr = d_psnr;
+  b->d_sse = d_sse;
+  b->last_stream = stream;
+  cudaError_t e = cudaMalloc(&b->d_jobs, sizeof(ImageJob) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_tile_sse, sizeof(float) * std::max<long long>(1, tiles));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_jobs, jobs.data(), sizeof(ImageJob) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    free_batch(b);
+    return e == cudaErrorMemoryAllocation ? ATDCT16_ENOMEM : ATDCT16_ECUDA;
+  }
+
+  const int sms = plan_num_sms(plan);
+  b->cfg = default_zonal_config();
+  b->ctas = zonal_config_max_ctas_per_sm(b->cfg);
+  if (flags & ATDCT16_BATCH_AUTOTUNE) {
+    const unsigned long long key = shape_key(h_images, n, sms);
+    ZonalConfig c;
+    int ctas;
+    float ms;
+    if (plan_tune_lookup(plan, key, &c, &ctas, &ms) || file_lookup(key, &c, &ctas, &ms)) {
+      b->cfg = c;
+      b->ctas = ctas;
+      b->tuned_ms = ms;
+      plan_tune_store(plan, key, c, ctas, ms);
+    } else {
+      const atdct16_status s = autotune(b, sms, stream);
+      if (s != ATDCT16_OK) {
+        free_batch(b);
+        return s;
+      }
+      plan_tune_store(plan, key, b->cfg, b->ctas, b->tuned_ms);
+      file_store(key, b->cfg, b->ctas, b->tuned_ms);
+    }
+  }
+  b->grid = grid_for(b->cfg, b->ctas, sms, tiles);
+
+  if (flags & ATDCT16_BATCH_GRAPH) {
+    // Capture on a private stream so that the caller's stream is untouched.
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+      // launches with dynamic shared memory above 48 KB set their attribute
+      // first; do one uncaptured launch so that happens outside the capture
+      e = launch_batch_once(b, b->cfg, b->grid, cs);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+      if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const cudaError_t le = launch_batch_once(b, b->cfg, b->grid, cs);
+        e = cudaStreamEndCapture(cs, &b->graph);
+        if (le != cudaSuccess) e = le;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+      cudaStreamDestroy(cs);
+    }
+    if (e != cudaSuccess) {
+      free_batch(b);
+      return ATDCT16_ECUDA;
+    }
+  }
+  *out = b;
+  return ATDCT16_OK;
+}
+
+atdct16_status atdct16_batch_launch(atdct16_batch_t b, cudaStream_t stream) {
+  if (!b) return ATDCT16_EINVAL;
+  b->last_stream = stream;
+  cudaError_t e = b->exec ? cudaGraphLaunch(b->exec, stream) : launch_batch_once(b, b->cfg, b->grid, stream);
+  return e == cudaSuccess ? ATDCT16_OK : ATDCT16_ECUDA;
+}
+
+atdct16_status atdct16_batch_info(atdct16_batch_t b, int32_t* variant, int32_t* warps, int32_t* prefetch,
+                                  int32_t* grid, int64_t* tiles, float* tuned_ms) {
+  if (!b) return ATDCT16_EINVAL;
+  if (variant) *variant = b->cfg.variant;
+  if (warps) *warps = b->cfg.warps;
+  if (prefetch) *prefetch = b->cfg.prefetch;
+  if (grid) *grid = b->grid;
+  if (tiles) *tiles = b->ntiles;
+  if (tuned_ms) *tuned_ms = b->tuned_ms;
+  return ATDCT16_OK;
+}
+
+atdct16_status atdct16_batch_destroy(atdct16_batch_t b) {
+  if (!b) return ATDCT16_EINVAL;
+  cudaSetDevice(b->device);
+  if (b->last_stream) cudaStreamSynchronize(b->last_stream);
+  free_batch(b);
+  return ATDCT16_OK;
+}
+
+}  // extern "C"

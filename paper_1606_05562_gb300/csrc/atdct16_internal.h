@@ -44,13 +44,20 @@ constexpr int kDevBadJob = 1;
 // Kernel launchers (atdct16_kernels.cu).  All asynchronous on `stream`.
 cudaError_t launch_zonal(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
                          float* d_tile_sse, int* d_status, int grid, cudaStream_t stream);
-// Zonal kernel variants: all-FP32 butterflies (default) or the forward
-// transform in 16-bit SWAR lanes.
-constexpr int kZonalF32 = 0;
-constexpr int kZonalSwar = 1;
-cudaError_t launch_zonal_variant(int variant, const ImageJob* d_jobs, int njobs, long long ntiles,
-                                 const float2* d_wtab, float* d_tile_sse, int* d_status, int grid,
-                                 cudaStream_t stream);
+// Launch shapes of the fused zonal kernel (chosen by the batch autotuner).
+constexpr int kZonalF32 = 0;   // all-FP32 butterflies
+constexpr int kZonalSwar = 1;  // forward transform in 16-bit SWAR lanes
+struct ZonalConfig {
+  int variant;   // kZonalF32 or kZonalSwar
+  int warps;     // warps per CTA: 2, 4 or 8 (SWAR: 4)
+  int prefetch;  // 1: load the next tile while computing the current one
+};
+bool zonal_config_supported(const ZonalConfig& c);
+ZonalConfig default_zonal_config();
+int zonal_config_max_ctas_per_sm(const ZonalConfig& c);
+cudaError_t launch_zonal_config(const ZonalConfig& cfg, const ImageJob* d_jobs, int njobs, long long ntiles,
+                                const float2* d_wtab, float* d_tile_sse, int* d_status, int grid,
+                                cudaStream_t stream);
 cudaError_t launch_quant(const ImageJob* d_jobs, int njobs, long long ntiles, const float4* d_qtab,
                          int16_t* d_levels, float* d_tile_sse, int* d_status, int grid,
                          cudaStream_t stream);
@@ -64,6 +71,17 @@ cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void*
 cudaError_t launch_psnr_pair(int dtype, const void* d_a, long long pitch_a, const void* d_b,
                              long long pitch_b, int w, int h, double* d_out, cudaStream_t stream);
 int zonal_ctas_per_sm();
+
+}  // namespace atdct16
+
+// Plan internals shared with the batch layer (atdct16_api.cu).
+struct atdct16_plan_st;
+namespace atdct16 {
+const float2* plan_zonal_table(const atdct16_plan_st* plan);
+int plan_num_sms(const atdct16_plan_st* plan);
+int plan_device(const atdct16_plan_st* plan);
+bool plan_tune_lookup(atdct16_plan_st* plan, unsigned long long key, ZonalConfig* cfg, int* ctas, float* ms);
+void plan_tune_store(atdct16_plan_st* plan, unsigned long long key, const ZonalConfig& cfg, int ctas, float ms);
 int quant_ctas_per_sm();
 
 }  // namespace atdct16

@@ -161,11 +161,12 @@ struct TileRef {
   int nb;
 };
 
-template <int kWarps>
+template <int kWarps, bool kPrefetch>
 __global__ void __launch_bounds__(32 * kWarps, 16 / kWarps)
 zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
              const float2* __restrict__ wtab, float* __restrict__ tile_sse, int* __restrict__ status) {
-  __shared__ ZonalWarpSmem smem[kWarps];
+  extern __shared__ __align__(16) unsigned char zsmem[];
+  ZonalWarpSmem* smem = reinterpret_cast<ZonalWarpSmem*>(zsmem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int p = lane >> 3, j = lane & 7;
   float4* buf = smem[warp].t;
@@ -241,7 +242,7 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
       ++tn;
     }
     uint4 na0, na1, nb0, nb1;
-    if (have_next) load(nxt, na0, na1, nb0, nb1);
+    if (kPrefetch && have_next) load(nxt, na0, na1, nb0, nb1);
 
     const bool va = p < cur.nb, vb = p + 4 < cur.nb;
     if (cur.r != wr) {  // warp-uniform: refresh the weight copy
@@ -345,7 +346,11 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
 
     if (!have_next) break;
     cur = nxt;
-    a0 = na0; a1 = na1; b0 = nb0; b1 = nb1;
+    if (kPrefetch) {
+      a0 = na0; a1 = na1; b0 = nb0; b1 = nb1;
+    } else {
+      load(cur, a0, a1, b0, b1);
+    }
   }
 }
 
@@ -933,27 +938,88 @@ __global__ void psnr_pair_finish(unsigned long long* slot, double npx, double pe
 // --------------------------------------------------------------------------
 // Launchers
 // --------------------------------------------------------------------------
-cudaError_t launch_zonal_variant(int variant, const ImageJob* d_jobs, int njobs, long long ntiles,
-                                 const float2* d_wtab, float* d_tile_sse, int* d_status, int grid,
-                                 cudaStream_t stream) {
-  if (ntiles <= 0) return cudaSuccess;
-  if (variant == kZonalSwar) {
-    // dynamic shared memory above 48 KB must be enabled per device
-    cudaError_t e = cudaFuncSetAttribute(zonal_swar_kernel<kZonalWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSwarWarpSmem * kZonalWarps);
+template <class K>
+static cudaError_t launch_with_smem(K kernel, int grid, int threads, int smem, cudaStream_t stream,
+                                   const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
+                                   float* d_tile_sse, int* d_status) {
+  // dynamic shared memory above 48 KB must be enabled per device
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    zonal_swar_kernel<kZonalWarps><<<grid, 32 * kZonalWarps, kSwarWarpSmem * kZonalWarps, stream>>>(
-        d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
-  } else {
-    zonal_f32_kernel<kZonalWarps><<<grid, 32 * kZonalWarps, 0, stream>>>(d_jobs, njobs, ntiles, d_wtab, d_tile_sse,
-                                                                         d_status);
   }
+  kernel<<<grid, threads, smem, stream>>>(d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
   return cudaGetLastError();
 }
 
+static int config_index(const ZonalConfig& c) {
+  if (c.variant == kZonalSwar) return c.warps == 4 ? 4 : -1;
+  if (c.warps == 2 && c.prefetch) return 0;
+  if (c.warps == 4 && c.prefetch) return 1;
+  if (c.warps == 8 && c.prefetch) return 2;
+  if (c.warps == 4 && !c.prefetch) return 3;
+  return -1;
+}
+
+bool zonal_config_supported(const ZonalConfig& c) { return config_index(c) >= 0; }
+
+cudaError_t launch_zonal_config(const ZonalConfig& cfg, const ImageJob* d_jobs, int njobs, long long ntiles,
+                                const float2* d_wtab, float* d_tile_sse, int* d_status, int grid,
+                                cudaStream_t stream) {
+  if (ntiles <= 0) return cudaSuccess;
+  const int threads = 32 * cfg.warps;
+  switch (config_index(cfg)) {
+    case 0:
+      return launch_with_smem(zonal_f32_kernel<2, true>, grid, threads, 2 * (int)sizeof(ZonalWarpSmem), stream,
+                              d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
+    case 1:
+      return launch_with_smem(zonal_f32_kernel<4, true>, grid, threads, 4 * (int)sizeof(ZonalWarpSmem), stream,
+                              d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
+    case 2:
+      return launch_with_smem(zonal_f32_kernel<8, true>, grid, threads, 8 * (int)sizeof(ZonalWarpSmem), stream,
+                              d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
+    case 3:
+      return launch_with_smem(zonal_f32_kernel<4, false>, grid, threads, 4 * (int)sizeof(ZonalWarpSmem), stream,
+                              d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
+    case 4:
+      return launch_with_smem(zonal_swar_kernel<4>, grid, threads, 4 * kSwarWarpSmem, stream, d_jobs, njobs,
+                              ntiles, d_wtab, d_tile_sse, d_status);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int zonal_config_max_ctas_per_sm(const ZonalConfig& cfg) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (config_index(cfg)) {
+    case 0:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_f32_kernel<2, true>, 64, 2 * sizeof(ZonalWarpSmem));
+      break;
+    case 1:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_f32_kernel<4, true>, 128, 4 * sizeof(ZonalWarpSmem));
+      break;
+    case 2:
+      cudaFuncSetAttribute(zonal_f32_kernel<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           8 * (int)sizeof(ZonalWarpSmem));
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_f32_kernel<8, true>, 256, 8 * sizeof(ZonalWarpSmem));
+      break;
+    case 3:
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_f32_kernel<4, false>, 128,
+                                                        4 * sizeof(ZonalWarpSmem));
+      break;
+    case 4:
+      cudaFuncSetAttribute(zonal_swar_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kSwarWarpSmem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_swar_kernel<4>, 128, 4 * kSwarWarpSmem);
+      break;
+  }
+  return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
+ZonalConfig default_zonal_config() { return ZonalConfig{kZonalF32, kZonalWarps, 1}; }
+
 cudaError_t launch_zonal(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
                          float* d_tile_sse, int* d_status, int grid, cudaStream_t stream) {
-  return launch_zonal_variant(kZonalF32, d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, grid, stream);
+  return launch_zonal_config(default_zonal_config(), d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, grid,
+                             stream);
 }
 
 cudaError_t launch_quant(const ImageJob* d_jobs, int njobs, long long ntiles, const float4* d_qtab,
@@ -1014,14 +1080,7 @@ cudaError_t launch_psnr_pair(int dtype, const void* d_a, long long pitch_a, cons
   return cudaGetLastError();
 }
 
-int zonal_ctas_per_sm() {
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_f32_kernel<kZonalWarps>, 32 * kZonalWarps, 0) !=
-          cudaSuccess ||
-      n < 1)
-    n = 1;
-  return n;
-}
+int zonal_ctas_per_sm() { return zonal_config_max_ctas_per_sm(default_zonal_config()); }
 int quant_ctas_per_sm() {
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, quant_kernel, kThreadsPerCta, 0) != cudaSuccess || n < 1) n = 1;

@@ -1,0 +1,115 @@
+"""Resident mixed-size batches under a CUDA graph with the autotuner
+(atdct16_batch_*), against the oracle and the per-call entry point."""
+
+import json
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1606_05562_gb300 import atdct16, build, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    atdct16.lib()
+    return t
+
+
+@pytest.fixture(scope="module")
+def plan(torch):
+    p = atdct16.Plan(atdct16.U8, max_images=256)
+    yield p
+    p.close()
+
+
+def _mixed(seed, n=40, lo=16, hi=400):
+    imgs = synth.mixed_batch(n, lo=lo, hi=hi, seed=seed)
+    rs = [int(v) for v in np.random.default_rng(seed).choice(synth.ZONAL_R_SWEEP, size=len(imgs))]
+    return imgs, rs
+
+
+def _dev(torch, imgs):
+    src = [torch.from_numpy(im).cuda() for im in imgs]
+    dst = [torch.full_like(s, 9) for s in src]
+    return src, dst
+
+
+@pytest.mark.parametrize("flags", [0, atdct16.BATCH_GRAPH, atdct16.BATCH_AUTOTUNE | atdct16.BATCH_GRAPH])
+def test_batch_matches_oracle_and_per_call(torch, plan, flags):
+    imgs, rs = _mixed(11)
+    src, dst = _dev(torch, imgs)
+    descs = [atdct16.image(s, d, r) for s, d, r in zip(src, dst, rs)]
+    psnr = torch.empty(len(imgs), dtype=torch.float64, device="cuda")
+    b = atdct16.Batch(plan, descs, psnr, flags=flags)
+    for _ in range(2):  # re-launching the same graph gives the same result
+        for d in dst:
+            d.fill_(9)
+        b.launch()
+        torch.cuda.synchronize()
+        for im, r, d, p in zip(imgs, rs, dst, psnr.cpu().tolist()):
+            ref = O.compress_zonal_exact(im, r)
+            assert np.array_equal(d.cpu().numpy(), ref["recon_u8"])
+            if math.isinf(ref["psnr"]):
+                assert math.isinf(p)
+            else:
+                assert p == pytest.approx(ref["psnr"], rel=1e-5, abs=1e-5)
+    # the per-call entry point gives the same bytes and PSNR
+    dst2 = [torch.full_like(s, 1) for s in src]
+    psnr2 = torch.empty_like(psnr)
+    plan.compress_zonal([atdct16.image(s, d, r) for s, d, r in zip(src, dst2, rs)], psnr2)
+    torch.cuda.synchronize()
+    for a, c in zip(dst, dst2):
+        assert torch.equal(a, c)
+    fin = ~psnr.isinf()
+    assert torch.equal(psnr.isinf(), psnr2.isinf())
+    assert torch.allclose(psnr[fin], psnr2[fin], rtol=1e-12, atol=0)
+    info = b.info()
+    assert info["tiles"] > 0 and info["grid"] > 0
+    if flags & atdct16.BATCH_AUTOTUNE:
+        assert info["tuned_ms"] > 0
+    b.close()
+
+
+def test_autotune_cache_file(torch, tmp_path, monkeypatch):
+    path = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("ATDCT16_TUNE_CACHE", str(path))
+    imgs, rs = _mixed(12, n=10)
+    src, dst = _dev(torch, imgs)
+    descs = [atdct16.image(s, d, r) for s, d, r in zip(src, dst, rs)]
+    psnr = torch.empty(len(imgs), dtype=torch.float64, device="cuda")
+    p1 = atdct16.Plan(atdct16.U8, max_images=16)
+    b1 = atdct16.Batch(p1, descs, psnr, flags=atdct16.BATCH_AUTOTUNE)
+    lines = path.read_text().strip().splitlines()
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["warps"] in (2, 4, 8) and rec["ms"] > 0
+    b1.close()
+    p1.close()
+    # a fresh plan finds the result in the file instead of re-tuning
+    p2 = atdct16.Plan(atdct16.U8, max_images=16)
+    b2 = atdct16.Batch(p2, descs, psnr, flags=atdct16.BATCH_AUTOTUNE)
+    assert len(path.read_text().strip().splitlines()) == 1
+    info = b2.info()
+    assert info["warps"] == rec["warps"] and info["prefetch"] == rec["prefetch"]
+    b2.close()
+    p2.close()
+
+
+def test_autotune_rejects_in_place(torch, plan):
+    img = torch.from_numpy(synth.ar1_image(64, 64, 0.9, 1)).cuda()
+    psnr = torch.empty(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(atdct16.Atdct16Error) as e:
+        atdct16.Batch(plan, [atdct16.image(img, img, 16)], psnr, flags=atdct16.BATCH_AUTOTUNE)
+    assert e.value.status == atdct16.EINVAL
+    b = atdct16.Batch(plan, [atdct16.image(img, img, 256)], psnr, flags=atdct16.BATCH_GRAPH)  # in place is fine untuned
+    b.launch()
+    torch.cuda.synchronize()
+    b.close()
