@@ -47,6 +47,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--no-extras", action="store_true", help="skip the mixed-batch and serving phases")
+    ap.add_argument("--mixed-images", type=int, default=1000)
+    ap.add_argument("--serve-rates", default="100,250,500,1000,2000,5000")
     return ap.parse_args()
 
 
@@ -221,6 +224,156 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+def mixed_batch_phase(torch, atdct16, synth, dev, n_images, seed=4):
+    """1000 mixed-size u8 AR(1) images (sides log-uniform in [128, 4096],
+    multiples of 16, rho in [0.8, 0.97]), zonal r = 36: per-image launches of
+    the plain entry point against one autotuned CUDA-graph launch of the
+    whole batch.  Images are crops of four seeded 4096x4096 AR(1) fields
+    (one rho each), copied into distinct device buffers."""
+    import numpy as np
+
+    rhos = (0.8, 0.85, 0.9, 0.97)
+    fields = [torch.from_numpy(synth.ar1_image(4096, 4096, rho, seed * 1000 + k)).to(dev) for k, rho in enumerate(rhos)]
+    sizes = synth.mixed_sizes(n_images, 128, 4096, seed + 7)
+    rng = np.random.default_rng(seed)
+    total = sum(h * w for h, w in sizes)
+    src_all = torch.empty(total, dtype=torch.uint8, device=dev)
+    dst_a = torch.empty_like(src_all)
+    dst_b = torch.empty_like(src_all)
+    srcs, da, db = [], [], []
+    off = 0
+    for i, (h, w) in enumerate(sizes):
+        f = fields[i % 4]
+        y0 = int(rng.integers(0, 4096 - h + 1)) // 16 * 16
+        x0 = int(rng.integers(0, 4096 - w + 1)) // 16 * 16
+        s = src_all[off:off + h * w].view(h, w)
+        s.copy_(f[y0:y0 + h, x0:x0 + w])
+        srcs.append(s)
+        da.append(dst_a[off:off + h * w].view(h, w))
+        db.append(dst_b[off:off + h * w].view(h, w))
+        off += h * w
+    r = 36
+    plan1 = atdct16.Plan(atdct16.U8, max_images=1)
+    p1 = torch.empty(n_images, dtype=torch.float64, device=dev)
+    descs_a = [atdct16.image(s, d, r) for s, d in zip(srcs, da)]
+
+    def per_image():
+        for i, d in enumerate(descs_a):
+            plan1.compress_zonal([d], p1[i:i + 1])
+
+    per_image()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    per_image()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_a = e0.elapsed_time(e1)
+    planb = atdct16.Plan(atdct16.U8, max_images=n_images, workspace_bytes=1 << 30)
+    p2 = torch.empty(n_images, dtype=torch.float64, device=dev)
+    t0 = time.perf_counter()
+    batch = atdct16.Batch(planb, [atdct16.image(s, d, r) for s, d in zip(srcs, db)], p2,
+                          flags=atdct16.BATCH_AUTOTUNE | atdct16.BATCH_GRAPH)
+    tune_s = time.perf_counter() - t0
+    batch.launch()
+    torch.cuda.synchronize()
+    reps = 10
+    e0.record()
+    for _ in range(reps):
+        batch.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / reps
+    same = bool(torch.equal(dst_a, dst_b)) and bool(torch.equal(p1.isinf(), p2.isinf()))
+    fin = ~p1.isinf()
+    same = same and bool(torch.equal(p1[fin], p2[fin]))
+    info = batch.info()
+    batch.close()
+    out = {"images": n_images, "pixels": int(total), "r": r,
+           "per_image_launches_gpx_s": total / (ms_a / 1e3) / 1e9,
+           "graph_batch_gpx_s": total / (ms_b / 1e3) / 1e9,
+           "graph_batch_gbs": 2.0 * total / (ms_b / 1e3) / 1e9,
+           "speedup": ms_a / ms_b, "identical_results": same, "autotune_s": tune_s, "tuned": info}
+    del fields, src_all, dst_a, dst_b
+    return out
+
+
+def serving_phase(torch, atdct16, synth, rates, seed=5):
+    """Poisson arrivals at each rate; uint8 requests with sides log-uniform in
+    [64, 8192] (multiples of 16) cut from a seeded 8192x8192 AR(1) field in
+    pinned host memory, r uniform in {6, 16, 36, 64}; 40 GB device arena.
+    Bounded sample: max(200, min(2000, rate x 1 s)) requests per rate."""
+    import threading
+
+    import numpy as np
+
+    field = torch.from_numpy(synth.ar1_image(8192, 8192, 0.95, seed * 1000)).pin_memory()
+    ring_bytes = 1 << 31
+    ring = torch.empty(ring_bytes, dtype=torch.uint8).pin_memory()
+    srv = atdct16.Server(memory_budget_bytes=40 << 30, max_batch=64, compute_slots=3)
+    results = []
+    for rate in rates:
+        n = int(max(200, min(2000, rate * 1.0)))
+        rng = np.random.default_rng(seed + int(rate))
+        sizes = synth.mixed_sizes(n, 64, 8192, seed * 31 + int(rate))
+        rs = rng.choice((6, 16, 36, 64), size=n)
+        arrivals = synth.poisson_arrivals(n, rate, seed * 17 + int(rate))
+        lat = [None] * n
+        tickets = [None] * n
+        done_upto = [0]
+        cv = threading.Condition()
+
+        def collector():
+            for i in range(n):
+                with cv:
+                    while tickets[i] is None:
+                        cv.wait()
+                _, l = srv.wait(tickets[i])
+                lat[i] = l
+                with cv:
+                    done_upto[0] = i + 1
+                    cv.notify_all()
+
+        th = threading.Thread(target=collector)
+        th.start()
+        ring_pos, slices = 0, []
+        t_start = time.perf_counter()
+        for i in range(n):
+            h, w = sizes[i]
+            y0 = int(rng.integers(0, 8192 - h + 1)) // 16 * 16
+            x0 = int(rng.integers(0, 8192 - w + 1)) // 16 * 16
+            if ring_pos + h * w > ring_bytes:
+                ring_pos = 0
+            # do not overwrite an output slice still in flight
+            while slices and any(s0 < ring_pos + h * w and ring_pos < s1 and k >= done_upto[0]
+                                 for (s0, s1, k) in slices[-64:]):
+                with cv:
+                    cv.wait(timeout=0.01)
+            dst = ring[ring_pos:ring_pos + h * w].view(h, w)
+            slices.append((ring_pos, ring_pos + h * w, i))
+            ring_pos += h * w
+            src = field[y0:y0 + h, x0:x0 + w]
+            delay = arrivals[i] - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            t = srv.submit(src, dst, int(rs[i]))
+            with cv:
+                tickets[i] = t
+                cv.notify_all()
+        th.join()
+        wall = time.perf_counter() - t_start
+        lat_ms = np.array(lat) * 1e3
+        px = sum(h * w for h, w in sizes)
+        results.append({"rate": rate, "requests": n, "p50_ms": float(np.percentile(lat_ms, 50)),
+                        "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
+                        "achieved_req_s": n / wall, "gpx_s": px / wall / 1e9, "pixels": int(px)})
+    st = srv.stats()
+    srv.close()
+    return {"rates": results, "launches": st["launches"], "arena_gb": 40,
+            "note": "latency = submission to completion, includes H2D and D2H copies"}
+
+
+# --------------------------------------------------------------------------
 def run_ours(args):
     import torch
 
@@ -354,6 +507,13 @@ def run_ours(args):
             "clocks": clk,
         }
         line["cpu_baseline"] = cpu_baseline(batch, args.cpu_seconds) if args.cpu_seconds > 0 else None
+        if not args.no_extras:
+            del sets
+            torch.cuda.empty_cache()
+            line["mixed_batch"] = mixed_batch_phase(torch, atdct16, synth, dev, args.mixed_images)
+            torch.cuda.empty_cache()
+            rates = [float(v) for v in args.serve_rates.split(",") if v]
+            line["serving"] = serving_phase(torch, atdct16, synth, rates)
         print(json.dumps(line), flush=True)
     plan.close()
     if dist:
