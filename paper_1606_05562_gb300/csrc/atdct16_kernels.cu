@@ -140,13 +140,26 @@ __device__ __forceinline__ float warp_sum(float v) {
 // Fused zonal compression: forward, keep the first r zig-zag coefficients,
 // S^2 scaling, inverse, round, store u8, per-tile SSE (Sec. 4 procedure).
 //
-// Shared memory per warp: the transpose buffer (lines = block columns, slots
-// = row pairs, 16-byte chunks XOR-swizzled by (line >> 1) & 7) and a copy of
-// the weight table of the warp's current r (chunks swizzled the same way).
-// The back-transpose uses the same line-per-column layout, so a lane only
+// Lane (p, j) = (lane & 3, lane >> 2) owns rows 2j, 2j+1 of blocks p and
+// p + 4 of a 16 x 128 tile (the two blocks ride in the halves of an f32x2),
+// so each quarter-warp touches two 64-byte row segments per global access.
+// Shared memory per warp: the transpose buffer (line p*16 + c = column c of
+// block pair p, slot = row pair, 16-byte chunks XOR-swizzled by
+// 2p ^ ((c >> 1) & 1)) and a copy of the weight table of the warp's current
+// r.  The back-transpose uses the same line-per-column layout, so a lane only
 // overwrites the two lines it alone has read.  The next tile's input rows
 // are loaded while the current tile is computed.
 // --------------------------------------------------------------------------
+// 16-byte read-only streaming load that does not allocate in L1: the input
+// is read exactly once, so a fill of the L1 data array would be wasted work.
+__device__ __forceinline__ uint4 ld_stream_na(const uint8_t* ptr) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(ptr));
+  return v;
+}
+
 struct alignas(16) ZonalWarpSmem {
   float4 t[4 * 16 * 8];  // 8 KB transpose buffer
   float4 w[16 * 8];      // 2 KB weights (kw_u, dw_u, kw_u+1, dw_u+1) per column
@@ -168,7 +181,8 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
   extern __shared__ __align__(16) unsigned char zsmem[];
   ZonalWarpSmem* smem = reinterpret_cast<ZonalWarpSmem*>(zsmem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int p = lane >> 3, j = lane & 7;
+  const int p = lane & 3, j = lane >> 2;
+  const int sw = 2 * p;  // line swizzle, without its column bit
   float4* buf = smem[warp].t;
   float4* wsm = smem[warp].w;
   const long long nwarps = (long long)gridDim.x * kWarps;
@@ -205,12 +219,12 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
   auto load = [&](const TileRef& ref, uint4& a0, uint4& a1, uint4& b0, uint4& b1) {
     a0 = a1 = b0 = b1 = make_uint4(0, 0, 0, 0);
     if (p < ref.nb) {
-      a0 = __ldcs(reinterpret_cast<const uint4*>(ref.src));
-      a1 = __ldcs(reinterpret_cast<const uint4*>(ref.src + ref.src_pitch));
+      a0 = ld_stream_na(ref.src);
+      a1 = ld_stream_na(ref.src + ref.src_pitch);
     }
     if (p + 4 < ref.nb) {
-      b0 = __ldcs(reinterpret_cast<const uint4*>(ref.src + 64));
-      b1 = __ldcs(reinterpret_cast<const uint4*>(ref.src + 64 + ref.src_pitch));
+      b0 = ld_stream_na(ref.src + 64);
+      b1 = ld_stream_na(ref.src + 64 + ref.src_pitch);
     }
   };
 
@@ -273,7 +287,7 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
         // row 0 of T sums all 16 inputs: remove 16 * 2^23 (exact)
         rv[0] = bsub(rv[0], make_float2(134217728.0f, 134217728.0f));
 #pragma unroll
-        for (int k = 0; k < 16; ++k) half[2 * ((p * 16 + k) * 8 + (j ^ ((k >> 1) & 7))) + tr] = rv[k];
+        for (int k = 0; k < 16; ++k) half[2 * ((p * 16 + k) * 8 + (j ^ sw ^ ((k >> 1) & 1))) + tr] = rv[k];
       }
     }
     __syncwarp();
@@ -288,7 +302,7 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
       float2 cv[16], y[16];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const float4 v = buf[line * 8 + (q ^ j)];
+        const float4 v = buf[line * 8 + (q ^ sw ^ (j & 1))];
         cv[2 * q] = make_float2(v.x, v.y);
         cv[2 * q + 1] = make_float2(v.z, v.w);
       }
@@ -306,20 +320,23 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
       inv16(y, uo);
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        buf[line * 8 + (q ^ j)] = make_float4(uo[2 * q].x, uo[2 * q].y, uo[2 * q + 1].x, uo[2 * q + 1].y);
+        buf[line * 8 + (q ^ sw ^ (j & 1))] = make_float4(uo[2 * q].x, uo[2 * q].y, uo[2 * q + 1].x, uo[2 * q + 1].y);
     }
     __syncwarp();
 
-    // ---- per row 2j + t: gather the row, inverse row pass -> exact Z,
-    // round half to even, clamp, pack, store
+    // ---- per row 2j + rr: gather the row (8-byte halves of the chunks),
+    // inverse row pass -> exact Z, round half to even, clamp, pack, store.
+    // Lanes with odd j >> 1 take their two rows in the opposite order: the
+    // lanes of a half-warp that meet on a chunk position then read its two
+    // different halves (conflict-free), while a quarter-warp still stores
+    // two whole 64-byte row segments.
 #pragma unroll
     for (int tr = 0; tr < 2; ++tr) {
+      const int rr = tr ^ ((j >> 1) & 1);
+      const float2* half = reinterpret_cast<const float2*>(buf) + rr;
       float2 v[16], z[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const float4 q4 = buf[(p * 16 + c) * 8 + (j ^ ((c >> 1) & 7))];
-        v[c] = tr ? make_float2(q4.z, q4.w) : make_float2(q4.x, q4.y);
-      }
+      for (int c = 0; c < 16; ++c) v[c] = half[2 * ((p * 16 + c) * 8 + (j ^ sw ^ ((c >> 1) & 1)))];
       inv16(v, z);
       unsigned oa[4], ob[4];
 #pragma unroll
@@ -334,7 +351,7 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
         oa[g] = pack_u8(qa[1], qa[0], pack_u8(qa[3], qa[2], 0u));
         ob[g] = pack_u8(qb[1], qb[0], pack_u8(qb[3], qb[2], 0u));
       }
-      uint8_t* d = cur.dst + tr * cur.dst_pitch;
+      uint8_t* d = cur.dst + rr * cur.dst_pitch;
       if (va) __stcs(reinterpret_cast<uint4*>(d), make_uint4(oa[0], oa[1], oa[2], oa[3]));
       if (vb) __stcs(reinterpret_cast<uint4*>(d + 64), make_uint4(ob[0], ob[1], ob[2], ob[3]));
     }
