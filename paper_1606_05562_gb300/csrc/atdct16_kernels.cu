@@ -42,6 +42,13 @@ __device__ __forceinline__ float u8_scaled(unsigned w, int k) {
   return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7404u | ((unsigned)k << 4)));
 }
 
+// SwarRow word (fields f_lo, f_hi, each value + 4096 < 2^13) -> the exact
+// floats 2^23 + 256 f = 2^23 + 2^20 + 256 value, one byte permute each.
+__device__ __forceinline__ float2 swar_row_f2(unsigned w) {
+  return make_float2(__uint_as_float(__byte_perm(w, 0x00004B00u, 0x5104u)),
+                     __uint_as_float(__byte_perm(w, 0x00004B00u, 0x5324u)));
+}
+
 // d = (c << 16) | (sat_u8(a) << 8) | sat_u8(b)   (PTX cvt.pack semantics)
 __device__ __forceinline__ unsigned pack_u8(unsigned a, unsigned b, unsigned c) {
   unsigned d;
@@ -141,15 +148,41 @@ __device__ __forceinline__ float warp_sum(float v) {
 // S^2 scaling, inverse, round, store u8, per-tile SSE (Sec. 4 procedure).
 //
 // Lane (p, j) = (lane & 3, lane >> 2) owns rows 2j, 2j+1 of blocks p and
-// p + 4 of a 16 x 128 tile (the two blocks ride in the halves of an f32x2),
-// so each quarter-warp touches two 64-byte row segments per global access.
-// Shared memory per warp: the transpose buffer (line p*16 + c = column c of
-// block pair p, slot = row pair, 16-byte chunks XOR-swizzled by
-// 2p ^ ((c >> 1) & 1)) and a copy of the weight table of the warp's current
-// r.  The back-transpose uses the same line-per-column layout, so a lane only
-// overwrites the two lines it alone has read.  The next tile's input rows
-// are loaded while the current tile is computed.
+// p + 4 of a 16 x 128 tile (the two blocks ride in the two halves of each
+// register), so each quarter-warp touches two 64-byte row segments per
+// global access.
+//
+// The forward row pass is exact integer work on 8-bit inputs: it runs on
+// the integer pipe, two blocks per 32-bit word (SwarRow, 13-bit fields),
+// and its outputs go through shared memory at 4 bytes per pair.  A byte
+// permute turns a field into the float 2^23 + 2^20 + 256 v, on which the
+// FP32 column pass is exact; the offsets cancel in every output but the
+// DC one, where 16 (2^23 + 2^20) is subtracted.  The rest runs on f32x2.
+//
+// Shared memory per warp, in 16-byte units (padded, so that every access is
+// a per-lane base plus a compile-time offset, and conflict-free):
+//   back-transpose   unit(p, c, q) = 138 p + 8 c + (c >> 1) + q: rows 2q,
+//                    2q+1 of column c of block pair p (549 units);
+//   forward transpose: the chunk with columns 2cc, 2cc+1 of rows 2q, 2q+1
+//                    sits at unit(p, 2cc + (1 ^ ((cc >> 1) & 1)), q), in the
+//                    line of the column that its only reader, lane (p, cc),
+//                    writes last, after it has read the whole chunk;
+//   weights          unit(c, h) = 549 + 9 c + h (143 units).
+// The next tile's input rows are loaded while the current tile is computed.
 // --------------------------------------------------------------------------
+constexpr int kZT2Units = 549;
+constexpr int kZWUnits = 143;
+constexpr int kZonalWarpSmemBytes = 16 * (kZT2Units + kZWUnits);
+
+struct ZonalTile {
+  const uint8_t* src;  // row 2j of block p of this lane
+  uint8_t* dst;
+  int src_pitch, dst_pitch;
+  int nb;              // valid 16-pixel blocks in the tile (1..8)
+  int t;               // tile index
+  int r;
+};
+
 // 16-byte read-only streaming load that does not allocate in L1: the input
 // is read exactly once, so a fill of the L1 data array would be wasted work.
 __device__ __forceinline__ uint4 ld_stream_na(const uint8_t* ptr) {
@@ -160,157 +193,168 @@ __device__ __forceinline__ uint4 ld_stream_na(const uint8_t* ptr) {
   return v;
 }
 
-struct alignas(16) ZonalWarpSmem {
-  float4 t[4 * 16 * 8];  // 8 KB transpose buffer
-  float4 w[16 * 8];      // 2 KB weights (kw_u, dw_u, kw_u+1, dw_u+1) per column
-};
-
-struct TileRef {
-  const uint8_t* src;  // row 2j of block A of this lane
-  uint8_t* dst;
-  long long t;
-  int src_pitch, dst_pitch;  // bytes (host checks they fit in 31 bits)
-  int r;
-  int nb;
-};
-
 template <int kWarps, bool kPrefetch>
-__global__ void __launch_bounds__(32 * kWarps, 16 / kWarps)
-zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
+__global__ void __launch_bounds__(32 * kWarps, 12 / kWarps)
+zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
              const float2* __restrict__ wtab, float* __restrict__ tile_sse, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char zsmem[];
-  ZonalWarpSmem* smem = reinterpret_cast<ZonalWarpSmem*>(zsmem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int p = lane & 3, j = lane >> 2;
-  const int sw = 2 * p;  // line swizzle, without its column bit
-  float4* buf = smem[warp].t;
-  float4* wsm = smem[warp].w;
-  const long long nwarps = (long long)gridDim.x * kWarps;
+  const int p = lane & 3, j = lane >> 2, jb1 = (j >> 1) & 1;
+  float4* const t2 = reinterpret_cast<float4*>(zsmem + warp * kZonalWarpSmemBytes);
+  float4* const wsm = t2 + kZT2Units;
+  const int ntiles = (int)ntiles_ll;  // the launcher checks ntiles < 2^31
 
-  int job = -1;
-  long long jb = 0, je = 0;
-  // Locate tile t: warp-uniform job lookup and this lane's row pointers.  The
-  // descriptor is re-read (it stays in L1) instead of being kept in registers.
-  auto locate = [&](long long t, TileRef& ref) -> bool {
-    if (t < jb || t >= je) {
-      warp_find_job(jobs, njobs, t, job);
-      jb = __ldg(&jobs[job].tile_begin);
-      je = jb + (long long)__ldg(&jobs[job].tiles_x) * (__ldg(&jobs[job].height) >> 4);
-      if (t < jb || t >= je) return false;
-    }
+  // Each warp takes a contiguous range of tiles and walks it with a cursor:
+  // one job lookup per image, then the tile column/band advance by addition.
+  const int nwarps = gridDim.x * kWarps;
+  const int per_warp = (ntiles + nwarps - 1) / nwarps;
+  const int t_first = (blockIdx.x * kWarps + warp) * per_warp;
+  const int t_stop = min(ntiles, t_first + per_warp);
+  if (t_first >= t_stop) return;
+
+  int c_t = 0, c_end = 0, tiles_x = 1, tx = 0, nb_last = 8, r_job = 0, src_pitch = 0, dst_pitch = 0;
+  const uint8_t* src_band = nullptr;  // this lane's row 2j of block p in tile column 0 of the band
+  uint8_t* dst_band = nullptr;
+  auto enter = [&](int t) -> bool {   // place the cursor on tile t
+    int job;
+    warp_find_job(jobs, njobs, t, job);
     const ImageJob* J = jobs + job;
-    const int tiles_x = __ldg(&J->tiles_x);
-    const long long lt = t - jb;
-    const int ty = (int)(lt / tiles_x);
-    const int tx = (int)(lt - (long long)ty * tiles_x);
-    const int x0 = tx * kTileW;
-    const long long row = (long long)(ty * kTileH + 2 * j);
-    ref.src_pitch = (int)__ldg(&J->src_pitch);
-    ref.dst_pitch = (int)__ldg(&J->dst_pitch);
-    ref.src = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->src))) +
-              row * ref.src_pitch + x0 + 16 * p;
-    ref.dst = reinterpret_cast<uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->dst))) +
-              row * ref.dst_pitch + x0 + 16 * p;
-    ref.t = t;
-    ref.r = __ldg(&J->param);
-    ref.nb = min(8, (__ldg(&J->width) - x0) >> 4);
+    const long long tb = __ldg(&J->tile_begin);
+    tiles_x = __ldg(&J->tiles_x);
+    const long long te = tb + (long long)tiles_x * (__ldg(&J->height) >> 4);
+    if (t < tb || t >= te || tiles_x < 1) return false;
+    c_end = (int)min(te, (long long)t_stop);
+    const int lt = (int)(t - tb);
+    const int ty = lt / tiles_x;
+    tx = lt - ty * tiles_x;
+    src_pitch = (int)__ldg(&J->src_pitch);
+    dst_pitch = (int)__ldg(&J->dst_pitch);
+    const long long row = (long long)ty * kTileH + 2 * j;
+    src_band = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->src))) +
+               row * src_pitch + 16 * p;
+    dst_band = reinterpret_cast<uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->dst))) +
+               row * dst_pitch + 16 * p;
+    nb_last = min(8, (__ldg(&J->width) - (tiles_x - 1) * kTileW) >> 4);
+    r_job = __ldg(&J->param);
+    c_t = t;
     return true;
   };
-  auto load = [&](const TileRef& ref, uint4& a0, uint4& a1, uint4& b0, uint4& b1) {
-    a0 = a1 = b0 = b1 = make_uint4(0, 0, 0, 0);
-    if (p < ref.nb) {
-      a0 = ld_stream_na(ref.src);
-      a1 = ld_stream_na(ref.src + ref.src_pitch);
+  auto take = [&](ZonalTile& z) {     // the cursor's tile
+    z.src = src_band + tx * kTileW;
+    z.dst = dst_band + tx * kTileW;
+    z.src_pitch = src_pitch;
+    z.dst_pitch = dst_pitch;
+    z.nb = tx == tiles_x - 1 ? nb_last : 8;
+    z.t = c_t;
+    z.r = r_job;
+  };
+  auto advance = [&]() -> bool {      // false: the job table does not cover the next tile
+    ++c_t;
+    if (++tx == tiles_x) {
+      tx = 0;
+      src_band += (long long)kTileH * src_pitch;
+      dst_band += (long long)kTileH * dst_pitch;
     }
-    if (p + 4 < ref.nb) {
-      b0 = ld_stream_na(ref.src + 64);
-      b1 = ld_stream_na(ref.src + 64 + ref.src_pitch);
+    return c_t >= t_stop || c_t < c_end || enter(c_t);
+  };
+  auto load = [&](const ZonalTile& z, uint4& a0, uint4& a1, uint4& b0, uint4& b1) {
+    a0 = a1 = b0 = b1 = make_uint4(0, 0, 0, 0);
+    if (p < z.nb) {
+      a0 = ld_stream_na(z.src);
+      a1 = ld_stream_na(z.src + z.src_pitch);
+    }
+    if (p + 4 < z.nb) {
+      b0 = ld_stream_na(z.src + 64);
+      b1 = ld_stream_na(z.src + 64 + z.src_pitch);
     }
   };
 
-  // Each warp takes a contiguous range of tiles, so consecutive tiles of a
-  // warp mostly belong to the same image (one descriptor lookup, one weight
-  // refresh per image rather than per tile).
-  const long long per_warp = (ntiles + nwarps - 1) / nwarps;
-  const long long gw = (long long)blockIdx.x * kWarps + warp;
-  const long long t_end = min(ntiles, (gw + 1) * per_warp);
-  long long t = gw * per_warp;
-  TileRef cur;
-  uint4 a0, a1, b0, b1;
-  while (t < t_end && !locate(t, cur)) {
+  if (!enter(t_first)) {
     if (lane == 0) set_status(status, kDevBadJob);
-    ++t;
+    return;
   }
-  if (t >= t_end) return;
-  load(cur, a0, a1, b0, b1);
   int wr = -1;  // r whose weights are in wsm
+  bool ok = true;
 
-  while (true) {
-    // ---- prefetch the next tile
-    long long tn = cur.t + 1;
-    TileRef nxt;
-    bool have_next = false;
-    while (tn < t_end) {
-      if (locate(tn, nxt)) { have_next = true; break; }
-      if (lane == 0) set_status(status, kDevBadJob);
-      ++tn;
-    }
-    uint4 na0, na1, nb0, nb1;
-    if (kPrefetch && have_next) load(nxt, na0, na1, nb0, nb1);
-
+  // One tile: X holds its input rows (a0, a1, b0, b1).  Once the row pass
+  // has consumed them, X receives the rows of the tile after the next one,
+  // so each load has about two tile times to land.  Returns whether cur now
+  // names that later tile.
+  auto process = [&](ZonalTile& cur, uint4 (&X)[4]) -> bool {
+    if (!kPrefetch) load(cur, X[0], X[1], X[2], X[3]);
     const bool va = p < cur.nb, vb = p + 4 < cur.nb;
     if (cur.r != wr) {  // warp-uniform: refresh the weight copy
       __syncwarp();
       const float4* src = reinterpret_cast<const float4*>(wtab) + (long long)cur.r * 128;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int g = lane * 4 + q, c = g >> 3, h = g & 7;
-        wsm[c * 8 + (h ^ ((c >> 1) & 7))] = __ldg(src + g);
+        const int g = lane * 4 + q;
+        wsm[9 * (g >> 3) + (g & 7)] = __ldg(src + g);
       }
       __syncwarp();
       wr = cur.r;
     }
 
-    // ---- row pass (Sec. 2 factorisation) on 2^23 + 256 x, one image row at
-    // a time; each row fills one half of its 16-byte chunks
+    // ---- row pass (Sec. 2 factorisation), exact, in SwarRow words: field
+    // lo = block p, hi = block p + 4
     {
-      float2* half = reinterpret_cast<float2*>(buf);
+      SwarRow rv[2][16];
 #pragma unroll
       for (int tr = 0; tr < 2; ++tr) {
-        const uint4& wa = tr ? a1 : a0;
-        const uint4& wb = tr ? b1 : b0;
-        float2 xv[16], rv[16];
+        const uint4& wa = X[tr];
+        const uint4& wb = X[2 + tr];
+        SwarRow xs[16];
 #pragma unroll
-        for (int n = 0; n < 16; ++n)
-          xv[n] = make_float2(u8_scaled(word_of(wa, n >> 2), n & 3), u8_scaled(word_of(wb, n >> 2), n & 3));
-        fwd16(xv, rv);
-        // row 0 of T sums all 16 inputs: remove 16 * 2^23 (exact)
-        rv[0] = bsub(rv[0], make_float2(134217728.0f, 134217728.0f));
-#pragma unroll
-        for (int k = 0; k < 16; ++k) half[2 * ((p * 16 + k) * 8 + (j ^ sw ^ ((k >> 1) & 1))) + tr] = rv[k];
+        for (int w = 0; w < 4; ++w) {
+          const unsigned lo = __byte_perm(word_of(wa, w), word_of(wb, w), 0x5410u);  // a0 a1 b0 b1
+          const unsigned hi = __byte_perm(word_of(wa, w), word_of(wb, w), 0x7632u);  // a2 a3 b2 b3
+          xs[4 * w + 0].v = (lo & 0x00FF00FFu) | kSwarRowBias;
+          xs[4 * w + 1].v = __byte_perm(lo, kSwarRowBias, 0x7351u);
+          xs[4 * w + 2].v = (hi & 0x00FF00FFu) | kSwarRowBias;
+          xs[4 * w + 3].v = __byte_perm(hi, kSwarRowBias, 0x7351u);
+        }
+        fwd16(xs, rv[tr]);
       }
+      uint4* const t1w = reinterpret_cast<uint4*>(t2 + 138 * p + j);
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc)
+        t1w[17 * cc + 8 * (1 ^ ((cc >> 1) & 1))] =
+            make_uint4(rv[0][2 * cc].v, rv[1][2 * cc].v, rv[0][2 * cc + 1].v, rv[1][2 * cc + 1].v);
     }
     __syncwarp();
 
+    ZonalTile fut;
+    const bool have_fut = ok && c_t < t_stop;
+    if (have_fut) {
+      take(fut);
+      ok = advance();
+      if (kPrefetch) load(fut, X[0], X[1], X[2], X[3]);
+    }
+
     // ---- per column c = 2j + i: column pass (y = 256 Y, exact), zonal mask
-    // and S^2 weights, dropped energy (Parseval), inverse column pass; the
-    // result goes back into the same line of the buffer.
+    // and S^2 weights, dropped energy (Parseval), inverse column pass into
+    // the back-transpose.  Lanes with odd j >> 1 take their two columns in
+    // the opposite order, so the 8-byte reads of the forward transpose are
+    // conflict-free; each lane's forward chunks sit in the line it writes last.
     float2 acc = make_float2(0.f, 0.f);
+    const uint2* const t1r = reinterpret_cast<const uint2*>(t2 + 138 * p + 17 * j + 8 * (1 ^ jb1));
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int line = p * 16 + 2 * j + i;
+    for (int ii = 0; ii < 2; ++ii) {
+      const int i = ii ^ jb1;
       float2 cv[16], y[16];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const float4 v = buf[line * 8 + (q ^ sw ^ (j & 1))];
-        cv[2 * q] = make_float2(v.x, v.y);
-        cv[2 * q + 1] = make_float2(v.z, v.w);
+        const uint2 v = t1r[2 * q + i];
+        cv[2 * q] = swar_row_f2(v.x);
+        cv[2 * q + 1] = swar_row_f2(v.y);
       }
       fwd16(cv, y);
-      const int wc = (2 * j + i) * 8;
+      // every input carries 2^23 + 2^20; only the DC row sums them
+      y[0] = bsub(y[0], make_float2(150994944.0f, 150994944.0f));
+      const float4* const wcol = wsm + 9 * (2 * j + i);
 #pragma unroll
       for (int h = 0; h < 8; ++h) {
-        const float4 w = wsm[wc + (h ^ j)];
+        const float4 w = wcol[h];
         acc = __ffma2_rn(f2mul(y[2 * h], w.y), y[2 * h], acc);
         acc = __ffma2_rn(f2mul(y[2 * h + 1], w.w), y[2 * h + 1], acc);
         y[2 * h] = f2mul(y[2 * h], w.x);
@@ -318,9 +362,10 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
       }
       float2 uo[16];
       inv16(y, uo);
+      float4* const t2w = t2 + 138 * p + 17 * j + 8 * i;
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        buf[line * 8 + (q ^ sw ^ (j & 1))] = make_float4(uo[2 * q].x, uo[2 * q].y, uo[2 * q + 1].x, uo[2 * q + 1].y);
+        t2w[q] = make_float4(uo[2 * q].x, uo[2 * q].y, uo[2 * q + 1].x, uo[2 * q + 1].y);
     }
     __syncwarp();
 
@@ -332,11 +377,11 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
     // two whole 64-byte row segments.
 #pragma unroll
     for (int tr = 0; tr < 2; ++tr) {
-      const int rr = tr ^ ((j >> 1) & 1);
-      const float2* half = reinterpret_cast<const float2*>(buf) + rr;
+      const int rr = tr ^ jb1;
+      const float2* const fin = reinterpret_cast<const float2*>(t2 + 138 * p + j) + rr;
       float2 v[16], z[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) v[c] = half[2 * ((p * 16 + c) * 8 + (j ^ sw ^ ((c >> 1) & 1)))];
+      for (int c = 0; c < 16; ++c) v[c] = fin[2 * (8 * c + (c >> 1))];
       inv16(v, z);
       unsigned oa[4], ob[4];
 #pragma unroll
@@ -361,15 +406,39 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
     if (lane == 0) tile_sse[cur.t] = tot * (1.0f / (256.0f * 2304.0f));
     __syncwarp();  // buffer reads done before the next tile's writes
 
-    if (!have_next) break;
-    cur = nxt;
-    if (kPrefetch) {
-      a0 = na0; a1 = na1; b0 = nb0; b1 = nb1;
-    } else {
-      load(cur, a0, a1, b0, b1);
-    }
+    if (have_fut) cur = fut;
+    return have_fut;
+  };
+
+  ZonalTile ta, tb;
+  uint4 xa[4], xb[4];
+  take(ta);
+  ok = advance();
+  if (kPrefetch) load(ta, xa[0], xa[1], xa[2], xa[3]);
+  bool more_b = ok && c_t < t_stop;
+  if (more_b) {
+    take(tb);
+    ok = advance();
+    if (kPrefetch) load(tb, xb[0], xb[1], xb[2], xb[3]);
   }
+  // Two copies of the tile body with the register sets swapped: no copy of
+  // a register that still has a load in flight.
+  bool more_a = true;
+  do {
+    if (more_a) more_a = process(ta, xa);
+    if (more_b) more_b = process(tb, xb);
+  } while (more_a || more_b);
+  if (!ok && lane == 0) set_status(status, kDevBadJob);
 }
+
+struct TileRef {
+  const uint8_t* src;  // row 2j of block A of this lane
+  uint8_t* dst;
+  long long t;
+  int src_pitch, dst_pitch;  // bytes (host checks they fit in 31 bits)
+  int r;
+  int nb;
+};
 
 // --------------------------------------------------------------------------
 // Fused zonal compression with the forward transform in 16-bit SWAR lanes.
@@ -983,19 +1052,20 @@ cudaError_t launch_zonal_config(const ZonalConfig& cfg, const ImageJob* d_jobs, 
                                 const float2* d_wtab, float* d_tile_sse, int* d_status, int grid,
                                 cudaStream_t stream) {
   if (ntiles <= 0) return cudaSuccess;
+  if (ntiles >= (1LL << 30)) return cudaErrorInvalidValue;  // tile indices are 32-bit in the kernels
   const int threads = 32 * cfg.warps;
   switch (config_index(cfg)) {
     case 0:
-      return launch_with_smem(zonal_f32_kernel<2, true>, grid, threads, 2 * (int)sizeof(ZonalWarpSmem), stream,
+      return launch_with_smem(zonal_f32_kernel<2, true>, grid, threads, 2 * kZonalWarpSmemBytes, stream,
                               d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
     case 1:
-      return launch_with_smem(zonal_f32_kernel<4, true>, grid, threads, 4 * (int)sizeof(ZonalWarpSmem), stream,
+      return launch_with_smem(zonal_f32_kernel<4, true>, grid, threads, 4 * kZonalWarpSmemBytes, stream,
                               d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
     case 2:
-      return launch_with_smem(zonal_f32_kernel<8, true>, grid, threads, 8 * (int)sizeof(ZonalWarpSmem), stream,
+      return launch_with_smem(zonal_f32_kernel<8, true>, grid, threads, 8 * kZonalWarpSmemBytes, stream,
                               d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
     case 3:
-      return launch_with_smem(zonal_f32_kernel<4, false>, grid, threads, 4 * (int)sizeof(ZonalWarpSmem), stream,
+      return launch_with_smem(zonal_f32_kernel<4, false>, grid, threads, 4 * kZonalWarpSmemBytes, stream,
                               d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
     case 4:
       return launch_with_smem(zonal_swar_kernel<4>, grid, threads, 4 * kSwarWarpSmem, stream, d_jobs, njobs,
@@ -1004,29 +1074,25 @@ cudaError_t launch_zonal_config(const ZonalConfig& cfg, const ImageJob* d_jobs, 
   return cudaErrorInvalidValue;
 }
 
+template <class K>
+static cudaError_t occupancy_with_smem(int* n, K kernel, int threads, int smem) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kernel, threads, smem);
+}
+
 int zonal_config_max_ctas_per_sm(const ZonalConfig& cfg) {
   int n = 0;
   cudaError_t e = cudaErrorInvalidValue;
+  const int zs = kZonalWarpSmemBytes;
   switch (config_index(cfg)) {
-    case 0:
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_f32_kernel<2, true>, 64, 2 * sizeof(ZonalWarpSmem));
-      break;
-    case 1:
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_f32_kernel<4, true>, 128, 4 * sizeof(ZonalWarpSmem));
-      break;
-    case 2:
-      cudaFuncSetAttribute(zonal_f32_kernel<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           8 * (int)sizeof(ZonalWarpSmem));
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_f32_kernel<8, true>, 256, 8 * sizeof(ZonalWarpSmem));
-      break;
-    case 3:
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_f32_kernel<4, false>, 128,
-                                                        4 * sizeof(ZonalWarpSmem));
-      break;
-    case 4:
-      cudaFuncSetAttribute(zonal_swar_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kSwarWarpSmem);
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_swar_kernel<4>, 128, 4 * kSwarWarpSmem);
-      break;
+    case 0: e = occupancy_with_smem(&n, zonal_f32_kernel<2, true>, 64, 2 * zs); break;
+    case 1: e = occupancy_with_smem(&n, zonal_f32_kernel<4, true>, 128, 4 * zs); break;
+    case 2: e = occupancy_with_smem(&n, zonal_f32_kernel<8, true>, 256, 8 * zs); break;
+    case 3: e = occupancy_with_smem(&n, zonal_f32_kernel<4, false>, 128, 4 * zs); break;
+    case 4: e = occupancy_with_smem(&n, zonal_swar_kernel<4>, 128, 4 * kSwarWarpSmem); break;
   }
   return (e == cudaSuccess && n > 0) ? n : 1;
 }
