@@ -172,7 +172,8 @@ __device__ __forceinline__ float warp_sum(float v) {
 // --------------------------------------------------------------------------
 constexpr int kZT2Units = 549;
 constexpr int kZWUnits = 143;
-constexpr int kZonalWarpSmemBytes = 16 * (kZT2Units + kZWUnits);
+constexpr int kZStageUnits = 2 * 4 * 32;  // two tiles of input rows, 4 x 16 bytes per lane
+constexpr int kZonalWarpSmemBytes = 16 * (kZT2Units + kZWUnits + kZStageUnits);
 
 struct ZonalTile {
   const uint8_t* src;  // row 2j of block p of this lane
@@ -193,6 +194,16 @@ __device__ __forceinline__ uint4 ld_stream_na(const uint8_t* ptr) {
   return v;
 }
 
+// Asynchronous 16-byte global -> shared copy (L2 only), its group commit and
+// the wait until at most N of this thread's groups are still in flight.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <int kWarps, bool kPrefetch>
 __global__ void __launch_bounds__(32 * kWarps, 12 / kWarps)
 zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
@@ -202,6 +213,7 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
   const int p = lane & 3, j = lane >> 2, jb1 = (j >> 1) & 1;
   float4* const t2 = reinterpret_cast<float4*>(zsmem + warp * kZonalWarpSmemBytes);
   float4* const wsm = t2 + kZT2Units;
+  uint4* const stg = reinterpret_cast<uint4*>(wsm + kZWUnits) + lane;  // + 128 s + 32 k
   const int ntiles = (int)ntiles_ll;  // the launcher checks ntiles < 2^31
 
   // Each warp takes a contiguous range of tiles and walks it with a cursor:
@@ -257,16 +269,21 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     }
     return c_t >= t_stop || c_t < c_end || enter(c_t);
   };
-  auto load = [&](const ZonalTile& z, uint4& a0, uint4& a1, uint4& b0, uint4& b1) {
-    a0 = a1 = b0 = b1 = make_uint4(0, 0, 0, 0);
+  // Input rows of tile z into staging slot st: word k = row 2j + (k & 1) of
+  // block p + 4 (k >> 1).  Each lane reads back only what it copied itself.
+  // Blocks past the image edge are not copied; their stale words are finite
+  // bytes whose results are never stored.
+  auto issue = [&](const ZonalTile& z, int st) {
+    uint4* d = stg + 128 * st;
     if (p < z.nb) {
-      a0 = ld_stream_na(z.src);
-      a1 = ld_stream_na(z.src + z.src_pitch);
+      cp_async16(d, z.src);
+      cp_async16(d + 32, z.src + z.src_pitch);
     }
     if (p + 4 < z.nb) {
-      b0 = ld_stream_na(z.src + 64);
-      b1 = ld_stream_na(z.src + 64 + z.src_pitch);
+      cp_async16(d + 64, z.src + 64);
+      cp_async16(d + 96, z.src + 64 + z.src_pitch);
     }
+    cp_async_commit();
   };
 
   if (!enter(t_first)) {
@@ -280,8 +297,25 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
   // has consumed them, X receives the rows of the tile after the next one,
   // so each load has about two tile times to land.  Returns whether cur now
   // names that later tile.
-  auto process = [&](ZonalTile& cur, uint4 (&X)[4]) -> bool {
-    if (!kPrefetch) load(cur, X[0], X[1], X[2], X[3]);
+  ZonalTile cur, nxt;
+  take(cur);
+  ok = advance();
+  issue(cur, 0);
+  bool have_nxt = kPrefetch && ok && c_t < t_stop;
+  if (have_nxt) {
+    take(nxt);
+    ok = advance();
+    issue(nxt, 1);
+  } else {
+    cp_async_commit();
+  }
+  int st = 0;
+  while (true) {
+    // ---- this tile's input rows (copied one or two tile times ago)
+    cp_async_wait<1>();
+    uint4 X[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) X[k] = stg[128 * st + 32 * k];
     const bool va = p < cur.nb, vb = p + 4 < cur.nb;
     if (cur.r != wr) {  // warp-uniform: refresh the weight copy
       __syncwarp();
@@ -323,12 +357,16 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     }
     __syncwarp();
 
+    // ---- the input rows of the tile after the next one, into the slot
+    // that X came from (X is consumed)
     ZonalTile fut;
-    const bool have_fut = ok && c_t < t_stop;
+    const bool have_fut = have_nxt && ok && c_t < t_stop;
     if (have_fut) {
       take(fut);
       ok = advance();
-      if (kPrefetch) load(fut, X[0], X[1], X[2], X[3]);
+      issue(fut, st);
+    } else {
+      cp_async_commit();
     }
 
     // ---- per column c = 2j + i: column pass (y = 256 Y, exact), zonal mask
@@ -406,28 +444,21 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     if (lane == 0) tile_sse[cur.t] = tot * (1.0f / (256.0f * 2304.0f));
     __syncwarp();  // buffer reads done before the next tile's writes
 
-    if (have_fut) cur = fut;
-    return have_fut;
-  };
-
-  ZonalTile ta, tb;
-  uint4 xa[4], xb[4];
-  take(ta);
-  ok = advance();
-  if (kPrefetch) load(ta, xa[0], xa[1], xa[2], xa[3]);
-  bool more_b = ok && c_t < t_stop;
-  if (more_b) {
-    take(tb);
-    ok = advance();
-    if (kPrefetch) load(tb, xb[0], xb[1], xb[2], xb[3]);
+    if (!kPrefetch) {  // no look-ahead: the next tile is fetched only now
+      if (!(ok && c_t < t_stop)) break;
+      take(cur);
+      ok = advance();
+      issue(cur, 0);
+      cp_async_commit();
+      continue;
+    }
+    if (!have_nxt) break;
+    cur = nxt;
+    nxt = fut;
+    have_nxt = have_fut;
+    st ^= 1;
   }
-  // Two copies of the tile body with the register sets swapped: no copy of
-  // a register that still has a load in flight.
-  bool more_a = true;
-  do {
-    if (more_a) more_a = process(ta, xa);
-    if (more_b) more_b = process(tb, xb);
-  } while (more_a || more_b);
+  cp_async_wait<0>();
   if (!ok && lane == 0) set_status(status, kDevBadJob);
 }
 
