@@ -42,11 +42,11 @@ __device__ __forceinline__ float u8_scaled(unsigned w, int k) {
   return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7404u | ((unsigned)k << 4)));
 }
 
-// SwarRow word (fields f_lo, f_hi, each value + 4096 < 2^13) -> the exact
-// floats 2^23 + 256 f = 2^23 + 2^20 + 256 value, one byte permute each.
-__device__ __forceinline__ float2 swar_row_f2(unsigned w) {
-  return make_float2(__uint_as_float(__byte_perm(w, 0x00004B00u, 0x5104u)),
-                     __uint_as_float(__byte_perm(w, 0x00004B00u, 0x5324u)));
+// Swar16 word (fields f_lo, f_hi < 2^16) -> the exact floats 2^23 + f, one
+// byte permute each.
+__device__ __forceinline__ float2 swar16_f2(unsigned w) {
+  return make_float2(__uint_as_float(__byte_perm(w, 0x00004B00u, 0x5410u)),
+                     __uint_as_float(__byte_perm(w, 0x00004B00u, 0x5432u)));
 }
 
 // d = (c << 16) | (sat_u8(a) << 8) | sat_u8(b)   (PTX cvt.pack semantics)
@@ -152,15 +152,18 @@ __device__ __forceinline__ float warp_sum(float v) {
 // register), so each quarter-warp touches two 64-byte row segments per
 // global access.
 //
-// The forward row pass is exact integer work on 8-bit inputs: it runs on
-// the integer pipe, two blocks per 32-bit word (SwarRow, 13-bit fields),
-// and its outputs go through shared memory at 4 bytes per pair.  A byte
-// permute turns a field into the float 2^23 + 2^20 + 256 v, on which the
-// FP32 column pass is exact; the offsets cancel in every output but the
-// DC one, where 16 (2^23 + 2^20) is subtracted.  The rest runs on f32x2.
+// The forward transform is exact integer work: both passes run on the
+// integer pipe, two blocks per 32-bit word (Swar16, int16 fields, one
+// 3-operand add per butterfly addition).  The row pass's DC output is
+// centred by -2048, which keeps every node of the column pass inside int16
+// (bounds in Sec. 2 arithmetic: |row outputs| <= 4080, column nodes within
+// [-32768, 32640]).  A byte permute and one exact FMA turn each coefficient
+// field into the float 256 Y; the mask, the S^2 weights, the dropped energy
+// and the inverse run on f32x2.
 //
 // Shared memory per warp, in 16-byte units (padded, so that every access is
-// a per-lane base plus a compile-time offset, and conflict-free):
+// a per-lane base plus a compile-time offset, and conflict-free), plus two
+// staging slots for the input rows of the next two tiles:
 //   back-transpose   unit(p, c, q) = 138 p + 8 c + (c >> 1) + q: rows 2q,
 //                    2q+1 of column c of block pair p (549 units);
 //   forward transpose: the chunk with columns 2cc, 2cc+1 of rows 2q, 2q+1
@@ -168,7 +171,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 //                    line of the column that its only reader, lane (p, cc),
 //                    writes last, after it has read the whole chunk;
 //   weights          unit(c, h) = 549 + 9 c + h (143 units).
-// The next tile's input rows are loaded while the current tile is computed.
+// The input rows of the tile after next are copied in while a tile is computed.
 // --------------------------------------------------------------------------
 constexpr int kZT2Units = 549;
 constexpr int kZWUnits = 143;
@@ -329,25 +332,27 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
       wr = cur.r;
     }
 
-    // ---- row pass (Sec. 2 factorisation), exact, in SwarRow words: field
-    // lo = block p, hi = block p + 4
+    // ---- row pass (Sec. 2 factorisation), exact, in Swar16 words: field
+    // lo = block p, hi = block p + 4.  The DC output is centred by -2048 so
+    // that the column pass stays inside int16.
     {
-      SwarRow rv[2][16];
+      Swar16 rv[2][16];
 #pragma unroll
       for (int tr = 0; tr < 2; ++tr) {
         const uint4& wa = X[tr];
         const uint4& wb = X[2 + tr];
-        SwarRow xs[16];
+        Swar16 xs[16];
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
           const unsigned lo = __byte_perm(word_of(wa, w), word_of(wb, w), 0x5410u);  // a0 a1 b0 b1
           const unsigned hi = __byte_perm(word_of(wa, w), word_of(wb, w), 0x7632u);  // a2 a3 b2 b3
-          xs[4 * w + 0].v = (lo & 0x00FF00FFu) | kSwarRowBias;
-          xs[4 * w + 1].v = __byte_perm(lo, kSwarRowBias, 0x7351u);
-          xs[4 * w + 2].v = (hi & 0x00FF00FFu) | kSwarRowBias;
-          xs[4 * w + 3].v = __byte_perm(hi, kSwarRowBias, 0x7351u);
+          xs[4 * w + 0].v = (lo & 0x00FF00FFu) | kSwarBias;
+          xs[4 * w + 1].v = __byte_perm(lo, kSwarBias, 0x7351u);
+          xs[4 * w + 2].v = (hi & 0x00FF00FFu) | kSwarBias;
+          xs[4 * w + 3].v = __byte_perm(hi, kSwarBias, 0x7351u);
         }
         fwd16(xs, rv[tr]);
+        rv[tr][0].v -= 0x08000800u;
       }
       uint4* const t1w = reinterpret_cast<uint4*>(t2 + 138 * p + j);
 #pragma unroll
@@ -369,32 +374,40 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
       cp_async_commit();
     }
 
-    // ---- per column c = 2j + i: column pass (y = 256 Y, exact), zonal mask
-    // and S^2 weights, dropped energy (Parseval), inverse column pass into
-    // the back-transpose.  Lanes with odd j >> 1 take their two columns in
+    // ---- per column c = 2j + i: column pass in Swar16 (exact int16), to
+    // y = 256 Y in floats, zonal mask and S^2 weights, dropped energy
+    // (Parseval), inverse column pass into the back-transpose.  Lanes with odd j >> 1 take their two columns in
     // the opposite order, so the 8-byte reads of the forward transpose are
     // conflict-free; each lane's forward chunks sit in the line it writes last.
-    float2 acc = make_float2(0.f, 0.f);
+    float2 acc = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
     const uint2* const t1r = reinterpret_cast<const uint2*>(t2 + 138 * p + 17 * j + 8 * (1 ^ jb1));
 #pragma unroll
     for (int ii = 0; ii < 2; ++ii) {
       const int i = ii ^ jb1;
-      float2 cv[16], y[16];
+      Swar16 cw[16], yw[16];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const uint2 v = t1r[2 * q + i];
-        cv[2 * q] = swar_row_f2(v.x);
-        cv[2 * q + 1] = swar_row_f2(v.y);
+        cw[2 * q].v = v.x;
+        cw[2 * q + 1].v = v.y;
       }
-      fwd16(cv, y);
-      // every input carries 2^23 + 2^20; only the DC row sums them
-      y[0] = bsub(y[0], make_float2(150994944.0f, 150994944.0f));
+      fwd16(cw, yw);
+      // field f -> float 2^23 + f (f = Y + 32768) -> 256 f - 256 (2^23 + 32768)
+      // = 256 Y in one exact FMA; the DC coefficient of column 0 also takes
+      // back the 16 * 2048 of the centring
+      const float dc = (2 * j + i) == 0 ? -2147483648.0f : -2155872256.0f;
+      float2 y[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const float o = u == 0 ? dc : -2155872256.0f;
+        y[u] = __ffma2_rn(swar16_f2(yw[u].v), make_float2(256.0f, 256.0f), make_float2(o, o));
+      }
       const float4* const wcol = wsm + 9 * (2 * j + i);
 #pragma unroll
       for (int h = 0; h < 8; ++h) {
         const float4 w = wcol[h];
         acc = __ffma2_rn(f2mul(y[2 * h], w.y), y[2 * h], acc);
-        acc = __ffma2_rn(f2mul(y[2 * h + 1], w.w), y[2 * h + 1], acc);
+        acc1 = __ffma2_rn(f2mul(y[2 * h + 1], w.w), y[2 * h + 1], acc1);
         y[2 * h] = f2mul(y[2 * h], w.x);
         y[2 * h + 1] = f2mul(y[2 * h + 1], w.z);
       }
@@ -440,6 +453,7 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     }
 
     // ---- tile SSE: dropped energy / (256 * 2304), summed over valid blocks
+    acc = __fadd2_rn(acc, acc1);
     const float tot = warp_sum((va ? acc.x : 0.f) + (vb ? acc.y : 0.f));
     if (lane == 0) tile_sse[cur.t] = tot * (1.0f / (256.0f * 2304.0f));
     __syncwarp();  // buffer reads done before the next tile's writes
