@@ -183,8 +183,8 @@ atdct16_status atdct16_psnr(atdct16_dtype dtype, const void* d_a, int64_t pitch_
  * Resident mixed-size batches (a fixed set of images compressed repeatedly).
  * atdct16_batch_create uploads the descriptors once, sizes the batch's own
  * per-tile partials, optionally autotunes the launch shape of the fused
- * zonal kernel on the batch itself (kernel variant, warps per CTA, prefetch
- * depth and CTAs per SM, i.e. tiles per CTA), and optionally captures the
+ * zonal kernel on the batch itself (kernel variant, warps per CTA and CTAs
+ * per SM, i.e. tiles per CTA), and optionally captures the
  * fused kernel and the PSNR finalize into one CUDA graph.  Each
  * atdct16_batch_launch then re-runs the whole batch (Sec. 4 procedure on
  * every image) with one graph launch.
@@ -205,8 +205,10 @@ atdct16_status atdct16_batch_create(atdct16_plan_t plan, const atdct16_image* h_
                                     atdct16_batch_t* batch);
 /* Re-run the batch on `stream` (asynchronous). */
 atdct16_status atdct16_batch_launch(atdct16_batch_t batch, cudaStream_t stream);
-/* Chosen launch shape: variant (0 FP32, 1 SWAR), warps per CTA, prefetch,
- * grid size, tile count and the tuned time per launch in ms (0 if untuned).
+/* Chosen launch shape: variant (0: column pass in FP32, 1: column pass in
+ * int16 SWAR), warps per CTA, prefetch (always 1: input rows are staged two
+ * tiles ahead), grid size, tile count and the tuned time per launch in ms
+ * (0 if untuned).
  * Any pointer may be NULL. */
 atdct16_status atdct16_batch_info(atdct16_batch_t batch, int32_t* variant, int32_t* warps, int32_t* prefetch,
                                   int32_t* grid, int64_t* tiles, float* tuned_ms);

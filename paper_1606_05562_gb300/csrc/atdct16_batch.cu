@@ -143,7 +143,7 @@ cudaError_t launch_batch_once(atdct16_batch_st* b, const ZonalConfig& cfg, int g
 // Time every candidate launch shape on the batch (min of 3 after a warm-up).
 atdct16_status autotune(atdct16_batch_st* b, int sms, cudaStream_t stream) {
   const ZonalConfig cands[] = {
-      {kZonalF32, 4, 1}, {kZonalF32, 2, 1}, {kZonalF32, 8, 1}, {kZonalF32, 4, 0}, {kZonalSwar, 4, 1},
+      {kZonalSwar, 4, 1}, {kZonalF32, 4, 1},
   };
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return ATDCT16_ECUDA;

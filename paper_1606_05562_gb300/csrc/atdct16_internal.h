@@ -45,8 +45,8 @@ constexpr int kDevBadJob = 1;
 cudaError_t launch_zonal(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
                          float* d_tile_sse, int* d_status, int grid, cudaStream_t stream);
 // Launch shapes of the fused zonal kernel (chosen by the batch autotuner).
-constexpr int kZonalF32 = 0;   // all-FP32 butterflies
-constexpr int kZonalSwar = 1;  // forward transform in 16-bit SWAR lanes
+constexpr int kZonalF32 = 0;   // integer row pass, FP32 column pass and inverse
+constexpr int kZonalSwar = 1;  // whole forward transform on the integer pipe (int16 SWAR)
 struct ZonalConfig {
   int variant;   // kZonalF32 or kZonalSwar
   int warps;     // warps per CTA: 2, 4 or 8 (SWAR: 4)

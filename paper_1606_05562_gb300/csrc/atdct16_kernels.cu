@@ -26,6 +26,8 @@
 #include "atdct16_butterfly.cuh"
 #include "atdct16_internal.h"
 
+#include <type_traits>
+
 namespace atdct16 {
 
 // --------------------------------------------------------------------------
@@ -40,6 +42,13 @@ __device__ __forceinline__ unsigned word_of(const uint4& v, int i) {
 // 2^23 + 256 * (byte k of w): exact float built by one byte permute.
 __device__ __forceinline__ float u8_scaled(unsigned w, int k) {
   return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7404u | ((unsigned)k << 4)));
+}
+
+// SwarRow word (fields f_lo, f_hi, each value + 4096 < 2^13) -> the exact
+// floats 2^23 + 256 f = 2^23 + 2^20 + 256 value, one byte permute each.
+__device__ __forceinline__ float2 swar_row_f2(unsigned w) {
+  return make_float2(__uint_as_float(__byte_perm(w, 0x00004B00u, 0x5104u)),
+                     __uint_as_float(__byte_perm(w, 0x00004B00u, 0x5324u)));
 }
 
 // Swar16 word (fields f_lo, f_hi < 2^16) -> the exact floats 2^23 + f, one
@@ -152,14 +161,15 @@ __device__ __forceinline__ float warp_sum(float v) {
 // register), so each quarter-warp touches two 64-byte row segments per
 // global access.
 //
-// The forward transform is exact integer work: both passes run on the
-// integer pipe, two blocks per 32-bit word (Swar16, int16 fields, one
-// 3-operand add per butterfly addition).  The row pass's DC output is
-// centred by -2048, which keeps every node of the column pass inside int16
-// (bounds in Sec. 2 arithmetic: |row outputs| <= 4080, column nodes within
-// [-32768, 32640]).  A byte permute and one exact FMA turn each coefficient
-// field into the float 256 Y; the mask, the S^2 weights, the dropped energy
-// and the inverse run on f32x2.
+// The forward transform is exact integer work.  The row pass runs on the
+// integer pipe, two blocks per 32-bit word (one 3-operand add per butterfly
+// addition).  The column pass runs either there too (kColSwar: int16
+// fields; the row pass centres its DC output by -2048, which keeps every
+// column node inside int16: |row outputs| <= 4080, column nodes within
+// [-32768, 32640]) and a byte permute plus one exact FMA turn each
+// coefficient field into the float 256 Y; or on f32x2 from 13-bit row
+// fields that a byte permute places into float mantissas.  The mask, the
+// S^2 weights, the dropped energy and the inverse run on f32x2.
 //
 // Shared memory per warp, in 16-byte units (padded, so that every access is
 // a per-lane base plus a compile-time offset, and conflict-free), plus two
@@ -207,7 +217,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int kWarps, bool kPrefetch>
+template <int kWarps, bool kColSwar>
 __global__ void __launch_bounds__(32 * kWarps, 12 / kWarps)
 zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
              const float2* __restrict__ wtab, float* __restrict__ tile_sse, int* __restrict__ status) {
@@ -218,6 +228,10 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
   float4* const wsm = t2 + kZT2Units;
   uint4* const stg = reinterpret_cast<uint4*>(wsm + kZWUnits) + lane;  // + 128 s + 32 k
   const int ntiles = (int)ntiles_ll;  // the launcher checks ntiles < 2^31
+  // row-pass words: 13-bit fields (bias 4096) for a float column pass,
+  // int16 fields (bias 32768) for an integer one
+  using Row = typename std::conditional<kColSwar, Swar16, SwarRow>::type;
+  constexpr unsigned kRowBias = kColSwar ? kSwarBias : kSwarRowBias;
 
   // Each warp takes a contiguous range of tiles and walks it with a cursor:
   // one job lookup per image, then the tile column/band advance by addition.
@@ -296,15 +310,11 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
   int wr = -1;  // r whose weights are in wsm
   bool ok = true;
 
-  // One tile: X holds its input rows (a0, a1, b0, b1).  Once the row pass
-  // has consumed them, X receives the rows of the tile after the next one,
-  // so each load has about two tile times to land.  Returns whether cur now
-  // names that later tile.
   ZonalTile cur, nxt;
   take(cur);
   ok = advance();
   issue(cur, 0);
-  bool have_nxt = kPrefetch && ok && c_t < t_stop;
+  bool have_nxt = ok && c_t < t_stop;
   if (have_nxt) {
     take(nxt);
     ok = advance();
@@ -326,33 +336,31 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int g = lane * 4 + q;
-        wsm[9 * (g >> 3) + (g & 7)] = __ldg(src + g);
+        wsm[9 * (g >> 3) + (g & 7)] = __ldg(src + g);  // (kw, dw) of rows 2h, 2h + 1 of column g >> 3
       }
       __syncwarp();
       wr = cur.r;
     }
 
-    // ---- row pass (Sec. 2 factorisation), exact, in Swar16 words: field
-    // lo = block p, hi = block p + 4.  The DC output is centred by -2048 so
-    // that the column pass stays inside int16.
+    // ---- row pass (Sec. 2 factorisation), exact, two blocks per word
     {
-      Swar16 rv[2][16];
+      Row rv[2][16];
 #pragma unroll
       for (int tr = 0; tr < 2; ++tr) {
         const uint4& wa = X[tr];
         const uint4& wb = X[2 + tr];
-        Swar16 xs[16];
+        Row xs[16];
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
           const unsigned lo = __byte_perm(word_of(wa, w), word_of(wb, w), 0x5410u);  // a0 a1 b0 b1
           const unsigned hi = __byte_perm(word_of(wa, w), word_of(wb, w), 0x7632u);  // a2 a3 b2 b3
-          xs[4 * w + 0].v = (lo & 0x00FF00FFu) | kSwarBias;
-          xs[4 * w + 1].v = __byte_perm(lo, kSwarBias, 0x7351u);
-          xs[4 * w + 2].v = (hi & 0x00FF00FFu) | kSwarBias;
-          xs[4 * w + 3].v = __byte_perm(hi, kSwarBias, 0x7351u);
+          xs[4 * w + 0].v = (lo & 0x00FF00FFu) | kRowBias;
+          xs[4 * w + 1].v = __byte_perm(lo, kRowBias, 0x7351u);
+          xs[4 * w + 2].v = (hi & 0x00FF00FFu) | kRowBias;
+          xs[4 * w + 3].v = __byte_perm(hi, kRowBias, 0x7351u);
         }
         fwd16(xs, rv[tr]);
-        rv[tr][0].v -= 0x08000800u;
+        if (kColSwar) rv[tr][0].v -= 0x08000800u;  // centre the DC output by -2048
       }
       uint4* const t1w = reinterpret_cast<uint4*>(t2 + 138 * p + j);
 #pragma unroll
@@ -374,33 +382,47 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
       cp_async_commit();
     }
 
-    // ---- per column c = 2j + i: column pass in Swar16 (exact int16), to
-    // y = 256 Y in floats, zonal mask and S^2 weights, dropped energy
-    // (Parseval), inverse column pass into the back-transpose.  Lanes with odd j >> 1 take their two columns in
-    // the opposite order, so the 8-byte reads of the forward transpose are
+    // ---- per column c = 2j + i: column pass (y = 256 Y, exact), mask and S^2
+    // weights, dropped energy (Parseval), inverse column pass into the
+    // back-transpose.  Lanes with odd j >> 1 take their two columns in the
+    // opposite order, so the 8-byte reads of the forward transpose are
     // conflict-free; each lane's forward chunks sit in the line it writes last.
     float2 acc = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
     const uint2* const t1r = reinterpret_cast<const uint2*>(t2 + 138 * p + 17 * j + 8 * (1 ^ jb1));
 #pragma unroll
     for (int ii = 0; ii < 2; ++ii) {
       const int i = ii ^ jb1;
-      Swar16 cw[16], yw[16];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const uint2 v = t1r[2 * q + i];
-        cw[2 * q].v = v.x;
-        cw[2 * q + 1].v = v.y;
-      }
-      fwd16(cw, yw);
-      // field f -> float 2^23 + f (f = Y + 32768) -> 256 f - 256 (2^23 + 32768)
-      // = 256 Y in one exact FMA; the DC coefficient of column 0 also takes
-      // back the 16 * 2048 of the centring
-      const float dc = (2 * j + i) == 0 ? -2147483648.0f : -2155872256.0f;
       float2 y[16];
+      if constexpr (kColSwar) {
+        Swar16 cw[16], yw[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const float o = u == 0 ? dc : -2155872256.0f;
-        y[u] = __ffma2_rn(swar16_f2(yw[u].v), make_float2(256.0f, 256.0f), make_float2(o, o));
+        for (int q = 0; q < 8; ++q) {
+          const uint2 v = t1r[2 * q + i];
+          cw[2 * q].v = v.x;
+          cw[2 * q + 1].v = v.y;
+        }
+        fwd16(cw, yw);
+        // field f -> float 2^23 + f (f = Y + 32768) -> 256 f - 256 (2^23 +
+        // 32768) = 256 Y in one exact FMA; the DC coefficient of column 0
+        // also takes back the 16 * 2048 of the centring
+        const float dc = (2 * j + i) == 0 ? -2147483648.0f : -2155872256.0f;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {  // scalar FMAs: immediate operands, no constant pairs to hold
+          const float o = u == 0 ? dc : -2155872256.0f;
+          const float2 f = swar16_f2(yw[u].v);
+          y[u] = make_float2(__fmaf_rn(f.x, 256.0f, o), __fmaf_rn(f.y, 256.0f, o));
+        }
+      } else {
+        float2 cv[16];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const uint2 v = t1r[2 * q + i];
+          cv[2 * q] = swar_row_f2(v.x);
+          cv[2 * q + 1] = swar_row_f2(v.y);
+        }
+        fwd16(cv, y);
+        // every input carries 2^23 + 2^20; only the DC row sums them
+        y[0] = bsub(y[0], make_float2(150994944.0f, 150994944.0f));
       }
       const float4* const wcol = wsm + 9 * (2 * j + i);
 #pragma unroll
@@ -458,14 +480,6 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     if (lane == 0) tile_sse[cur.t] = tot * (1.0f / (256.0f * 2304.0f));
     __syncwarp();  // buffer reads done before the next tile's writes
 
-    if (!kPrefetch) {  // no look-ahead: the next tile is fetched only now
-      if (!(ok && c_t < t_stop)) break;
-      take(cur);
-      ok = advance();
-      issue(cur, 0);
-      cp_async_commit();
-      continue;
-    }
     if (!have_nxt) break;
     cur = nxt;
     nxt = fut;
@@ -474,267 +488,6 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
   }
   cp_async_wait<0>();
   if (!ok && lane == 0) set_status(status, kDevBadJob);
-}
-
-struct TileRef {
-  const uint8_t* src;  // row 2j of block A of this lane
-  uint8_t* dst;
-  long long t;
-  int src_pitch, dst_pitch;  // bytes (host checks they fit in 31 bits)
-  int r;
-  int nb;
-};
-
-// --------------------------------------------------------------------------
-// Fused zonal compression with the forward transform in 16-bit SWAR lanes.
-//
-// The forward transform is exact integer work whose every node fits int16
-// once the DC column is centred (row-pass outputs of T's all-ones row minus
-// 2048): it runs on two blocks per 32-bit register (offset-binary lanes, one
-// 3-input integer add per butterfly addition) on the integer pipe, leaving
-// the FP32 pipe to the inverse.  Conversion to FP32 happens once per
-// coefficient, fused with the zonal mask and the row weight W_u:
-//   word -> (mask ? word : bias) -> two magic floats 2^23 + 32768 + Y
-//   -> D = f W_u - (2^23 + 32768) W_u   (one f32x2 FMA, exact).
-// The column weight W_c is applied in the inverse row stage, where c is a
-// compile-time index.  SSE is accumulated from e = Z - 2304 x with the input
-// rows re-read (they are still in L1/L2).
-//
-// Shared memory per warp (13 KB): T1 (SWAR words, 4 KB), T2 (float2 pairs,
-// 8 KB) and the keep-masks of the warp's current r (1 KB), each with a
-// 16-byte-chunk XOR swizzle that is conflict-free for its writers and readers.
-// Lanes with odd p handle their two rows in the opposite order, so their
-// 8-byte reads of T2 fall in the other half of each chunk.
-// --------------------------------------------------------------------------
-constexpr int kSwarWarpSmem = 4096 + 8192 + 1024;
-
-// W = 48 S^2 for rows 0..15 of T (S printed in Sec. 2: 1/4, 1/sqrt(12), 1/sqrt(8))
-__host__ __device__ constexpr float w48(int i) {
-  return (i == 0 || i == 1 || i == 5 || i == 8) ? 3.f : ((i == 3 || i == 4 || i == 11 || i == 12) ? 6.f : 4.f);
-}
-
-__device__ __forceinline__ unsigned lop_select(unsigned w, unsigned m, unsigned other) {
-  return (w & m) | (~m & other);
-}
-
-template <int kWarps>
-__global__ void __launch_bounds__(32 * kWarps, 16 / kWarps)
-zonal_swar_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
-                  const float2* __restrict__ wtab, float* __restrict__ tile_sse, int* __restrict__ status) {
-  extern __shared__ __align__(16) unsigned char dsmem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int p = lane >> 3, j = lane & 7, po = p & 1;
-  unsigned char* wbase = dsmem + warp * kSwarWarpSmem;
-  uint4* t1 = reinterpret_cast<uint4*>(wbase);            // 256 chunks
-  float4* t2 = reinterpret_cast<float4*>(wbase + 4096);   // 512 chunks
-  uint4* msk = reinterpret_cast<uint4*>(wbase + 12288);   // 64 chunks
-  const long long nwarps = (long long)gridDim.x * kWarps;
-
-  int job = -1;
-  long long jb = 0, je = 0;
-  auto locate = [&](long long t, TileRef& ref) -> bool {
-    if (t < jb || t >= je) {
-      warp_find_job(jobs, njobs, t, job);
-      jb = __ldg(&jobs[job].tile_begin);
-      je = jb + (long long)__ldg(&jobs[job].tiles_x) * (__ldg(&jobs[job].height) >> 4);
-      if (t < jb || t >= je) return false;
-    }
-    const ImageJob* J = jobs + job;
-    const int tiles_x = __ldg(&J->tiles_x);
-    const long long lt = t - jb;
-    const int ty = (int)(lt / tiles_x);
-    const int tx = (int)(lt - (long long)ty * tiles_x);
-    const int x0 = tx * kTileW;
-    const long long row = (long long)(ty * kTileH + 2 * j);
-    ref.src_pitch = (int)__ldg(&J->src_pitch);
-    ref.dst_pitch = (int)__ldg(&J->dst_pitch);
-    ref.src = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->src))) +
-              row * ref.src_pitch + x0 + 16 * p;
-    ref.dst = reinterpret_cast<uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->dst))) +
-              row * ref.dst_pitch + x0 + 16 * p;
-    ref.t = t;
-    ref.r = __ldg(&J->param);
-    ref.nb = min(8, (__ldg(&J->width) - x0) >> 4);
-    return true;
-  };
-  auto load = [&](const TileRef& ref, uint4& a0, uint4& a1, uint4& b0, uint4& b1) {
-    a0 = a1 = b0 = b1 = make_uint4(0, 0, 0, 0);
-    if (p < ref.nb) {
-      a0 = __ldg(reinterpret_cast<const uint4*>(ref.src));
-      a1 = __ldg(reinterpret_cast<const uint4*>(ref.src + ref.src_pitch));
-    }
-    if (p + 4 < ref.nb) {
-      b0 = __ldg(reinterpret_cast<const uint4*>(ref.src + 64));
-      b1 = __ldg(reinterpret_cast<const uint4*>(ref.src + 64 + ref.src_pitch));
-    }
-  };
-
-  const long long per_warp = (ntiles + nwarps - 1) / nwarps;
-  const long long gw = (long long)blockIdx.x * kWarps + warp;
-  const long long t_end = min(ntiles, (gw + 1) * per_warp);
-  long long t = gw * per_warp;
-  TileRef cur;
-  uint4 a0, a1, b0, b1;
-  while (t < t_end && !locate(t, cur)) {
-    if (lane == 0) set_status(status, kDevBadJob);
-    ++t;
-  }
-  if (t >= t_end) return;
-  load(cur, a0, a1, b0, b1);
-  int mr = -1;  // r whose keep-masks are in msk
-
-  while (true) {
-    long long tn = cur.t + 1;
-    TileRef nxt;
-    bool have_next = false;
-    while (tn < t_end) {
-      if (locate(tn, nxt)) { have_next = true; break; }
-      if (lane == 0) set_status(status, kDevBadJob);
-      ++tn;
-    }
-    uint4 na0, na1, nb0, nb1;
-    if (have_next) load(nxt, na0, na1, nb0, nb1);
-
-    const bool va = p < cur.nb, vb = p + 4 < cur.nb;
-    if (cur.r != mr) {  // warp-uniform: rebuild the keep-mask words of this r
-      __syncwarp();
-      const float4* wr4 = reinterpret_cast<const float4*>(wtab) + (long long)cur.r * 128;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int e0 = lane * 8 + 4 * h;  // coefficients e0..e0+3: c = e0 >> 4, u = e0 & 15
-        const float4 k01 = __ldg(wr4 + (e0 >> 1));
-        const float4 k23 = __ldg(wr4 + (e0 >> 1) + 1);
-        const int c = e0 >> 4, q = (e0 & 15) >> 2;
-        msk[(c >> 1) * 8 + (((c & 1) * 4 + q) ^ (c >> 1))] =
-            make_uint4(k01.x != 0.f ? ~0u : 0u, k01.z != 0.f ? ~0u : 0u, k23.x != 0.f ? ~0u : 0u, k23.z != 0.f ? ~0u : 0u);
-      }
-      __syncwarp();
-      mr = cur.r;
-    }
-
-    // ---- row pass in SWAR lanes (A, B) for rows 2j, 2j+1; DC centring
-    {
-      Swar16 x0v[16], x1v[16], r0[16], r1[16];
-#pragma unroll
-      for (int k = 0; k < 16; k += 2) {
-        const int wi = k >> 2, bi = k & 3;
-        const unsigned sel0 = (unsigned)(bi | ((bi + 1) << 4) | ((4 + bi) << 8) | ((5 + bi) << 12));
-        const unsigned t0 = __byte_perm(word_of(a0, wi), word_of(b0, wi), sel0);
-        const unsigned t1w = __byte_perm(word_of(a1, wi), word_of(b1, wi), sel0);
-        const unsigned sel1 = (unsigned)((bi + 1) | (bi << 4) | ((5 + bi) << 8) | ((4 + bi) << 12));
-        const unsigned u0 = __byte_perm(word_of(a0, wi), word_of(b0, wi), sel1);
-        const unsigned u1 = __byte_perm(word_of(a1, wi), word_of(b1, wi), sel1);
-        x0v[k].v = lop_select(t0, 0x00FF00FFu, kSwarBias);
-        x1v[k].v = lop_select(t1w, 0x00FF00FFu, kSwarBias);
-        x0v[k + 1].v = lop_select(u0, 0x00FF00FFu, kSwarBias);
-        x1v[k + 1].v = lop_select(u1, 0x00FF00FFu, kSwarBias);
-      }
-      fwd16(x0v, r0);
-      fwd16(x1v, r1);
-      r0[0].v -= 0x08000800u;  // centre the DC column: R[m][0] - 2048 in both lanes
-      r1[0].v -= 0x08000800u;
-      uint2* t1h = reinterpret_cast<uint2*>(t1);
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int chunk = ((p >> 1) * 16 + k) * 8 + (((j >> 1) + 4 * po) ^ ((k >> 1) & 7));
-        t1h[2 * chunk + (j & 1)] = make_uint2(r0[k].v, r1[k].v);
-      }
-    }
-    __syncwarp();
-
-    // ---- per column c = 2j + i: SWAR column pass, mask + W_u + FP32
-    // conversion, FP32 inverse column pass, into T2 line c
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int c = 2 * j + i;
-      Swar16 cv[16], y[16];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint4 v = t1[((p >> 1) * 16 + c) * 8 + ((q + 4 * po) ^ j)];
-        cv[4 * q].v = v.x;
-        cv[4 * q + 1].v = v.y;
-        cv[4 * q + 2].v = v.z;
-        cv[4 * q + 3].v = v.w;
-      }
-      fwd16(cv, y);
-      // Y[0][0] came out of the centred DC column 32768 low: its lane value
-      // already equals Y + 0, so it converts with offset 2^23 instead.
-      const float k00 = (c == 0) ? -8388608.0f * w48(0) : -8421376.0f * w48(0);
-      const unsigned zero00 = (c == 0) ? 0u : kSwarBias;  // word that converts to 0
-      float2 d[16];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint4 m4 = msk[j * 8 + ((i * 4 + q) ^ j)];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int u = 4 * q + e;
-          const unsigned mw = e == 0 ? m4.x : (e == 1 ? m4.y : (e == 2 ? m4.z : m4.w));
-          const unsigned w = lop_select(y[u].v, mw, u == 0 ? zero00 : kSwarBias);
-          const float flo = __uint_as_float((w & 0xFFFFu) | 0x4B000000u);
-          const float fhi = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7432u));
-          const float wu = w48(u);
-          const float kk = u == 0 ? k00 : -8421376.0f * wu;  // -(2^23 + 32768) W_u
-          d[u] = __ffma2_rn(make_float2(flo, fhi), make_float2(wu, wu), make_float2(kk, kk));
-        }
-      }
-      float2 uo[16];
-      inv16(d, uo);
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        t2[(p * 16 + c) * 8 + (q ^ j)] = make_float4(uo[2 * q].x, uo[2 * q].y, uo[2 * q + 1].x, uo[2 * q + 1].y);
-    }
-    __syncwarp();
-
-    // ---- per row ar (odd p: rows in reverse order): W_c, inverse row pass,
-    // round half to even, clamp, pack, store; SSE from Z - 2304 x
-    float2 acc = make_float2(0.f, 0.f);
-    const float2* t2h = reinterpret_cast<const float2*>(t2);
-#pragma unroll
-    for (int tr = 0; tr < 2; ++tr) {
-      const int h = tr ^ po;  // row 2j + h
-      float2 v[16], z[16];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const float wc = w48(c);
-        v[c] = f2mul(t2h[2 * ((p * 16 + c) * 8 + (j ^ ((c >> 1) & 7))) + h], wc);
-      }
-      inv16(v, z);
-      const uint8_t* srow = cur.src + h * cur.src_pitch;
-      const uint4 xa = va ? __ldg(reinterpret_cast<const uint4*>(srow)) : make_uint4(0, 0, 0, 0);
-      const uint4 xb = vb ? __ldg(reinterpret_cast<const uint4*>(srow + 64)) : make_uint4(0, 0, 0, 0);
-      unsigned oa[4], ob[4];
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        unsigned qa[4], qb[4];
-        const unsigned wxa = word_of(xa, g), wxb = word_of(xb, g);
-#pragma unroll
-        for (int e4 = 0; e4 < 4; ++e4) {
-          const float2 zz = z[4 * g + e4];
-          const float2 e = rne_denormal(f2mul(zz, kInv2304));
-          qa[e4] = __float_as_uint(e.x);
-          qb[e4] = __float_as_uint(e.y);
-          const float2 xf = make_float2(__uint2float_rn((wxa >> (8 * e4)) & 0xFFu),
-                                        __uint2float_rn((wxb >> (8 * e4)) & 0xFFu));
-          const float2 err = __ffma2_rn(xf, make_float2(-2304.f, -2304.f), zz);
-          acc = __ffma2_rn(err, err, acc);
-        }
-        oa[g] = pack_u8(qa[1], qa[0], pack_u8(qa[3], qa[2], 0u));
-        ob[g] = pack_u8(qb[1], qb[0], pack_u8(qb[3], qb[2], 0u));
-      }
-      uint8_t* dd = cur.dst + h * cur.dst_pitch;
-      if (va) __stcs(reinterpret_cast<uint4*>(dd), make_uint4(oa[0], oa[1], oa[2], oa[3]));
-      if (vb) __stcs(reinterpret_cast<uint4*>(dd + 64), make_uint4(ob[0], ob[1], ob[2], ob[3]));
-    }
-
-    // ---- tile SSE: sum of e^2 / 2304^2 over valid blocks
-    const float tot = warp_sum((va ? acc.x : 0.f) + (vb ? acc.y : 0.f));
-    if (lane == 0) tile_sse[cur.t] = tot * (1.0f / (2304.0f * 2304.0f));
-    __syncwarp();
-
-    if (!have_next) break;
-    cur = nxt;
-    a0 = na0; a1 = na1; b0 = nb0; b1 = nb1;
-  }
 }
 
 // --------------------------------------------------------------------------
@@ -1083,12 +836,8 @@ static cudaError_t launch_with_smem(K kernel, int grid, int threads, int smem, c
 }
 
 static int config_index(const ZonalConfig& c) {
-  if (c.variant == kZonalSwar) return c.warps == 4 ? 4 : -1;
-  if (c.warps == 2 && c.prefetch) return 0;
-  if (c.warps == 4 && c.prefetch) return 1;
-  if (c.warps == 8 && c.prefetch) return 2;
-  if (c.warps == 4 && !c.prefetch) return 3;
-  return -1;
+  if (!c.prefetch || c.warps != 4) return -1;
+  return c.variant == kZonalSwar ? 0 : (c.variant == kZonalF32 ? 1 : -1);
 }
 
 bool zonal_config_supported(const ZonalConfig& c) { return config_index(c) >= 0; }
@@ -1101,20 +850,11 @@ cudaError_t launch_zonal_config(const ZonalConfig& cfg, const ImageJob* d_jobs, 
   const int threads = 32 * cfg.warps;
   switch (config_index(cfg)) {
     case 0:
-      return launch_with_smem(zonal_f32_kernel<2, true>, grid, threads, 2 * kZonalWarpSmemBytes, stream,
-                              d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
+      return launch_with_smem(zonal_f32_kernel<4, true>, grid, threads, 4 * kZonalWarpSmemBytes, stream, d_jobs,
+                              njobs, ntiles, d_wtab, d_tile_sse, d_status);
     case 1:
-      return launch_with_smem(zonal_f32_kernel<4, true>, grid, threads, 4 * kZonalWarpSmemBytes, stream,
-                              d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
-    case 2:
-      return launch_with_smem(zonal_f32_kernel<8, true>, grid, threads, 8 * kZonalWarpSmemBytes, stream,
-                              d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
-    case 3:
-      return launch_with_smem(zonal_f32_kernel<4, false>, grid, threads, 4 * kZonalWarpSmemBytes, stream,
-                              d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
-    case 4:
-      return launch_with_smem(zonal_swar_kernel<4>, grid, threads, 4 * kSwarWarpSmem, stream, d_jobs, njobs,
-                              ntiles, d_wtab, d_tile_sse, d_status);
+      return launch_with_smem(zonal_f32_kernel<4, false>, grid, threads, 4 * kZonalWarpSmemBytes, stream, d_jobs,
+                              njobs, ntiles, d_wtab, d_tile_sse, d_status);
   }
   return cudaErrorInvalidValue;
 }
@@ -1133,16 +873,13 @@ int zonal_config_max_ctas_per_sm(const ZonalConfig& cfg) {
   cudaError_t e = cudaErrorInvalidValue;
   const int zs = kZonalWarpSmemBytes;
   switch (config_index(cfg)) {
-    case 0: e = occupancy_with_smem(&n, zonal_f32_kernel<2, true>, 64, 2 * zs); break;
-    case 1: e = occupancy_with_smem(&n, zonal_f32_kernel<4, true>, 128, 4 * zs); break;
-    case 2: e = occupancy_with_smem(&n, zonal_f32_kernel<8, true>, 256, 8 * zs); break;
-    case 3: e = occupancy_with_smem(&n, zonal_f32_kernel<4, false>, 128, 4 * zs); break;
-    case 4: e = occupancy_with_smem(&n, zonal_swar_kernel<4>, 128, 4 * kSwarWarpSmem); break;
+    case 0: e = occupancy_with_smem(&n, zonal_f32_kernel<4, true>, 128, 4 * zs); break;
+    case 1: e = occupancy_with_smem(&n, zonal_f32_kernel<4, false>, 128, 4 * zs); break;
   }
   return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
-ZonalConfig default_zonal_config() { return ZonalConfig{kZonalF32, kZonalWarps, 1}; }
+ZonalConfig default_zonal_config() { return ZonalConfig{kZonalSwar, kZonalWarps, 1}; }
 
 cudaError_t launch_zonal(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
                          float* d_tile_sse, int* d_status, int grid, cudaStream_t stream) {

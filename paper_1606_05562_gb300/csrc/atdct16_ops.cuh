@@ -29,6 +29,18 @@ constexpr unsigned kSwarBias = 0x80008000u;
 ATDCT16_OPS_HD Swar16 badd(Swar16 a, Swar16 b) { return Swar16{a.v + b.v - kSwarBias}; }
 ATDCT16_OPS_HD Swar16 bsub(Swar16 a, Swar16 b) { return Swar16{a.v - b.v + kSwarBias}; }
 
+// The same with the bias 4096: each field holds value + 4096, exact while
+// every true lane value stays in [-4096, 61439].  A 1-D pass over 8-bit
+// inputs never leaves [-4080, 4080] (at most 16 terms of magnitude <= 255),
+// so its outputs are 13-bit field values that a byte permute can place
+// directly into the mantissa of a float.
+struct SwarRow {
+  unsigned v;
+};
+constexpr unsigned kSwarRowBias = 0x10001000u;
+ATDCT16_OPS_HD SwarRow badd(SwarRow a, SwarRow b) { return SwarRow{a.v + b.v - kSwarRowBias}; }
+ATDCT16_OPS_HD SwarRow bsub(SwarRow a, SwarRow b) { return SwarRow{a.v - b.v + kSwarRowBias}; }
+
 #ifdef __CUDACC__
 __device__ __forceinline__ unsigned long long f2_bits(float2 v) {
   return (unsigned long long)__float_as_uint(v.x) | ((unsigned long long)__float_as_uint(v.y) << 32);
