@@ -318,7 +318,7 @@ atdct16_status atdct16_compress_quant(atdct16_plan_t plan, const atdct16_image* 
   long long ntiles = 0;
   atdct16_status s = stage_jobs(plan, h_images, n, 2, stream, &ntiles, d_levels != nullptr);
   if (s != ATDCT16_OK) return s;
-  const int grid = (int)std::min<long long>(plan->quant_grid, (ntiles + kWarpsPerCta - 1) / kWarpsPerCta);
+  const int grid = (int)std::min<long long>(plan->quant_grid, (ntiles + kZonalWarps - 1) / kZonalWarps);
   const int pk = prof_begin(plan, stream);
   cudaError_t e = launch_quant(plan->d_jobs, n, ntiles, plan->d_qtab, d_levels, plan->d_tile_sse,
                                plan->d_status, grid, stream);

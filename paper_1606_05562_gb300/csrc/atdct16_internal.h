@@ -12,7 +12,7 @@ constexpr int kTileW = 128;
 constexpr int kTileH = 16;
 constexpr int kWarpsPerCta = 8;
 constexpr int kThreadsPerCta = 32 * kWarpsPerCta;
-constexpr int kZonalWarps = 4;  // warps per CTA of the fused zonal kernel
+constexpr int kZonalWarps = 4;  // warps per CTA of the fused zonal and quantisation kernels
 
 // One image of a batch, as the kernels see it (64 bytes).
 struct ImageJob {

@@ -491,157 +491,282 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
 }
 
 // --------------------------------------------------------------------------
-// Fused quantisation (S absorbed into the quantiser) for int16 planes.
+// Fused quantisation (S absorbed into the quantiser) for int16 planes
+// (Sec. 2 last paragraph, Sec. 5.3).
+//
+// Same organisation as the zonal kernel: lane (p, j) = (lane & 3, lane >> 2)
+// owns rows 2j, 2j+1 of blocks p and p + 4 of a 16 x 128-sample tile, input
+// rows are staged with cp.async two tiles ahead, each warp walks a
+// contiguous tile range with a cursor, and the transposes go through the
+// padded line-per-column buffer unit(p, c, q) = 138 p + 8 c + (c >> 1) + q
+// (the column pass overwrites, in place, the two lines each lane alone
+// reads).  All arithmetic is FP32 on f32x2: int16 samples give exact
+// integer Y (|Y| <= 2^23).  Per coefficient, with (k, s, g, Q) =
+// (fp32(s_u s_v / Qstep), s_u s_v, s_u s_v Qstep, Qstep):
+//   L  = floor(fp32(fp32(|Y| k) + 0.5))         (floor by a round-down add
+//                                                of 2^23, exact for L < 2^22)
+//   e  = s |Y| - L Q                             (B - B', Parseval)
+//   Y' = sign(Y) L g                             (S B' S entry)
+// and the reconstruction is rint to int16 (magic-number add, saturating pack).
 // --------------------------------------------------------------------------
+constexpr int kQStageUnits = 2 * 8 * 32;  // two tiles of input rows, 8 x 16 bytes per lane
+constexpr int kQuantWarpSmemBytes = 16 * (kZT2Units + kQStageUnits);
+
 __device__ __forceinline__ float i16_lo(unsigned w) { return (float)(short)(w & 0xffffu); }
 __device__ __forceinline__ float i16_hi(unsigned w) { return (float)(short)(w >> 16); }
 
-__global__ void __launch_bounds__(kThreadsPerCta, 1)
-quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
+__device__ __forceinline__ float2 f2abs(float2 v) {
+  return make_float2(__uint_as_float(__float_as_uint(v.x) & 0x7fffffffu),
+                     __uint_as_float(__float_as_uint(v.y) & 0x7fffffffu));
+}
+// a + b rounded toward -inf, both halves
+__device__ __forceinline__ float2 f2add_rm(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(d);
+}
+// magnitude of m with the sign of s, both halves
+__device__ __forceinline__ float2 f2copysign(float2 m, float2 s) {
+  return make_float2(__uint_as_float((__float_as_uint(m.x) & 0x7fffffffu) | (__float_as_uint(s.x) & 0x80000000u)),
+                     __uint_as_float((__float_as_uint(m.y) & 0x7fffffffu) | (__float_as_uint(s.y) & 0x80000000u)));
+}
+
+struct QuantTile {
+  const uint8_t* src;  // row 2j of block p of this lane
+  uint8_t* dst;
+  int src_pitch, dst_pitch;
+  int nb;              // valid 16-sample blocks in the tile (1..8)
+  int t;               // tile index
+  int qp;
+  long long lvl;       // level index of (u, v) = (0, 0) of block p of this tile
+};
+
+template <bool kLevels>
+__global__ void __launch_bounds__(128, 3)
+quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
              const float4* __restrict__ qtab, int16_t* __restrict__ levels, float* __restrict__ tile_sse,
              int* __restrict__ status) {
-  __shared__ WarpBuf sbuf[kWarpsPerCta];
+  extern __shared__ __align__(16) unsigned char qsmem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int p = lane >> 3, j = lane & 7;
-  float4* buf = sbuf[warp].c;
-  const long long nwarps = (long long)gridDim.x * kWarpsPerCta;
+  const int p = lane & 3, j = lane >> 2, jb1 = (j >> 1) & 1;
+  float4* const tb = reinterpret_cast<float4*>(qsmem + warp * kQuantWarpSmemBytes);
+  uint4* const stg = reinterpret_cast<uint4*>(tb + kZT2Units) + lane;  // + 256 s + 32 k
+  const int ntiles = (int)ntiles_ll;  // the launcher checks ntiles < 2^30
+  constexpr int kWarps = 4;
+  const int nwarps = gridDim.x * kWarps;
+  const int per_warp = (ntiles + nwarps - 1) / nwarps;
+  const int t_first = (blockIdx.x * kWarps + warp) * per_warp;
+  const int t_stop = min(ntiles, t_first + per_warp);
+  if (t_first >= t_stop) return;
 
-  int job = -1;
-  long long jb = 0, je = 0;
-  ImageJob J;
-  for (long long t = (long long)blockIdx.x * kWarpsPerCta + warp; t < ntiles; t += nwarps) {
-    if (t < jb || t >= je) {
-      warp_find_job(jobs, njobs, t, job);
-      J = jobs[job];
-      jb = J.tile_begin;
-      je = jb + (long long)J.tiles_x * (J.height >> 4);
-      if (t < jb || t >= je) {
-        if (lane == 0) set_status(status, kDevBadJob);
-        continue;
-      }
+  int c_t = 0, c_end = 0, tiles_x = 1, tx = 0, ty = 0, nb_last = 8, qp_job = 0, src_pitch = 0, dst_pitch = 0;
+  int bpr = 0;
+  long long lvl_base = 0;
+  const uint8_t* src_band = nullptr;  // this lane's row 2j of block p in tile column 0 of the band
+  uint8_t* dst_band = nullptr;
+  auto enter = [&](int t) -> bool {
+    int job;
+    warp_find_job(jobs, njobs, t, job);
+    const ImageJob* J = jobs + job;
+    const long long tb0 = __ldg(&J->tile_begin);
+    tiles_x = __ldg(&J->tiles_x);
+    const long long te = tb0 + (long long)tiles_x * (__ldg(&J->height) >> 4);
+    if (t < tb0 || t >= te || tiles_x < 1) return false;
+    c_end = (int)min(te, (long long)t_stop);
+    const int lt = (int)(t - tb0);
+    ty = lt / tiles_x;
+    tx = lt - ty * tiles_x;
+    src_pitch = (int)__ldg(&J->src_pitch);
+    dst_pitch = (int)__ldg(&J->dst_pitch);
+    const long long row = (long long)ty * kTileH + 2 * j;
+    src_band = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->src))) +
+               row * src_pitch + 32 * p;
+    dst_band = reinterpret_cast<uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->dst))) +
+               row * dst_pitch + 32 * p;
+    const int width = __ldg(&J->width);
+    nb_last = min(8, (width - (tiles_x - 1) * kTileW) >> 4);
+    bpr = width >> 4;
+    lvl_base = __ldg(&J->level_base);
+    qp_job = __ldg(&J->param);
+    c_t = t;
+    return true;
+  };
+  auto take = [&](QuantTile& z) {
+    z.src = src_band + tx * (2 * kTileW);
+    z.dst = dst_band + tx * (2 * kTileW);
+    z.src_pitch = src_pitch;
+    z.dst_pitch = dst_pitch;
+    z.nb = tx == tiles_x - 1 ? nb_last : 8;
+    z.t = c_t;
+    z.qp = qp_job;
+    z.lvl = lvl_base + ((long long)ty * bpr + tx * 8 + p) * 256;
+  };
+  auto advance = [&]() -> bool {
+    ++c_t;
+    if (++tx == tiles_x) {
+      tx = 0;
+      ++ty;
+      src_band += (long long)kTileH * src_pitch;
+      dst_band += (long long)kTileH * dst_pitch;
     }
-    const long long lt = t - jb;
-    const int ty = (int)(lt / J.tiles_x);
-    const int tx = (int)(lt - (long long)ty * J.tiles_x);
-    const int x0 = tx * kTileW, y0 = ty * kTileH;
-    const int nb = min(8, (J.width - x0) >> 4);
-    const bool va = p < nb, vb = p + 4 < nb;
+    return c_t >= t_stop || c_t < c_end || enter(c_t);
+  };
+  // Staging word k of slot st: row 2j + ((k >> 1) & 1), block p + 4 (k >> 2),
+  // samples 8 (k & 1) .. 8 (k & 1) + 7.
+  auto issue = [&](const QuantTile& z, int st) {
+    uint4* d = stg + 256 * st;
+    if (p < z.nb) {
+      cp_async16(d, z.src);
+      cp_async16(d + 32, z.src + 16);
+      cp_async16(d + 64, z.src + z.src_pitch);
+      cp_async16(d + 96, z.src + z.src_pitch + 16);
+    }
+    if (p + 4 < z.nb) {
+      cp_async16(d + 128, z.src + 128);
+      cp_async16(d + 160, z.src + 144);
+      cp_async16(d + 192, z.src + z.src_pitch + 128);
+      cp_async16(d + 224, z.src + z.src_pitch + 144);
+    }
+    cp_async_commit();
+  };
 
-    // ---- load rows 2j, 2j+1 of A and B: 32 B each
-    const uint8_t* s = J.src + (long long)(y0 + 2 * j) * J.src_pitch + 2 * (x0 + 16 * p);
-    uint4 a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = b[i] = make_uint4(0, 0, 0, 0);
-    if (va) {
-      a[0] = __ldcs(reinterpret_cast<const uint4*>(s));
-      a[1] = __ldcs(reinterpret_cast<const uint4*>(s + 16));
-      a[2] = __ldcs(reinterpret_cast<const uint4*>(s + J.src_pitch));
-      a[3] = __ldcs(reinterpret_cast<const uint4*>(s + J.src_pitch + 16));
-    }
-    if (vb) {
-      b[0] = __ldcs(reinterpret_cast<const uint4*>(s + 128));
-      b[1] = __ldcs(reinterpret_cast<const uint4*>(s + 144));
-      b[2] = __ldcs(reinterpret_cast<const uint4*>(s + J.src_pitch + 128));
-      b[3] = __ldcs(reinterpret_cast<const uint4*>(s + J.src_pitch + 144));
-    }
-    float2 x0v[16], x1v[16], r0[16], r1[16];
-#pragma unroll
-    for (int n = 0; n < 16; ++n) {
-      const int wi = (n >> 1) & 3, hi = n & 1, part = n >> 3;
-      const unsigned wa0 = word_of(a[part], wi), wb0 = word_of(b[part], wi);
-      const unsigned wa1 = word_of(a[2 + part], wi), wb1 = word_of(b[2 + part], wi);
-      x0v[n] = make_float2(hi ? i16_hi(wa0) : i16_lo(wa0), hi ? i16_hi(wb0) : i16_lo(wb0));
-      x1v[n] = make_float2(hi ? i16_hi(wa1) : i16_lo(wa1), hi ? i16_hi(wb1) : i16_lo(wb1));
-    }
-    fwd16(x0v, r0);
-    fwd16(x1v, r1);
-    float2 c0[16], c1[16];
-    transpose_rows_to_cols(buf, p, j, r0, r1, c0, c1);
-    float2 ya[16], yb[16];
-    fwd16(c0, ya);  // exact integers Y
-    fwd16(c1, yb);
-
-    // ---- quantise: level = sign(Y) floor(fp32(|Y| k) + 0.5), k = fp32(s/Qstep)
-    const float4* q0 = qtab + ((long long)J.param * 16 + 2 * j) * 16;
-    const float4* q1 = q0 + 16;
-    float2 acc = make_float2(0.f, 0.f);
-    const long long lbase = J.level_base;
-    const int bpr = J.width >> 4;
-    const long long blk_a = (long long)(y0 >> 4) * bpr + (x0 >> 4) + p;
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const float4 qa = __ldg(q0 + u), qb = __ldg(q1 + u);  // (k, s, g, Qstep)
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        float2& y = i ? yb[u] : ya[u];
-        const float4& q = i ? qb : qa;
-        const float la = copysignf(floorf(__fadd_rn(__fmul_rn(fabsf(y.x), q.x), 0.5f)), y.x);
-        const float lb = copysignf(floorf(__fadd_rn(__fmul_rn(fabsf(y.y), q.x), 0.5f)), y.y);
-        // Parseval: error energy of B - B' in the orthonormal domain
-        const float ea = fmaf(la, -q.w, __fmul_rn(y.x, q.y));
-        const float eb = fmaf(lb, -q.w, __fmul_rn(y.y, q.y));
-        acc.x = fmaf(ea, ea, acc.x);
-        acc.y = fmaf(eb, eb, acc.y);
-        if (levels) {
-          const int col = 2 * j + i;
-          if (va) levels[lbase + blk_a * 256 + u * 16 + col] = (int16_t)la;
-          if (vb) levels[lbase + (blk_a + 4) * 256 + u * 16 + col] = (int16_t)lb;
-        }
-        y = make_float2(la * q.z, lb * q.z);  // S B' S entry
-      }
-    }
-    float2 u0[16], u1[16];
-    inv16(ya, u0);
-    inv16(yb, u1);
-    float2 v0[16], v1[16];
-    transpose_cols_to_rows(buf, p, j, u0, u1, v0, v1);
-    float2 z0[16], z1[16];
-    inv16(v0, z0);
-    inv16(v1, z1);
-
-    // ---- rint, clamp to int16, store
-    uint4 oa[4], ob[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      // words 2i, 2i+1 of each 16-sample row hold samples 4i .. 4i+3
-      const int n = 4 * i;
-      const int row_part = 0;
-      (void)row_part;
-      unsigned a00 = pack_s16(__float2int_rn(z0[n + 1].x), __float2int_rn(z0[n].x));
-      unsigned a01 = pack_s16(__float2int_rn(z0[n + 3].x), __float2int_rn(z0[n + 2].x));
-      unsigned b00 = pack_s16(__float2int_rn(z0[n + 1].y), __float2int_rn(z0[n].y));
-      unsigned b01 = pack_s16(__float2int_rn(z0[n + 3].y), __float2int_rn(z0[n + 2].y));
-      unsigned a10 = pack_s16(__float2int_rn(z1[n + 1].x), __float2int_rn(z1[n].x));
-      unsigned a11 = pack_s16(__float2int_rn(z1[n + 3].x), __float2int_rn(z1[n + 2].x));
-      unsigned b10 = pack_s16(__float2int_rn(z1[n + 1].y), __float2int_rn(z1[n].y));
-      unsigned b11 = pack_s16(__float2int_rn(z1[n + 3].y), __float2int_rn(z1[n + 2].y));
-      // oa[0..1]: row 2j (32 B), oa[2..3]: row 2j+1
-      unsigned* pa0 = reinterpret_cast<unsigned*>(&oa[i >> 1]);
-      unsigned* pa1 = reinterpret_cast<unsigned*>(&oa[2 + (i >> 1)]);
-      unsigned* pb0 = reinterpret_cast<unsigned*>(&ob[i >> 1]);
-      unsigned* pb1 = reinterpret_cast<unsigned*>(&ob[2 + (i >> 1)]);
-      const int o = 2 * (i & 1);
-      pa0[o] = a00; pa0[o + 1] = a01;
-      pa1[o] = a10; pa1[o + 1] = a11;
-      pb0[o] = b00; pb0[o + 1] = b01;
-      pb1[o] = b10; pb1[o + 1] = b11;
-    }
-    uint8_t* d = J.dst + (long long)(y0 + 2 * j) * J.dst_pitch + 2 * (x0 + 16 * p);
-    if (va) {
-      __stcs(reinterpret_cast<uint4*>(d), oa[0]);
-      __stcs(reinterpret_cast<uint4*>(d + 16), oa[1]);
-      __stcs(reinterpret_cast<uint4*>(d + J.dst_pitch), oa[2]);
-      __stcs(reinterpret_cast<uint4*>(d + J.dst_pitch + 16), oa[3]);
-    }
-    if (vb) {
-      __stcs(reinterpret_cast<uint4*>(d + 128), ob[0]);
-      __stcs(reinterpret_cast<uint4*>(d + 144), ob[1]);
-      __stcs(reinterpret_cast<uint4*>(d + J.dst_pitch + 128), ob[2]);
-      __stcs(reinterpret_cast<uint4*>(d + J.dst_pitch + 144), ob[3]);
-    }
-    const float tot = warp_sum((va ? acc.x : 0.f) + (vb ? acc.y : 0.f));
-    if (lane == 0) tile_sse[t] = tot;
+  if (!enter(t_first)) {
+    if (lane == 0) set_status(status, kDevBadJob);
+    return;
   }
+  bool ok = true;
+  QuantTile cur, nxt;
+  take(cur);
+  ok = advance();
+  issue(cur, 0);
+  bool have_nxt = ok && c_t < t_stop;
+  if (have_nxt) {
+    take(nxt);
+    ok = advance();
+    issue(nxt, 1);
+  } else {
+    cp_async_commit();
+  }
+  int st = 0;
+  while (true) {
+    cp_async_wait<1>();
+    uint4 X[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) X[k] = stg[256 * st + 32 * k];
+    const bool va = p < cur.nb, vb = p + 4 < cur.nb;
+
+    // ---- row pass on rows 2j, 2j+1 (exact), into the line-per-column buffer
+    {
+      float2* const half = reinterpret_cast<float2*>(tb + 138 * p + j);
+#pragma unroll
+      for (int tr = 0; tr < 2; ++tr) {
+        float2 xv[16], rv[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) {
+          const unsigned wa = word_of(X[2 * tr + (n >> 3)], (n & 7) >> 1);
+          const unsigned wb = word_of(X[4 + 2 * tr + (n >> 3)], (n & 7) >> 1);
+          xv[n] = (n & 1) ? make_float2(i16_hi(wa), i16_hi(wb)) : make_float2(i16_lo(wa), i16_lo(wb));
+        }
+        fwd16(xv, rv);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) half[2 * (8 * k + (k >> 1)) + tr] = rv[k];
+      }
+    }
+    __syncwarp();
+
+    QuantTile fut;
+    const bool have_fut = have_nxt && ok && c_t < t_stop;
+    if (have_fut) {
+      take(fut);
+      ok = advance();
+      issue(fut, st);
+    } else {
+      cp_async_commit();
+    }
+
+    // ---- per column c = 2j + i: column pass (exact Y), quantise, error
+    // energy, dequantise, inverse column pass, back into the same line
+    float2 acc = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int c = 2 * j + i;
+      float4* const line = tb + 138 * p + 17 * j + 8 * i;
+      float2 cv[16], y[16];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 v = line[q];
+        cv[2 * q] = make_float2(v.x, v.y);
+        cv[2 * q + 1] = make_float2(v.z, v.w);
+      }
+      fwd16(cv, y);
+      const float4* const qc = qtab + ((long long)cur.qp * 16 + c) * 16;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const float4 q = __ldg(qc + u);  // (k, s, g, Qstep)
+        const float2 a = f2abs(y[u]);
+        const float2 b = __fadd2_rn(__fmul2_rn(a, make_float2(q.x, q.x)), make_float2(0.5f, 0.5f));
+        const float2 f = f2add_rm(b, make_float2(8388608.0f, 8388608.0f));  // floor(b) + 2^23
+        const float2 L = __fadd2_rn(f, make_float2(-8388608.0f, -8388608.0f));
+        const float2 e = __ffma2_rn(L, make_float2(-q.w, -q.w), __fmul2_rn(a, make_float2(q.y, q.y)));
+        float2& s = (u & 1) ? acc1 : acc;
+        s = __ffma2_rn(e, e, s);
+        if (kLevels) {
+          const int la = (int)(__float_as_uint(f.x) - 0x4B000000u), lb = (int)(__float_as_uint(f.y) - 0x4B000000u);
+          if (va) levels[cur.lvl + u * 16 + c] = (int16_t)(y[u].x < 0.f ? -la : la);
+          if (vb) levels[cur.lvl + 4 * 256 + u * 16 + c] = (int16_t)(y[u].y < 0.f ? -lb : lb);
+        }
+        y[u] = f2copysign(__fmul2_rn(L, make_float2(q.z, q.z)), y[u]);
+      }
+      float2 uo[16];
+      inv16(y, uo);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) line[q] = make_float4(uo[2 * q].x, uo[2 * q].y, uo[2 * q + 1].x, uo[2 * q + 1].y);
+    }
+    __syncwarp();
+
+    // ---- per row 2j + rr: gather (8-byte halves, conflict-free with the
+    // row-order swap of the zonal kernel), inverse row pass, rint, pack, store
+#pragma unroll
+    for (int tr = 0; tr < 2; ++tr) {
+      const int rr = tr ^ jb1;
+      const float2* const fin = reinterpret_cast<const float2*>(tb + 138 * p + j) + rr;
+      float2 v[16], z[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v[c] = fin[2 * (8 * c + (c >> 1))];
+      inv16(v, z);
+      unsigned oa[8], ob[8];
+#pragma unroll
+      for (int n = 0; n < 8; ++n) {
+        // rint by the magic add 1.5 * 2^23 (|z| < 2^22), then saturate to int16
+        const float2 m0 = __fadd2_rn(z[2 * n], make_float2(12582912.0f, 12582912.0f));
+        const float2 m1 = __fadd2_rn(z[2 * n + 1], make_float2(12582912.0f, 12582912.0f));
+        oa[n] = pack_s16((int)(__float_as_uint(m1.x) - 0x4B400000u), (int)(__float_as_uint(m0.x) - 0x4B400000u));
+        ob[n] = pack_s16((int)(__float_as_uint(m1.y) - 0x4B400000u), (int)(__float_as_uint(m0.y) - 0x4B400000u));
+      }
+      uint8_t* d = cur.dst + rr * cur.dst_pitch;
+      if (va) {
+        __stcs(reinterpret_cast<uint4*>(d), make_uint4(oa[0], oa[1], oa[2], oa[3]));
+        __stcs(reinterpret_cast<uint4*>(d + 16), make_uint4(oa[4], oa[5], oa[6], oa[7]));
+      }
+      if (vb) {
+        __stcs(reinterpret_cast<uint4*>(d + 128), make_uint4(ob[0], ob[1], ob[2], ob[3]));
+        __stcs(reinterpret_cast<uint4*>(d + 144), make_uint4(ob[4], ob[5], ob[6], ob[7]));
+      }
+    }
+
+    acc = __fadd2_rn(acc, acc1);
+    const float tot = warp_sum((va ? acc.x : 0.f) + (vb ? acc.y : 0.f));
+    if (lane == 0) tile_sse[cur.t] = tot;
+    __syncwarp();  // buffer reads done before the next tile's writes
+
+    if (!have_nxt) break;
+    cur = nxt;
+    nxt = fut;
+    have_nxt = have_fut;
+    st ^= 1;
+  }
+  cp_async_wait<0>();
+  if (!ok && lane == 0) set_status(status, kDevBadJob);
 }
 
 // --------------------------------------------------------------------------
@@ -822,17 +947,24 @@ __global__ void psnr_pair_finish(unsigned long long* slot, double npx, double pe
 // --------------------------------------------------------------------------
 // Launchers
 // --------------------------------------------------------------------------
-template <class K>
-static cudaError_t launch_with_smem(K kernel, int grid, int threads, int smem, cudaStream_t stream,
-                                   const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
-                                   float* d_tile_sse, int* d_status) {
+template <class K, class... Args>
+static cudaError_t launch_with_smem(K kernel, int grid, int threads, int smem, cudaStream_t stream, Args... args) {
   // dynamic shared memory above 48 KB must be enabled per device
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
-  kernel<<<grid, threads, smem, stream>>>(d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status);
+  kernel<<<grid, threads, smem, stream>>>(args...);
   return cudaGetLastError();
+}
+
+template <class K>
+static cudaError_t occupancy_with_smem(int* n, K kernel, int threads, int smem) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kernel, threads, smem);
 }
 
 static int config_index(const ZonalConfig& c) {
@@ -859,15 +991,6 @@ cudaError_t launch_zonal_config(const ZonalConfig& cfg, const ImageJob* d_jobs, 
   return cudaErrorInvalidValue;
 }
 
-template <class K>
-static cudaError_t occupancy_with_smem(int* n, K kernel, int threads, int smem) {
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kernel, threads, smem);
-}
-
 int zonal_config_max_ctas_per_sm(const ZonalConfig& cfg) {
   int n = 0;
   cudaError_t e = cudaErrorInvalidValue;
@@ -891,9 +1014,12 @@ cudaError_t launch_quant(const ImageJob* d_jobs, int njobs, long long ntiles, co
                          int16_t* d_levels, float* d_tile_sse, int* d_status, int grid,
                          cudaStream_t stream) {
   if (ntiles <= 0) return cudaSuccess;
-  quant_kernel<<<grid, kThreadsPerCta, 0, stream>>>(d_jobs, njobs, ntiles, d_qtab, d_levels, d_tile_sse,
-                                                      d_status);
-  return cudaGetLastError();
+  if (ntiles >= (1LL << 30)) return cudaErrorInvalidValue;  // tile indices are 32-bit in the kernel
+  if (d_levels)
+    return launch_with_smem(quant_kernel<true>, grid, 128, 4 * kQuantWarpSmemBytes, stream, d_jobs, njobs, ntiles,
+                            d_qtab, d_levels, d_tile_sse, d_status);
+  return launch_with_smem(quant_kernel<false>, grid, 128, 4 * kQuantWarpSmemBytes, stream, d_jobs, njobs, ntiles,
+                          d_qtab, d_levels, d_tile_sse, d_status);
 }
 
 cudaError_t launch_psnr_finalize(const ImageJob* d_jobs, int njobs, long long ntiles, const float* d_tile_sse,
@@ -948,7 +1074,7 @@ cudaError_t launch_psnr_pair(int dtype, const void* d_a, long long pitch_a, cons
 int zonal_ctas_per_sm() { return zonal_config_max_ctas_per_sm(default_zonal_config()); }
 int quant_ctas_per_sm() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, quant_kernel, kThreadsPerCta, 0) != cudaSuccess || n < 1) n = 1;
+  if (occupancy_with_smem(&n, quant_kernel<false>, 128, 4 * kQuantWarpSmemBytes) != cudaSuccess || n < 1) n = 1;
   return n;
 }
 
