@@ -47,7 +47,10 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     ap.add_argument("--e2e-steps", type=int, default=30)
-    ap.add_argument("--no-extras", action="store_true", help="skip the mixed-batch and serving phases")
+    ap.add_argument("--no-extras", action="store_true", help="skip the quantisation, mixed-batch and serving phases")
+    ap.add_argument("--quant-only", action="store_true",
+                    help="run only the quantisation phase (--steps/--warmup apply) and print its JSON")
+    ap.add_argument("--quant-frames", type=int, default=24)
     ap.add_argument("--mixed-images", type=int, default=1000)
     ap.add_argument("--serve-rates", default="100,250,500,1000,2000,5000")
     return ap.parse_args()
@@ -221,6 +224,48 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# --------------------------------------------------------------------------
+def quant_phase(torch, atdct16, synth, dev, n_frames, steps, warmup, peak_gbs):
+    """4:2:0 int16 residual frames (1920x1088 luma + two 960x544 chroma
+    planes, Laplace(0, 6) with 30 % zeros, seed 3), every plane quantised at
+    each QP in {22, 27, 32, 37} in one call: the first n_frames frames of the
+    240-frame sequence.  Reports throughput and the HBM fraction of the
+    quantisation kernel (4 bytes per sample: int16 in, int16 out), without
+    and with the optional level output (+2 bytes per sample)."""
+    frames = synth.residual_frames(n_frames)
+    planes = [torch.from_numpy(p).to(dev) for fr in frames for p in fr]
+    qps = synth.QUANT_QP_SWEEP
+    outs = [[torch.empty_like(p) for p in planes] for _ in qps]
+    descs = [atdct16.image(p, o, qp) for qp, oo in zip(qps, outs) for p, o in zip(planes, oo)]
+    samples = sum(p.numel() for p in planes) * len(qps)
+    plan = atdct16.Plan(atdct16.I16, max_images=len(descs), workspace_bytes=1 << 30)
+    psnr = torch.empty(len(descs), dtype=torch.float64, device=dev)
+    levels = torch.empty(samples, dtype=torch.int16, device=dev)
+    res = {"frames": n_frames, "planes_per_qp": len(planes), "qps": list(qps), "samples_per_step": samples,
+           "steps": steps}
+    for tag, lv in (("no_levels", None), ("levels", levels)):
+        for _ in range(max(warmup, 3)):
+            plan.compress_quant(descs, psnr, levels=lv)
+        torch.cuda.synchronize()
+        plan.set_profiling(True)
+        plan.profile()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.compress_quant(descs, psnr, levels=lv)
+        e1.record()
+        torch.cuda.synchronize()
+        n, kms = plan.profile()
+        plan.set_profiling(False)
+        ms = e0.elapsed_time(e1) / steps
+        k = kms / max(n, 1)
+        byts = samples * (6 if lv is not None else 4)
+        res[tag] = {"ms_per_step": ms, "kernel_ms": k, "gsamples_s": samples / (ms / 1e3) / 1e9,
+                    "kernel_gbs": byts / (k / 1e3) / 1e9, "kernel_frac_hbm": byts / (k / 1e3) / 1e9 / peak_gbs}
+    res["mean_psnr_db"] = float(psnr.mean().item())
+    return res
 
 
 # --------------------------------------------------------------------------
@@ -510,6 +555,8 @@ def run_ours(args):
         if not args.no_extras:
             del sets
             torch.cuda.empty_cache()
+            line["quant"] = quant_phase(torch, atdct16, synth, dev, args.quant_frames, 20, 3, peak)
+            torch.cuda.empty_cache()
             line["mixed_batch"] = mixed_batch_phase(torch, atdct16, synth, dev, args.mixed_images)
             torch.cuda.empty_cache()
             rates = [float(v) for v in args.serve_rates.split(",") if v]
@@ -521,10 +568,28 @@ def run_ours(args):
     return 0
 
 
+def run_quant_only(args):
+    """The quantisation phase alone, on one GPU (profiling entry)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_1606_05562_gb300 import atdct16, synth
+    from paper_1606_05562_gb300 import build as b
+
+    b.build()
+    peak, _ = measured_peak_hbm()
+    res = quant_phase(torch, atdct16, synth, dev, args.quant_frames, args.steps, args.warmup, peak)
+    print(json.dumps({"quant": res}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.quant_only:
+        return run_quant_only(args)
     return run_ours(args)
 
 

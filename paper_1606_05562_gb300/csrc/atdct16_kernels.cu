@@ -514,6 +514,13 @@ constexpr int kQuantWarpSmemBytes = 16 * (kZT2Units + kQStageUnits);
 
 __device__ __forceinline__ float i16_lo(unsigned w) { return (float)(short)(w & 0xffffu); }
 __device__ __forceinline__ float i16_hi(unsigned w) { return (float)(short)(w >> 16); }
+// int16 field of a word -> 2^23 + 32768 + v as an exact float (offset binary
+// placed in the mantissa): one logic op (low field) or a permute plus a logic
+// op (high field), on the integer pipe.
+__device__ __forceinline__ float i16_lo_m(unsigned w) { return __uint_as_float(((w & 0xffffu) ^ 0x8000u) | 0x4B000000u); }
+__device__ __forceinline__ float i16_hi_m(unsigned w) {
+  return __uint_as_float(__byte_perm(w, 0x4B00u, 0x5432u) ^ 0x8000u);
+}
 
 __device__ __forceinline__ float2 f2abs(float2 v) {
   return make_float2(__uint_as_float(__float_as_uint(v.x) & 0x7fffffffu),
@@ -530,6 +537,13 @@ __device__ __forceinline__ float2 f2copysign(float2 m, float2 s) {
   return make_float2(__uint_as_float((__float_as_uint(m.x) & 0x7fffffffu) | (__float_as_uint(s.x) & 0x80000000u)),
                      __uint_as_float((__float_as_uint(m.y) & 0x7fffffffu) | (__float_as_uint(s.y) & 0x80000000u)));
 }
+
+// Row u of T has nnz_u = 48 / W_u nonzeros: 16, 12 or 8 (class 0, 1, 2);
+// quant_class_row gives one row of each class.
+__host__ __device__ constexpr int quant_uclass(int u) {
+  return (0x56945290u >> (2 * u)) & 3u;  // classes of u = 0..15: 0 0 1 2 2 0 1 1 0 1 1 2 2 1 1 1
+}
+__host__ __device__ constexpr int quant_class_row(int cl) { return cl == 0 ? 0 : (cl == 1 ? 2 : 3); }
 
 struct QuantTile {
   const uint8_t* src;  // row 2j of block p of this lane
@@ -647,9 +661,26 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
   } else {
     cp_async_commit();
   }
+  // Quantiser constants of the lane's two columns c = 2j + i: s_u s_v takes
+  // one of three values per column (nnz_u in {16, 12, 8}), so k and g are
+  // three register pairs per column, refreshed when the QP changes.
+  int wq = -1;
+  float kq[2][3], gq[2][3], qstep = 1.f;
   int st = 0;
   while (true) {
     cp_async_wait<1>();
+    if (cur.qp != wq) {
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int cl = 0; cl < 3; ++cl) {
+          const float4 q = __ldg(qtab + ((long long)cur.qp * 16 + 2 * j + i) * 16 + quant_class_row(cl));
+          kq[i][cl] = q.x;
+          gq[i][cl] = q.z;
+          qstep = q.w;
+        }
+      wq = cur.qp;
+    }
     uint4 X[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) X[k] = stg[256 * st + 32 * k];
@@ -665,7 +696,8 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
         for (int n = 0; n < 16; ++n) {
           const unsigned wa = word_of(X[2 * tr + (n >> 3)], (n & 7) >> 1);
           const unsigned wb = word_of(X[4 + 2 * tr + (n >> 3)], (n & 7) >> 1);
-          xv[n] = (n & 1) ? make_float2(i16_hi(wa), i16_hi(wb)) : make_float2(i16_lo(wa), i16_lo(wb));
+          const float2 m = (n & 1) ? make_float2(i16_hi_m(wa), i16_hi_m(wb)) : make_float2(i16_lo_m(wa), i16_lo_m(wb));
+          xv[n] = __fadd2_rn(m, make_float2(-8421376.0f, -8421376.0f));  // exact v
         }
         fwd16(xv, rv);
 #pragma unroll
@@ -699,23 +731,24 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
         cv[2 * q + 1] = make_float2(v.z, v.w);
       }
       fwd16(cv, y);
-      const float4* const qc = qtab + ((long long)cur.qp * 16 + c) * 16;
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
-        const float4 q = __ldg(qc + u);  // (k, s, g, Qstep)
+        const float k = kq[i][quant_uclass(u)], g = gq[i][quant_uclass(u)];
         const float2 a = f2abs(y[u]);
-        const float2 b = __fadd2_rn(__fmul2_rn(a, make_float2(q.x, q.x)), make_float2(0.5f, 0.5f));
+        const float2 t = __fmul2_rn(a, make_float2(k, k));
+        const float2 b = __fadd2_rn(t, make_float2(0.5f, 0.5f));
         const float2 f = f2add_rm(b, make_float2(8388608.0f, 8388608.0f));  // floor(b) + 2^23
         const float2 L = __fadd2_rn(f, make_float2(-8388608.0f, -8388608.0f));
-        const float2 e = __ffma2_rn(L, make_float2(-q.w, -q.w), __fmul2_rn(a, make_float2(q.y, q.y)));
-        float2& s = (u & 1) ? acc1 : acc;
-        s = __ffma2_rn(e, e, s);
+        // B - B' = Qstep (|Y| s / Qstep - L) ~ Qstep (t - L); Qstep^2 is applied per tile
+        const float2 e = bsub(t, L);
+        float2& sacc = (u & 1) ? acc1 : acc;
+        sacc = __ffma2_rn(e, e, sacc);
         if (kLevels) {
           const int la = (int)(__float_as_uint(f.x) - 0x4B000000u), lb = (int)(__float_as_uint(f.y) - 0x4B000000u);
           if (va) levels[cur.lvl + u * 16 + c] = (int16_t)(y[u].x < 0.f ? -la : la);
           if (vb) levels[cur.lvl + 4 * 256 + u * 16 + c] = (int16_t)(y[u].y < 0.f ? -lb : lb);
         }
-        y[u] = f2copysign(__fmul2_rn(L, make_float2(q.z, q.z)), y[u]);
+        y[u] = f2copysign(__fmul2_rn(L, make_float2(g, g)), y[u]);
       }
       float2 uo[16];
       inv16(y, uo);
@@ -756,7 +789,7 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
 
     acc = __fadd2_rn(acc, acc1);
     const float tot = warp_sum((va ? acc.x : 0.f) + (vb ? acc.y : 0.f));
-    if (lane == 0) tile_sse[cur.t] = tot;
+    if (lane == 0) tile_sse[cur.t] = tot * qstep * qstep;
     __syncwarp();  // buffer reads done before the next tile's writes
 
     if (!have_nxt) break;
