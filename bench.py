@@ -135,10 +135,18 @@ def measured_peak_hbm():
 
 
 def kernel_source_sha256():
+    """Hash of the zonal kernel's source: the headers it includes and the part
+    of atdct16_kernels.cu before the quantisation kernel (its helpers and the
+    kernel itself)."""
     h = hashlib.sha256()
-    for f in ("atdct16_kernels.cu", "atdct16_butterfly.cuh", "atdct16_ops.cuh", "atdct16_internal.h"):
-        with open(os.path.join(ROOT, "paper_1606_05562_gb300", "csrc", f), "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_1606_05562_gb300", "csrc")
+    for f in ("atdct16_butterfly.cuh", "atdct16_ops.cuh", "atdct16_internal.h"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "atdct16_kernels.cu"), "rb") as fh:
+        text = fh.read()
+    cut = text.find(b"// Fused quantisation")
+    h.update(text if cut < 0 else text[:cut])
     return h.hexdigest()
 
 
@@ -231,14 +239,17 @@ def quant_phase(torch, atdct16, synth, dev, n_frames, steps, warmup, peak_gbs):
     """4:2:0 int16 residual frames (1920x1088 luma + two 960x544 chroma
     planes, Laplace(0, 6) with 30 % zeros, seed 3), every plane quantised at
     each QP in {22, 27, 32, 37} in one call: the first n_frames frames of the
-    240-frame sequence.  Reports throughput and the HBM fraction of the
-    quantisation kernel (4 bytes per sample: int16 in, int16 out), without
-    and with the optional level output (+2 bytes per sample)."""
+    240-frame sequence, one input copy per QP.  Reports throughput and the
+    HBM fraction of the quantisation kernel (4 bytes per sample: int16 in,
+    int16 out), without and with the optional level output (+2 bytes per
+    sample)."""
     frames = synth.residual_frames(n_frames)
     planes = [torch.from_numpy(p).to(dev) for fr in frames for p in fr]
     qps = synth.QUANT_QP_SWEEP
+    # one copy of the input per QP, so no QP reads another's input from L2
+    ins = [[p.clone() for p in planes] for _ in qps]
     outs = [[torch.empty_like(p) for p in planes] for _ in qps]
-    descs = [atdct16.image(p, o, qp) for qp, oo in zip(qps, outs) for p, o in zip(planes, oo)]
+    descs = [atdct16.image(p, o, qp) for qp, ii, oo in zip(qps, ins, outs) for p, o in zip(ii, oo)]
     samples = sum(p.numel() for p in planes) * len(qps)
     plan = atdct16.Plan(atdct16.I16, max_images=len(descs), workspace_bytes=1 << 30)
     psnr = torch.empty(len(descs), dtype=torch.float64, device=dev)
