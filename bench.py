@@ -249,7 +249,7 @@ def quant_phase(torch, atdct16, synth, dev, n_frames, steps, warmup, peak_gbs):
     # one copy of the input per QP, so no QP reads another's input from L2
     ins = [[p.clone() for p in planes] for _ in qps]
     outs = [[torch.empty_like(p) for p in planes] for _ in qps]
-    descs = [atdct16.image(p, o, qp) for qp, ii, oo in zip(qps, ins, outs) for p, o in zip(ii, oo)]
+    descs = atdct16.descriptors([atdct16.image(p, o, qp) for qp, ii, oo in zip(qps, ins, outs) for p, o in zip(ii, oo)])
     samples = sum(p.numel() for p in planes) * len(qps)
     plan = atdct16.Plan(atdct16.I16, max_images=len(descs), workspace_bytes=1 << 30)
     psnr = torch.empty(len(descs), dtype=torch.float64, device=dev)
@@ -459,7 +459,8 @@ def run_ours(args):
     for _ in range(N_SETS):
         src = base.unsqueeze(0).repeat(nr, 1, 1, 1).contiguous()
         dst = torch.empty_like(src)
-        descs = [atdct16.image(src[k, i], dst[k, i], r) for k, r in enumerate(R_SWEEP) for i in range(N_IMAGES)]
+        descs = atdct16.descriptors(
+            [atdct16.image(src[k, i], dst[k, i], r) for k, r in enumerate(R_SWEEP) for i in range(N_IMAGES)])
         sets.append((src, dst, descs))
     plan = atdct16.Plan(atdct16.U8, max_images=jobs)
     psnr = torch.empty(jobs, dtype=torch.float64, device=dev)
@@ -521,7 +522,8 @@ def run_ours(args):
     d_dst = torch.empty((nr, N_IMAGES, SIDE, SIDE), dtype=torch.uint8, device=dev)
     h_dst = torch.empty(d_dst.shape, dtype=torch.uint8).pin_memory()
     h_psnr = torch.empty(jobs, dtype=torch.float64).pin_memory()
-    e2e_descs = [atdct16.image(d_src[i], d_dst[k, i], r) for k, r in enumerate(R_SWEEP) for i in range(N_IMAGES)]
+    e2e_descs = atdct16.descriptors(
+        [atdct16.image(d_src[i], d_dst[k, i], r) for k, r in enumerate(R_SWEEP) for i in range(N_IMAGES)])
 
     def e2e_step():
         d_src.copy_(h_src, non_blocking=True)

@@ -157,6 +157,18 @@ def host_butterfly(values, inverse=False):
     return list(o)
 
 
+def descriptors(images):
+    """A reusable C array of Image descriptors.  Building the array costs
+    about 0.2 us per image on the host; a caller that compresses the same
+    set of buffers repeatedly builds it once and passes it instead of a
+    list."""
+    return (Image * len(images))(*images)
+
+
+def _as_array(images):
+    return images if isinstance(images, C.Array) else descriptors(images)
+
+
 def image(src, dst, param, width=None, height=None):
     """Descriptor for a 2-D (H, W) torch tensor pair (row pitch from strides)."""
     h, w = src.shape[-2], src.shape[-1]
@@ -201,13 +213,14 @@ class Plan:
                                      out.stride(-2) * out.element_size(), _stream(stream)), "inverse")
 
     def compress_zonal(self, images, psnr, sse=None, stream=None):
-        """``images``: list of Image descriptors (param = r)."""
-        arr = (Image * len(images))(*images)
+        """``images``: list of Image descriptors (param = r), or an array from
+        ``descriptors``."""
+        arr = _as_array(images)
         _check(lib().atdct16_compress_zonal(self._h, arr, len(images), _ptr(psnr), _ptr(sse), _stream(stream)),
                "compress_zonal")
 
     def compress_quant(self, images, psnr, levels=None, sse=None, stream=None):
-        arr = (Image * len(images))(*images)
+        arr = _as_array(images)
         _check(lib().atdct16_compress_quant(self._h, arr, len(images), _ptr(levels), _ptr(psnr), _ptr(sse),
                                             _stream(stream)), "compress_quant")
 
@@ -234,7 +247,7 @@ class Batch:
     def __init__(self, plan, images, psnr, sse=None, flags=BATCH_AUTOTUNE | BATCH_GRAPH, stream=None):
         self._h = C.c_void_p()
         self.plan = plan  # keeps the plan alive
-        arr = (Image * len(images))(*images)
+        arr = _as_array(images)
         _check(lib().atdct16_batch_create(plan.handle, arr, len(images), _ptr(psnr), _ptr(sse), flags,
                                           _stream(stream), C.byref(self._h)), "batch_create")
 
@@ -314,7 +327,7 @@ class Server:
 def compress_zonal_noalloc(images, psnr, sse=None, stream=None):
     """Zonal compression through the entry point that allocates nothing (no
     plan; at most 64 images and 131072 tiles per call)."""
-    arr = (Image * len(images))(*images)
+    arr = _as_array(images)
     _check(lib().atdct16_compress_zonal_noalloc(arr, len(images), _ptr(psnr), _ptr(sse), _stream(stream)),
            "compress_zonal_noalloc")
 

@@ -21,14 +21,22 @@ struct atdct16_plan_st {
   int num_sms = 0;
   int zonal_grid = 0;
   int quant_grid = 0;
-  ImageJob* d_jobs = nullptr;
-  ImageJob* h_jobs = nullptr;           // pinned staging for the descriptor upload
+  ImageJob* d_jobs = nullptr;           // descriptors of the current call (one of d_jobs_buf[0..1])
+  ImageJob* h_jobs = nullptr;           // pinned staging of the current call (one of h_jobs_buf[0..1])
+  // Two descriptor buffers, used by alternate calls: the upload of a call's
+  // descriptors runs on copy_stream while the previous call still computes.
+  ImageJob* d_jobs_buf[2] = {nullptr, nullptr};
+  ImageJob* h_jobs_buf[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t uploaded[2] = {nullptr, nullptr};  // upload of buffer b complete
+  cudaEvent_t consumed[2] = {nullptr, nullptr};  // kernels reading buffer b complete
+  bool uploaded_pending[2] = {false, false};
+  bool consumed_pending[2] = {false, false};
+  int buf = 1;                                   // buffer of the current call
   float2* d_wtab = nullptr;             // zonal weights [r][c][u]
   float4* d_qtab = nullptr;             // quantiser constants [QP][c][u]
   float* d_tile_sse = nullptr;          // per-tile SSE partials
   int* d_status = nullptr;
-  cudaEvent_t upload_done = nullptr;    // staging buffers may be rewritten after this
-  bool upload_pending = false;
   cudaStream_t last_stream = nullptr;
   // autotuner results for this plan: batch-shape key -> (config, CTAs per SM, ms)
   struct Tuned {
@@ -101,18 +109,22 @@ atdct16_status check_image(const atdct16_image& im, int elem, bool need_dst) {
   return ATDCT16_OK;
 }
 
-// Fill the pinned descriptor staging buffer and upload it on `stream`.
+// Fill a pinned descriptor staging buffer and upload it.  Calls alternate
+// between two buffers; the upload runs on the plan's copy stream (so it
+// overlaps the previous call's kernels) and `stream` waits for it.  While
+// `stream` is being captured into a graph the upload goes on `stream` itself.
 atdct16_status stage_jobs(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n, int elem,
                           cudaStream_t stream, long long* ntiles_out, bool with_level_base) {
-  if (plan->upload_pending) {
-    // the previous upload must have left the staging buffers before reuse
-    if (cudaEventSynchronize(plan->upload_done) != cudaSuccess) return ATDCT16_ECUDA;
-    plan->upload_pending = false;
+  const int b = plan->buf ^ 1;
+  if (plan->uploaded_pending[b]) {
+    if (cudaEventSynchronize(plan->uploaded[b]) != cudaSuccess) return ATDCT16_ECUDA;
+    plan->uploaded_pending[b] = false;
   }
+  ImageJob* const hj = plan->h_jobs_buf[b];
   long long tiles = 0, blocks = 0;
   for (int i = 0; i < n; ++i) {
     const atdct16_image& im = h_images[i];
-    ImageJob& J = plan->h_jobs[i];
+    ImageJob& J = hj[i];
     J.src = static_cast<const uint8_t*>(im.src);
     J.dst = static_cast<uint8_t*>(im.dst);
     J.src_pitch = im.src_pitch;
@@ -127,14 +139,39 @@ atdct16_status stage_jobs(atdct16_plan_t plan, const atdct16_image* h_images, in
     blocks += (long long)(im.width / 16) * (im.height / 16);
   }
   if (tiles > plan->max_tiles) return ATDCT16_ENOMEM;
-  cudaError_t e = cudaMemcpyAsync(plan->d_jobs, plan->h_jobs, sizeof(ImageJob) * n, cudaMemcpyHostToDevice, stream);
-  if (e == cudaSuccess) e = cudaEventRecord(plan->upload_done, stream);
-  if (e != cudaSuccess) return ATDCT16_ECUDA;
-  plan->upload_pending = true;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return ATDCT16_ECUDA;
+  const size_t bytes = sizeof(ImageJob) * n;
+  cudaError_t e = cudaSuccess;
+  if (cap == cudaStreamCaptureStatusNone) {
+    if (plan->consumed_pending[b]) e = cudaStreamWaitEvent(plan->copy_stream, plan->consumed[b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(plan->d_jobs_buf[b], hj, bytes, cudaMemcpyHostToDevice, plan->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(plan->uploaded[b], plan->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, plan->uploaded[b], 0);
+    if (e != cudaSuccess) return ATDCT16_ECUDA;
+    plan->uploaded_pending[b] = true;
+  } else {
+    // inside a capture: everything on the capturing stream, after any work
+    // still reading this buffer has drained
+    if (plan->consumed_pending[b] && cudaEventSynchronize(plan->consumed[b]) != cudaSuccess) return ATDCT16_ECUDA;
+    e = cudaMemcpyAsync(plan->d_jobs_buf[b], hj, bytes, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return ATDCT16_ECUDA;
+  }
+  plan->consumed_pending[b] = false;
+  plan->buf = b;
+  plan->d_jobs = plan->d_jobs_buf[b];
+  plan->h_jobs = hj;
   plan->last_stream = stream;
   *ntiles_out = tiles;
   (void)elem;
   return ATDCT16_OK;
+}
+
+// After the kernels that read the current descriptor buffer are enqueued.
+void jobs_consumed(atdct16_plan_t plan, cudaStream_t stream) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
+  if (cudaEventRecord(plan->consumed[plan->buf], stream) == cudaSuccess) plan->consumed_pending[plan->buf] = true;
 }
 
 }  // namespace
@@ -185,15 +222,19 @@ atdct16_status atdct16_host_butterfly(const int32_t* in, int32_t* out, int32_t i
 atdct16_status atdct16_plan_destroy(atdct16_plan_t plan) {
   if (!plan) return ATDCT16_EINVAL;
   cudaSetDevice(plan->device);
-  if (plan->upload_done) cudaEventSynchronize(plan->upload_done);
   if (plan->last_stream) cudaStreamSynchronize(plan->last_stream);
-  cudaFree(plan->d_jobs);
+  if (plan->copy_stream) cudaStreamSynchronize(plan->copy_stream);
+  cudaFree(plan->d_jobs_buf[0]);
   cudaFree(plan->d_wtab);
   cudaFree(plan->d_qtab);
   cudaFree(plan->d_tile_sse);
   cudaFree(plan->d_status);
-  cudaFreeHost(plan->h_jobs);
-  if (plan->upload_done) cudaEventDestroy(plan->upload_done);
+  cudaFreeHost(plan->h_jobs_buf[0]);
+  for (int b = 0; b < 2; ++b) {
+    if (plan->uploaded[b]) cudaEventDestroy(plan->uploaded[b]);
+    if (plan->consumed[b]) cudaEventDestroy(plan->consumed[b]);
+  }
+  if (plan->copy_stream) cudaStreamDestroy(plan->copy_stream);
   for (cudaEvent_t ev : plan->prof_events) cudaEventDestroy(ev);
   delete plan;
   return ATDCT16_OK;
@@ -246,13 +287,23 @@ atdct16_status atdct16_plan_create(atdct16_plan_t* out, atdct16_dtype dtype, int
   }
 
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMalloc(&plan->d_jobs, sizeof(ImageJob) * max_images);
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_jobs_buf[0], 2 * sizeof(ImageJob) * max_images);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_wtab, sizeof(float2) * kZonalTableEntries);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_qtab, sizeof(float4) * kQuantTableEntries);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_tile_sse, sizeof(float) * plan->max_tiles);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_status, sizeof(int));
-  if (e == cudaSuccess) e = cudaHostAlloc(&plan->h_jobs, sizeof(ImageJob) * max_images, cudaHostAllocDefault);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->upload_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaHostAlloc(&plan->h_jobs_buf[0], 2 * sizeof(ImageJob) * max_images, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaEventCreateWithFlags(&plan->uploaded[b], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->consumed[b], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) {
+    plan->d_jobs_buf[1] = plan->d_jobs_buf[0] + max_images;
+    plan->h_jobs_buf[1] = plan->h_jobs_buf[0] + max_images;
+    plan->d_jobs = plan->d_jobs_buf[0];
+    plan->h_jobs = plan->h_jobs_buf[0];
+  }
   if (e == cudaSuccess) e = cudaMemcpy(plan->d_wtab, wtab.data(), sizeof(float2) * kZonalTableEntries, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(plan->d_qtab, qtab.data(), sizeof(float4) * kQuantTableEntries, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(plan->d_status, 0, sizeof(int));
@@ -303,6 +354,7 @@ atdct16_status atdct16_compress_zonal(atdct16_plan_t plan, const atdct16_image* 
   prof_end(plan, pk, stream);
   if (e == cudaSuccess)
     e = launch_psnr_finalize(plan->d_jobs, n, ntiles, plan->d_tile_sse, 255.0, d_psnr, d_sse, stream);
+  if (e == cudaSuccess) jobs_consumed(plan, stream);
   return from_cuda(e);
 }
 
@@ -325,6 +377,7 @@ atdct16_status atdct16_compress_quant(atdct16_plan_t plan, const atdct16_image* 
   prof_end(plan, pk, stream);
   if (e == cudaSuccess)
     e = launch_psnr_finalize(plan->d_jobs, n, ntiles, plan->d_tile_sse, 255.0, d_psnr, d_sse, stream);
+  if (e == cudaSuccess) jobs_consumed(plan, stream);
   return from_cuda(e);
 }
 

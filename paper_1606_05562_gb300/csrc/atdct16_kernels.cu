@@ -207,6 +207,12 @@ __device__ __forceinline__ uint4 ld_stream_na(const uint8_t* ptr) {
   return v;
 }
 
+// Programmatic dependent launch: a kernel lets the next kernel of its stream
+// (launched with the programmatic-serialisation attribute) be scheduled
+// early; that kernel waits for this grid's completion and memory flush.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait_primary() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Asynchronous 16-byte global -> shared copy (L2 only), its group commit and
 // the wait until at most N of this thread's groups are still in flight.
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
@@ -228,6 +234,7 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
   float4* const wsm = t2 + kZT2Units;
   uint4* const stg = reinterpret_cast<uint4*>(wsm + kZWUnits) + lane;  // + 128 s + 32 k
   const int ntiles = (int)ntiles_ll;  // the launcher checks ntiles < 2^31
+  pdl_launch_dependents();  // the PSNR finalize may be scheduled; it waits for this grid
   // row-pass words: 13-bit fields (bias 4096) for a float column pass,
   // int16 fields (bias 32768) for an integer one
   using Row = typename std::conditional<kColSwar, Swar16, SwarRow>::type;
@@ -566,6 +573,7 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
   float4* const tb = reinterpret_cast<float4*>(qsmem + warp * kQuantWarpSmemBytes);
   uint4* const stg = reinterpret_cast<uint4*>(tb + kZT2Units) + lane;  // + 256 s + 32 k
   const int ntiles = (int)ntiles_ll;  // the launcher checks ntiles < 2^30
+  pdl_launch_dependents();  // the PSNR finalize may be scheduled; it waits for this grid
   constexpr int kWarps = 4;
   const int nwarps = gridDim.x * kWarps;
   const int per_warp = (ntiles + nwarps - 1) / nwarps;
@@ -808,6 +816,7 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
 __global__ void psnr_finalize_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
                                      const float* __restrict__ tile_sse, double peak,
                                      double* __restrict__ psnr, double* __restrict__ sse_out) {
+  pdl_wait_primary();  // the producing kernel's partials are complete and visible
   const int lane = threadIdx.x & 31;
   const int job = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (job >= njobs) return;
@@ -1059,9 +1068,17 @@ cudaError_t launch_psnr_finalize(const ImageJob* d_jobs, int njobs, long long nt
                                  double peak, double* d_psnr, double* d_sse, cudaStream_t stream) {
   if (njobs <= 0) return cudaSuccess;
   const int warps = 8;
-  psnr_finalize_kernel<<<(njobs + warps - 1) / warps, 32 * warps, 0, stream>>>(d_jobs, njobs, ntiles, d_tile_sse,
-                                                                               peak, d_psnr, d_sse);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((njobs + warps - 1) / warps);
+  cfg.blockDim = dim3(32 * warps);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, psnr_finalize_kernel, d_jobs, njobs, ntiles, d_tile_sse, peak, d_psnr, d_sse);
 }
 
 cudaError_t launch_forward(int dtype, const void* d_src, long long pitch, int w, int h, int32_t* d_coef,
