@@ -238,6 +238,12 @@ class Plan:
 
 
 BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2
+ZONAL_VARIANTS = ("f32", "swar", "mma")
+
+
+def batch_variant(v):
+    """Flag that pins the zonal kernel variant of a Batch (0, 1 or 2)."""
+    return (v + 1) << 8
 
 
 class Batch:
@@ -259,7 +265,7 @@ class Batch:
         t, ms = C.c_int64(), C.c_float()
         _check(lib().atdct16_batch_info(self._h, C.byref(v), C.byref(w), C.byref(p), C.byref(g), C.byref(t),
                                         C.byref(ms)), "batch_info")
-        return {"variant": ("f32", "swar")[v.value], "warps": w.value, "prefetch": p.value, "grid": g.value,
+        return {"variant": ZONAL_VARIANTS[v.value], "warps": w.value, "prefetch": p.value, "grid": g.value,
                 "tiles": t.value, "tuned_ms": ms.value}
 
     def close(self):

@@ -143,7 +143,7 @@ cudaError_t launch_batch_once(atdct16_batch_st* b, const ZonalConfig& cfg, int g
 // Time every candidate launch shape on the batch (min of 3 after a warm-up).
 atdct16_status autotune(atdct16_batch_st* b, int sms, cudaStream_t stream) {
   const ZonalConfig cands[] = {
-      {kZonalSwar, 4, 1}, {kZonalF32, 4, 1},
+      {kZonalSwar, 4, 1}, {kZonalF32, 4, 1}, {kZonalMma, 4, 1},
   };
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return ATDCT16_ECUDA;
@@ -208,7 +208,13 @@ atdct16_status atdct16_batch_create(atdct16_plan_t plan, const atdct16_image* h_
                                     double* d_sse, uint32_t flags, cudaStream_t stream, atdct16_batch_t* out) {
   if (!out) return ATDCT16_EINVAL;
   *out = nullptr;
-  if (!plan || !h_images || !d_psnr || n < 1 || (flags & ~(ATDCT16_BATCH_AUTOTUNE | ATDCT16_BATCH_GRAPH)))
+  if (!plan || !h_images || !d_psnr || n < 1 ||
+      (flags & ~(ATDCT16_BATCH_AUTOTUNE | ATDCT16_BATCH_GRAPH | ATDCT16_BATCH_VARIANT_MASK)))
+    return ATDCT16_EINVAL;
+  // a pinned kernel variant (1 + variant in the variant field) excludes autotuning
+  const unsigned pinned = (flags & ATDCT16_BATCH_VARIANT_MASK) >> ATDCT16_BATCH_VARIANT_SHIFT;
+  if (pinned && ((flags & ATDCT16_BATCH_AUTOTUNE) ||
+                 !zonal_config_supported(ZonalConfig{(int)pinned - 1, kZonalWarps, 1})))
     return ATDCT16_EINVAL;
   for (int i = 0; i < n; ++i) {
     const atdct16_status s = check_zonal_image(h_images[i]);
@@ -257,7 +263,7 @@ atdct16_status atdct16_batch_create(atdct16_plan_t plan, const atdct16_image* h_
   }
 
   const int sms = plan_num_sms(plan);
-  b->cfg = default_zonal_config();
+  b->cfg = pinned ? ZonalConfig{(int)pinned - 1, kZonalWarps, 1} : default_zonal_config();
   b->ctas = zonal_config_max_ctas_per_sm(b->cfg);
   if (flags & ATDCT16_BATCH_AUTOTUNE) {
     const unsigned long long key = shape_key(h_images, n, sms);

@@ -47,8 +47,9 @@ cudaError_t launch_zonal(const ImageJob* d_jobs, int njobs, long long ntiles, co
 // Launch shapes of the fused zonal kernel (chosen by the batch autotuner).
 constexpr int kZonalF32 = 0;   // integer row pass, FP32 column pass and inverse
 constexpr int kZonalSwar = 1;  // whole forward transform on the integer pipe (int16 SWAR)
+constexpr int kZonalMma = 2;   // forward transform as f16 tensor-core products (exact)
 struct ZonalConfig {
-  int variant;   // kZonalF32 or kZonalSwar
+  int variant;   // kZonalF32, kZonalSwar or kZonalMma
   int warps;     // warps per CTA: 2, 4 or 8 (SWAR: 4)
   int prefetch;  // 1: load the next tile while computing the current one
 };

@@ -219,6 +219,11 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
 }
+// The same with src_bytes (0 or 16) read and the rest of the 16 filled with zeros.
+__device__ __forceinline__ void cp_async16_zfill(void* smem_dst, const void* gsrc, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gsrc), "r"(src_bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -486,6 +491,374 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     const float tot = warp_sum((va ? acc.x : 0.f) + (vb ? acc.y : 0.f));
     if (lane == 0) tile_sse[cur.t] = tot * (1.0f / (256.0f * 2304.0f));
     __syncwarp();  // buffer reads done before the next tile's writes
+
+    if (!have_nxt) break;
+    cur = nxt;
+    nxt = fut;
+    have_nxt = have_fut;
+    st ^= 1;
+  }
+  cp_async_wait<0>();
+  if (!ok && lane == 0) set_status(status, kDevBadJob);
+}
+
+// --------------------------------------------------------------------------
+// Fused zonal compression with the forward transform on the tensor cores.
+//
+// The 2-D forward transform of a block is two exact 16x16 integer products,
+// P = T X and Y = P T^T, and both run as m16n8k16 f16 MMAs with FP32
+// accumulation: X enters as the f16 values 1024 + x (one byte permute per
+// pair, straight from an ldmatrix.trans of the staged rows, which hands each
+// lane the B-operand pairs (rows 2q, 2q+1) of pixel columns 2g and 2g+1);
+// P's DC row is centred through the accumulator initialisation
+// (-16384 - 2048), so every entry of P lies in [-2048, 2040] and is exact in
+// f16; P's accumulator fragments are the A operand of the second product
+// (its column order is absorbed into a permuted constant T^T), whose
+// accumulator starts at +32768 on Y[0][0] to undo the centring.  All
+// products are integers below 2^24: Y is exact.
+//
+// Each lane then holds Y at the fixed positions (u, v) = (g, 2q..2q+1),
+// (g+8, ...), (g, 8+2q..), (g+8, 8+2q..) of every block (g = lane >> 2,
+// q = lane & 3), so the zonal weights of the warp's current r live in
+// registers (as f32x2 pairs over v, v+1).  The masked, weighted V goes to
+// the back-transpose buffer as (block p, block p+4) pairs; the inverse
+// column and row passes, the exact rounding and the stores are those of the
+// integer-pipe kernel.
+//
+// Shared memory per warp (13.4 KB): the back-transpose
+// unit(p, c, q) = R(p) + 8 c + (c & 14) + q, R = (0, 145, 292, 437)
+// (16-byte units, 579 of them), conflict-free for the MMA-side 8-byte
+// writes, the column pass's 16-byte reads and writes and the row pass's
+// 8-byte reads (lanes with odd j take their two rows in reverse order); and
+// two staging slots of 16 rows x 16 bytes per block, row r of block b at
+// 16 b + (r ^ x(b & 3)), x = (0, 1, 4, 5): conflict-free for the cp.async
+// writes and the ldmatrix reads.
+// --------------------------------------------------------------------------
+constexpr int kMUnits = 579;
+constexpr int kMStageUnits = 2 * 128;
+constexpr int kZonalMmaWarpSmemBytes = 16 * (kMUnits + kMStageUnits);
+
+__host__ __device__ constexpr int mma_region(int p) { return p == 0 ? 0 : (p == 1 ? 145 : (p == 2 ? 292 : 437)); }
+__host__ __device__ constexpr int mma_unit(int p, int c, int q) { return mma_region(p) + 8 * c + (c & 14) + q; }
+__device__ __forceinline__ int stage_slot(int b, int r) {
+  const int pb = b & 3;
+  return 16 * b + (r ^ ((pb & 1) | ((pb & 2) << 1)));
+}
+
+__device__ __forceinline__ void ldsm_x4_trans(unsigned addr, unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+// D = A B + C, m16n8k16, A row-major f16, B column-major f16, C/D f32
+__device__ __forceinline__ void mma_16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1,
+                                          const float (&c)[4]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%10, %11, %12, %13};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c[0]), "f"(c[1]), "f"(c[2]),
+        "f"(c[3]));
+}
+// (lo, hi) -> f16x2 with lo in the low half (exact for the integers used)
+__device__ __forceinline__ unsigned pack_f16x2(float lo, float hi) {
+  unsigned d;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ unsigned f16_of_t(int t) { return t == 0 ? 0u : (t > 0 ? 0x3C00u : 0xBC00u); }
+__device__ __forceinline__ unsigned f16x2_of_t(int lo, int hi) { return f16_of_t(lo) | (f16_of_t(hi) << 16); }
+
+template <int kWarps>
+__global__ void __launch_bounds__(32 * kWarps, 12 / kWarps)
+zonal_mma_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
+                 const float2* __restrict__ wtab, float* __restrict__ tile_sse, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char msmem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, q = lane & 3;  // MMA fragment coordinates
+  const int p = q, j = g;                 // back half: block pair p, row pair j
+  float4* const tb = reinterpret_cast<float4*>(msmem + warp * kZonalMmaWarpSmemBytes);
+  uint4* const stg = reinterpret_cast<uint4*>(tb + kMUnits);  // + 128 slot + stage_slot(b, r)
+  const int ntiles = (int)ntiles_ll;  // the launcher checks ntiles < 2^30
+  pdl_launch_dependents();
+
+  // ---- constant MMA operands from the Sec. 2 factorisation: columns of T
+  // are the butterfly's responses to unit vectors
+  unsigned ta[4], tbf[2][2];
+  {
+    // rows g and g + 8 of the columns k = 2q, 2q+1, 2q+8, 2q+9, 4q .. 4q+3
+    int tg[8], tg8[8];
+    const int ks[8] = {2 * q, 2 * q + 1, 2 * q + 8, 2 * q + 9, 4 * q, 4 * q + 1, 4 * q + 2, 4 * q + 3};
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      int e[16], col[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) e[k] = k == ks[n] ? 1 : 0;
+      fwd16(e, col);
+      int a = 0, b8 = 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        a = u == g ? col[u] : a;
+        b8 = u == g ? col[u + 8] : b8;
+      }
+      tg[n] = a;
+      tg8[n] = b8;
+    }
+    // stage 1, A = T (m = u, k = pixel row): rows g, g + 8; k = 2q, 2q+1, 2q+8, 2q+9
+    ta[0] = f16x2_of_t(tg[0], tg[1]);
+    ta[1] = f16x2_of_t(tg8[0], tg8[1]);
+    ta[2] = f16x2_of_t(tg[2], tg[3]);
+    ta[3] = f16x2_of_t(tg8[2], tg8[3]);
+    // stage 2, B[k][v] = T[v][col(k)], col(2q) = 4q, col(2q+1) = 4q+2,
+    // col(2q+8) = 4q+1, col(2q+9) = 4q+3; n = v = g (tile 0) or g + 8 (tile 1)
+    tbf[0][0] = f16x2_of_t(tg[4], tg[6]);
+    tbf[0][1] = f16x2_of_t(tg[5], tg[7]);
+    tbf[1][0] = f16x2_of_t(tg8[4], tg8[6]);
+    tbf[1][1] = f16x2_of_t(tg8[5], tg8[7]);
+  }
+
+  const int nwarps = gridDim.x * kWarps;
+  const int per_warp = (ntiles + nwarps - 1) / nwarps;
+  const int t_first = (blockIdx.x * kWarps + warp) * per_warp;
+  const int t_stop = min(ntiles, t_first + per_warp);
+  if (t_first >= t_stop) return;
+
+  int c_t = 0, c_end = 0, tiles_x = 1, tx = 0, nb_last = 8, r_job = 0, src_pitch = 0, dst_pitch = 0;
+  const uint8_t* src_band = nullptr;  // row 0 of the current band, tile column 0
+  uint8_t* dst_band = nullptr;        // this lane's row 2j of block p in tile column 0 of the band
+  auto enter = [&](int t) -> bool {
+    int job;
+    warp_find_job(jobs, njobs, t, job);
+    const ImageJob* J = jobs + job;
+    const long long tb0 = __ldg(&J->tile_begin);
+    tiles_x = __ldg(&J->tiles_x);
+    const long long te = tb0 + (long long)tiles_x * (__ldg(&J->height) >> 4);
+    if (t < tb0 || t >= te || tiles_x < 1) return false;
+    c_end = (int)min(te, (long long)t_stop);
+    const int lt = (int)(t - tb0);
+    const int ty = lt / tiles_x;
+    tx = lt - ty * tiles_x;
+    src_pitch = (int)__ldg(&J->src_pitch);
+    dst_pitch = (int)__ldg(&J->dst_pitch);
+    const long long row0 = (long long)ty * kTileH;
+    src_band = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->src))) +
+               (row0 + 2 * j) * src_pitch + 16 * p;
+    dst_band = reinterpret_cast<uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->dst))) +
+               (row0 + 2 * j) * dst_pitch + 16 * p;
+    nb_last = min(8, (__ldg(&J->width) - (tiles_x - 1) * kTileW) >> 4);
+    r_job = __ldg(&J->param);
+    c_t = t;
+    return true;
+  };
+  auto take = [&](ZonalTile& z) {
+    z.src = src_band + tx * kTileW;
+    z.dst = dst_band + tx * kTileW;
+    z.src_pitch = src_pitch;
+    z.dst_pitch = dst_pitch;
+    z.nb = tx == tiles_x - 1 ? nb_last : 8;
+    z.t = c_t;
+    z.r = r_job;
+  };
+  auto advance = [&]() -> bool {
+    ++c_t;
+    if (++tx == tiles_x) {
+      tx = 0;
+      src_band += (long long)kTileH * src_pitch;
+      dst_band += (long long)kTileH * dst_pitch;
+    }
+    return c_t >= t_stop || c_t < c_end || enter(c_t);
+  };
+  // Rows 2j, 2j+1 of blocks p and p+4 of tile z into staging slot st.
+  // Blocks past the image edge are filled with zeros (nothing is read):
+  // their coefficients and dropped energy are then exactly 0.
+  auto issue = [&](const ZonalTile& z, int st) {
+    uint4* const d = stg + 128 * st;
+    const int na = p < z.nb ? 16 : 0, nb4 = p + 4 < z.nb ? 16 : 0;
+    const uint8_t* sa = na ? z.src : z.src - 16 * p;  // a valid address either way
+    const uint8_t* sb = nb4 ? z.src + 64 : sa;
+    cp_async16_zfill(d + stage_slot(p, 2 * j), sa, na);
+    cp_async16_zfill(d + stage_slot(p, 2 * j + 1), sa + (na ? z.src_pitch : 0), na);
+    cp_async16_zfill(d + stage_slot(p + 4, 2 * j), sb, nb4);
+    cp_async16_zfill(d + stage_slot(p + 4, 2 * j + 1), sb + (nb4 ? z.src_pitch : 0), nb4);
+    cp_async_commit();
+  };
+
+  if (!enter(t_first)) {
+    if (lane == 0) set_status(status, kDevBadJob);
+    return;
+  }
+  bool ok = true;
+  int wr = -1;
+  // Zonal weights at this lane's coefficient positions, as f32x2 pairs over
+  // (v, v+1): [nt][h] = rows u = g + 8 h, columns v = 8 nt + 2q, +1;
+  // kw = keep W_u W_v, dw = (1 - keep) W_u W_v (the table holds them / 256)
+  float2 kwp[2][2], dwp[2][2];
+  const unsigned stg_base = (unsigned)__cvta_generic_to_shared(stg);
+  // back-transpose bases of this lane: V writes (float2 units), column lines, row reads
+  const int v_lane = 72 * q + 2 * g;
+  const int rp = mma_region(p);
+  // ldmatrix row address of this lane within a slot, for block pair b:
+  // matrix (lane >> 3) = (block b + 4 (lane >> 4), rows 8 ((lane >> 3) & 1) ..)
+  const int lrow = 8 * ((lane >> 3) & 1) + (lane & 7);
+  // accumulator input of every MMA: four registers holding 0 (opaque, so they
+  // are kept rather than rebuilt for each product)
+  float zero4[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) asm("mov.b32 %0, 0;" : "=f"(zero4[k]));
+  const float2 i1 = g == 0 ? make_float2(-18432.0f, -18432.0f) : make_float2(0.f, 0.f);
+  const float i2 = lane == 0 ? 32768.0f : 0.0f;
+
+  ZonalTile cur, nxt;
+  take(cur);
+  ok = advance();
+  issue(cur, 0);
+  bool have_nxt = ok && c_t < t_stop;
+  if (have_nxt) {
+    take(nxt);
+    ok = advance();
+    issue(nxt, 1);
+  } else {
+    cp_async_commit();
+  }
+  int st = 0;
+  while (true) {
+    cp_async_wait<1>();
+    __syncwarp();  // every lane's copies of this tile are visible to the warp
+    if (cur.r != wr) {
+      const float2* wr_tab = wtab + (long long)cur.r * 256;
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int u = g + 8 * h, v = 8 * nt + 2 * q;
+          const float2 w0 = __ldg(wr_tab + v * 16 + u), w1 = __ldg(wr_tab + (v + 1) * 16 + u);  // [r][c][u]
+          kwp[nt][h] = make_float2(256.0f * w0.x, 256.0f * w1.x);
+          dwp[nt][h] = make_float2(256.0f * w0.y, 256.0f * w1.y);
+        }
+      wr = cur.r;
+    }
+
+    // ---- forward transform of the eight blocks on the tensor cores, mask +
+    // weights + dropped energy in registers, V into the buffer.  First the
+    // row products of all eight blocks (independent MMAs back to back), then
+    // the column products and the weighting, block pair by block pair.
+    unsigned a2[4][2][4];  // [block pair][block b, b + 4][A fragment] of P, f16
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      unsigned x0, x1, x2, x3;  // blocks b (rows 0-7, 8-15), b + 4 (rows 0-7, 8-15)
+      ldsm_x4_trans(stg_base + 16 * (128 * st + stage_slot(b + 4 * (lane >> 4), lrow)), x0, x1, x2, x3);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const unsigned lo = s ? x2 : x0, hi = s ? x3 : x1;
+        // B operands: pixel column 2g (even tile) and 2g + 1 (odd tile), rows (2q, 2q+1), (2q+8, 2q+9)
+        const unsigned be0 = __byte_perm(lo, 0x6464u, 0x4240u), be1 = __byte_perm(hi, 0x6464u, 0x4240u);
+        const unsigned bo0 = __byte_perm(lo, 0x6464u, 0x4341u), bo1 = __byte_perm(hi, 0x6464u, 0x4341u);
+        float pe[4], po[4];
+        mma_16816(pe, ta, be0, be1, zero4);
+        mma_16816(po, ta, bo0, bo1, zero4);
+        // row u = 0 of P: remove 16 * 1024 and centre by -2048 (now |P| <= 2048)
+        const float2 p0 = __fadd2_rn(make_float2(pe[0], pe[1]), i1), p1 = __fadd2_rn(make_float2(po[0], po[1]), i1);
+        a2[b][s][0] = pack_f16x2(p0.x, p0.y);
+        a2[b][s][1] = pack_f16x2(pe[2], pe[3]);
+        a2[b][s][2] = pack_f16x2(p1.x, p1.y);
+        a2[b][s][3] = pack_f16x2(po[2], po[3]);
+      }
+    }
+    float2 acc = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+    float* const vdst = reinterpret_cast<float*>(tb) + v_lane;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      float yb[2][2][4];  // [block b, b + 4][nt][fragment]
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        mma_16816(yb[s][0], a2[b][s], tbf[0][0], tbf[0][1], zero4);
+        mma_16816(yb[s][1], a2[b][s], tbf[1][0], tbf[1][1], zero4);
+        yb[s][0][0] += i2;  // Y[0][0]: undo the centring
+      }
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float2 ya = make_float2(yb[0][nt][2 * h], yb[0][nt][2 * h + 1]);  // block b, (v, v+1)
+          const float2 yB = make_float2(yb[1][nt][2 * h], yb[1][nt][2 * h + 1]);  // block b + 4
+          acc = __ffma2_rn(__fmul2_rn(ya, dwp[nt][h]), ya, acc);
+          acc1 = __ffma2_rn(__fmul2_rn(yB, dwp[nt][h]), yB, acc1);
+          const float2 va2 = __fmul2_rn(ya, kwp[nt][h]), vb2 = __fmul2_rn(yB, kwp[nt][h]);
+          // block b's value at word 0 and block b + 4's at word 1 of the pair
+          // (u, v), u = g + 8h, v = 8 nt + 2q + e: float index
+          // 4 unit(b, v, u >> 1) + 2 (u & 1) = 4 (R(b) + 72 nt + 8 e + 4 h) + 72 q + 2 g
+          const int cu = 4 * (mma_region(b) + 72 * nt + 4 * h);
+          vdst[cu] = va2.x;
+          vdst[cu + 1] = vb2.x;
+          vdst[cu + 32] = va2.y;
+          vdst[cu + 33] = vb2.y;
+        }
+    }
+    acc = __fadd2_rn(acc, acc1);
+    __syncwarp();
+
+    // ---- the input rows of the tile after the next one, into the slot just read
+    ZonalTile fut;
+    const bool have_fut = have_nxt && ok && c_t < t_stop;
+    if (have_fut) {
+      take(fut);
+      ok = advance();
+      issue(fut, st);
+    } else {
+      cp_async_commit();
+    }
+
+    // ---- per column c = 2j + i: inverse column pass, in place
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      float4* const line = tb + rp + 18 * j + 8 * i;  // unit(p, 2j + i, 0)
+      float2 y[16], uo[16];
+#pragma unroll
+      for (int qq = 0; qq < 8; ++qq) {
+        const float4 v = line[qq];
+        y[2 * qq] = make_float2(v.x, v.y);
+        y[2 * qq + 1] = make_float2(v.z, v.w);
+      }
+      inv16(y, uo);
+#pragma unroll
+      for (int qq = 0; qq < 8; ++qq)
+        line[qq] = make_float4(uo[2 * qq].x, uo[2 * qq].y, uo[2 * qq + 1].x, uo[2 * qq + 1].y);
+    }
+    __syncwarp();
+
+    // ---- per row 2j + rr: inverse row pass -> exact Z, round half to even,
+    // clamp, pack, store (lanes with odd j take their rows in reverse order)
+    const bool va = p < cur.nb, vb = p + 4 < cur.nb;
+#pragma unroll
+    for (int tr = 0; tr < 2; ++tr) {
+      const int rr = tr ^ (j & 1);
+      const float2* const fin = reinterpret_cast<const float2*>(tb + rp + j) + rr;
+      float2 v[16], z[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v[c] = fin[2 * (8 * c + (c & 14))];
+      inv16(v, z);
+      unsigned oa[4], ob[4];
+#pragma unroll
+      for (int gg = 0; gg < 4; ++gg) {
+        unsigned qa[4], qb[4];
+#pragma unroll
+        for (int e4 = 0; e4 < 4; ++e4) {
+          const float2 e = rne_denormal(f2mul(z[4 * gg + e4], kInv2304));
+          qa[e4] = __float_as_uint(e.x);
+          qb[e4] = __float_as_uint(e.y);
+        }
+        oa[gg] = pack_u8(qa[1], qa[0], pack_u8(qa[3], qa[2], 0u));
+        ob[gg] = pack_u8(qb[1], qb[0], pack_u8(qb[3], qb[2], 0u));
+      }
+      uint8_t* d = cur.dst + rr * cur.dst_pitch;
+      if (va) __stcs(reinterpret_cast<uint4*>(d), make_uint4(oa[0], oa[1], oa[2], oa[3]));
+      if (vb) __stcs(reinterpret_cast<uint4*>(d + 64), make_uint4(ob[0], ob[1], ob[2], ob[3]));
+    }
+
+    // ---- tile SSE: dropped energy / 2304 (weights carry the 256)
+    const float tot = warp_sum(acc.x + acc.y);
+    if (lane == 0) tile_sse[cur.t] = tot * (1.0f / 2304.0f);
+    __syncwarp();
 
     if (!have_nxt) break;
     cur = nxt;
@@ -1011,7 +1384,7 @@ static cudaError_t occupancy_with_smem(int* n, K kernel, int threads, int smem) 
 
 static int config_index(const ZonalConfig& c) {
   if (!c.prefetch || c.warps != 4) return -1;
-  return c.variant == kZonalSwar ? 0 : (c.variant == kZonalF32 ? 1 : -1);
+  return c.variant == kZonalSwar ? 0 : (c.variant == kZonalF32 ? 1 : (c.variant == kZonalMma ? 2 : -1));
 }
 
 bool zonal_config_supported(const ZonalConfig& c) { return config_index(c) >= 0; }
@@ -1029,6 +1402,9 @@ cudaError_t launch_zonal_config(const ZonalConfig& cfg, const ImageJob* d_jobs, 
     case 1:
       return launch_with_smem(zonal_f32_kernel<4, false>, grid, threads, 4 * kZonalWarpSmemBytes, stream, d_jobs,
                               njobs, ntiles, d_wtab, d_tile_sse, d_status);
+    case 2:
+      return launch_with_smem(zonal_mma_kernel<4>, grid, threads, 4 * kZonalMmaWarpSmemBytes, stream, d_jobs,
+                              njobs, ntiles, d_wtab, d_tile_sse, d_status);
   }
   return cudaErrorInvalidValue;
 }
@@ -1040,6 +1416,7 @@ int zonal_config_max_ctas_per_sm(const ZonalConfig& cfg) {
   switch (config_index(cfg)) {
     case 0: e = occupancy_with_smem(&n, zonal_f32_kernel<4, true>, 128, 4 * zs); break;
     case 1: e = occupancy_with_smem(&n, zonal_f32_kernel<4, false>, 128, 4 * zs); break;
+    case 2: e = occupancy_with_smem(&n, zonal_mma_kernel<4>, 128, 4 * kZonalMmaWarpSmemBytes); break;
   }
   return (e == cudaSuccess && n > 0) ? n : 1;
 }

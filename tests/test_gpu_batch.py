@@ -70,7 +70,10 @@ def test_batch_matches_oracle_and_per_call(torch, plan, flags):
         assert torch.equal(a, c)
     fin = ~psnr.isinf()
     assert torch.equal(psnr.isinf(), psnr2.isinf())
-    assert torch.allclose(psnr[fin], psnr2[fin], rtol=1e-12, atol=0)
+    # the same kernel gives the same PSNR to the bit; an autotuned batch may run
+    # another kernel variant, whose FP32 per-tile energy sums in another order
+    rtol = 1e-6 if flags & atdct16.BATCH_AUTOTUNE else 1e-12
+    assert torch.allclose(psnr[fin], psnr2[fin], rtol=rtol, atol=0)
     info = b.info()
     assert info["tiles"] > 0 and info["grid"] > 0
     if flags & atdct16.BATCH_AUTOTUNE:
@@ -112,4 +115,27 @@ def test_autotune_rejects_in_place(torch, plan):
     b = atdct16.Batch(plan, [atdct16.image(img, img, 256)], psnr, flags=atdct16.BATCH_GRAPH)  # in place is fine untuned
     b.launch()
     torch.cuda.synchronize()
+    b.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_every_kernel_variant_matches_oracle(torch, plan, variant):
+    """Each zonal kernel variant, pinned: bit-exact pixels against the exact
+    oracle, PSNR within the FP tolerance (r spans every mask extent)."""
+    rs = [0, 1, 2, 6, 16, 36, 64, 100, 150, 255, 256]
+    imgs = _mixed(11)[0][:len(rs)]
+    src, dst = _dev(torch, imgs)
+    descs = [atdct16.image(s, d, r) for s, d, r in zip(src, dst, rs)]
+    psnr = torch.empty(len(imgs), dtype=torch.float64, device="cuda")
+    b = atdct16.Batch(plan, descs, psnr, flags=atdct16.BATCH_GRAPH | atdct16.batch_variant(variant))
+    assert b.info()["variant"] == atdct16.ZONAL_VARIANTS[variant]
+    b.launch()
+    torch.cuda.synchronize()
+    for im, r, d, p in zip(imgs, rs, dst, psnr.cpu().tolist()):
+        ref = O.compress_zonal_exact(im, r)
+        assert np.array_equal(d.cpu().numpy(), ref["recon_u8"]), (variant, r)
+        if math.isinf(ref["psnr"]):
+            assert math.isinf(p)
+        else:
+            assert p == pytest.approx(ref["psnr"], rel=1e-5, abs=1e-5)
     b.close()
