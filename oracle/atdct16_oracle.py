@@ -28,7 +28,7 @@ any zonal mask, the reconstruction is the rational number
 it exactly.  FP64 is used for the orthonormal-domain definition (a second,
 independent route), the quantiser, PSNR and the Table 2 measures.
 
-Readings of points the paper leaves open (each one is listed in the design doc):
+Readings of points the paper leaves open:
 
 * Block orientation: ``A`` is indexed [row m][column n];
   ``Y[u, v] = sum_m sum_n T[u, m] A[m, n] T[v, n]`` (u = vertical frequency).
