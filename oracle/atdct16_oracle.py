@@ -313,6 +313,58 @@ def psnr_images(a: np.ndarray, b: np.ndarray, peak: float = 255.0) -> float:
     return psnr_from_sse(float(np.sum(d * d)), d.size, peak)
 
 
+# --------------------------------------------------------------------------
+# Sec. 4: SSIM, the second quality measure (Wang, Bovik, Sheikh and Simoncelli
+# 2004, which the paper cites).  Reading of the parameters the paper leaves to
+# that reference: an 11x11 circular Gaussian window with standard deviation
+# 1.5, normalised to sum 1; K1 = 0.01, K2 = 0.03, dynamic range L = 255;
+# every window position that lies inside the image ("valid" positions, no
+# padding, no downsampling); MSSIM is the mean of the map.  Applied to the
+# original and the stored (rounded, clamped) reconstruction.
+# --------------------------------------------------------------------------
+SSIM_WIN = 11
+SSIM_SIGMA = 1.5
+SSIM_C1 = (0.01 * 255.0) ** 2
+SSIM_C2 = (0.03 * 255.0) ** 2
+
+
+def ssim_window() -> np.ndarray:
+    """The normalised 11x11 Gaussian weights, FP64."""
+    k = np.arange(SSIM_WIN, dtype=np.float64) - (SSIM_WIN - 1) / 2.0
+    g = np.exp(-(k[:, None] ** 2 + k[None, :] ** 2) / (2.0 * SSIM_SIGMA ** 2))
+    return g / g.sum()
+
+
+def ssim_map(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """SSIM at every valid window position: the weighted means, variances and
+    covariance of the two windows, then
+    ``(2 mu_a mu_b + C1)(2 s_ab + C2) / ((mu_a^2 + mu_b^2 + C1)(s_a^2 + s_b^2 + C2))``."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    w = ssim_window()
+    wa = np.lib.stride_tricks.sliding_window_view(a, (SSIM_WIN, SSIM_WIN))
+    wb = np.lib.stride_tricks.sliding_window_view(b, (SSIM_WIN, SSIM_WIN))
+    mu_a = np.einsum("ijkl,kl->ij", wa, w)
+    mu_b = np.einsum("ijkl,kl->ij", wb, w)
+    s_aa = np.einsum("ijkl,kl->ij", (wa - mu_a[:, :, None, None]) ** 2, w)
+    s_bb = np.einsum("ijkl,kl->ij", (wb - mu_b[:, :, None, None]) ** 2, w)
+    s_ab = np.einsum("ijkl,kl->ij", (wa - mu_a[:, :, None, None]) * (wb - mu_b[:, :, None, None]), w)
+    num = (2.0 * mu_a * mu_b + SSIM_C1) * (2.0 * s_ab + SSIM_C2)
+    den = (mu_a * mu_a + mu_b * mu_b + SSIM_C1) * (s_aa + s_bb + SSIM_C2)
+    return num / den
+
+
+def mssim(a: np.ndarray, b: np.ndarray) -> float:
+    """Mean SSIM over the valid window positions."""
+    return float(np.mean(ssim_map(a, b)))
+
+
+def ape(measure: float, reference: float) -> float:
+    """Absolute percentage error of a quality measure against the exact DCT's
+    (Sec. 4): ``100 |m - m_DCT| / m_DCT``."""
+    return 100.0 * abs(measure - reference) / abs(reference)
+
+
 def compress_zonal_exact(img: np.ndarray, r: int) -> dict:
     """Sec. 4 procedure with exact arithmetic: forward, keep the first ``r``
     zig-zag coefficients, inverse, reassemble; SSE of the unrounded

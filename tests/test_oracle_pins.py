@@ -359,3 +359,69 @@ def test_pins_catch_planted_mistakes():
     t7 = t.copy(); t7[9, 4] = 1; mutants.append((t7, w, p2, zig))            # dropped zero
     for i, m in enumerate(mutants):
         assert not _pins_pass(*m), f"mutant {i} passed the pins"
+
+
+# --------------------------------------------------------------------------
+# SSIM (Sec. 4, Wang et al. 2004) and APE.
+# --------------------------------------------------------------------------
+def _ssim_by_filters(a, b, sigma=O.SSIM_SIGMA, win=O.SSIM_WIN, c1=O.SSIM_C1, c2=O.SSIM_C2):
+    """The same measure through a library route: separable Gaussian filtering
+    (scipy.ndimage, radius 5) and the moment form E[xy] - E[x] E[y], cropped
+    to the positions whose window lies inside the image."""
+    from scipy import ndimage
+
+    r = (win - 1) // 2
+    f = lambda x: ndimage.gaussian_filter(x, sigma, truncate=r / sigma, mode="constant")[r:-r, r:-r]
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    mu_a, mu_b = f(a), f(b)
+    s_aa = f(a * a) - mu_a * mu_a
+    s_bb = f(b * b) - mu_b * mu_b
+    s_ab = f(a * b) - mu_a * mu_b
+    m = ((2 * mu_a * mu_b + c1) * (2 * s_ab + c2)) / ((mu_a ** 2 + mu_b ** 2 + c1) * (s_aa + s_bb + c2))
+    return float(m.mean()), m.shape
+
+
+def test_ssim_matches_filter_route():
+    rng = np.random.default_rng(7)
+    for h, w in ((16, 16), (24, 40), (37, 29)):
+        a = rng.integers(0, 256, (h, w)).astype(np.uint8)
+        b = np.clip(a.astype(int) + rng.integers(-30, 31, (h, w)), 0, 255).astype(np.uint8)
+        ref, shape = _ssim_by_filters(a, b)
+        assert O.ssim_map(a, b).shape == shape == (h - 10, w - 10)
+        assert O.mssim(a, b) == pytest.approx(ref, rel=0, abs=1e-12)
+
+
+def test_ssim_closed_forms():
+    rng = np.random.default_rng(8)
+    a = rng.integers(0, 256, (20, 23)).astype(np.uint8)
+    assert O.mssim(a, a) == pytest.approx(1.0, abs=1e-15)
+    b = np.clip(a.astype(int) + rng.integers(-9, 10, a.shape), 0, 255).astype(np.uint8)
+    assert O.mssim(a, b) == pytest.approx(O.mssim(b, a), abs=1e-15)  # symmetric
+    assert O.mssim(a, b) < 1.0
+    # constant images: variances and covariance vanish, only the luminance term remains
+    for c_a, c_b in ((0, 0), (10, 200), (128, 129), (255, 0)):
+        x = np.full((16, 16), c_a, np.uint8)
+        y = np.full((16, 16), c_b, np.uint8)
+        want = (2.0 * c_a * c_b + O.SSIM_C1) / (c_a * c_a + c_b * c_b + O.SSIM_C1)
+        assert O.mssim(x, y) == pytest.approx(want, rel=1e-13)
+    # the window is the sampled Gaussian exp(-d^2 / 4.5), normalised
+    w = O.ssim_window()
+    assert w.shape == (11, 11) and w.sum() == pytest.approx(1.0, abs=1e-15)
+    assert w[5, 5] / w[5, 6] == pytest.approx(math.exp(1.0 / 4.5), rel=1e-14)
+    assert w[0, 0] / w[5, 5] == pytest.approx(math.exp(-50.0 / 4.5), rel=1e-12)
+
+
+def test_ssim_pin_catches_planted_mistakes():
+    rng = np.random.default_rng(9)
+    a = rng.integers(0, 256, (30, 30)).astype(np.uint8)
+    b = np.clip(a.astype(int) + rng.integers(-40, 41, a.shape), 0, 255).astype(np.uint8)
+    ref = O.mssim(a, b)
+    for kw in ({"sigma": 1.0}, {"c1": (0.03 * 255) ** 2}, {"c2": (0.01 * 255) ** 2}):
+        assert abs(_ssim_by_filters(a, b, **kw)[0] - ref) > 1e-9, kw  # far outside the pin tolerance
+
+
+def test_ape_closed_form():
+    assert O.ape(110.0, 100.0) == pytest.approx(10.0)
+    assert O.ape(90.0, 100.0) == pytest.approx(10.0)
+    assert O.ape(0.5, 0.5) == 0.0
