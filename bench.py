@@ -280,6 +280,26 @@ def quant_phase(torch, atdct16, synth, dev, n_frames, steps, warmup, peak_gbs):
 
 
 # --------------------------------------------------------------------------
+def ssim_phase(torch, atdct16, plan, descs, n_jobs, px, reps=5):
+    """SSIM (Sec. 4) of every reconstruction of one bench step against its
+    original, through atdct16_ssim_batch: time per batch and the mean MSSIM
+    per zonal r."""
+    out = torch.empty(n_jobs, dtype=torch.float64, device="cuda")
+    plan.ssim(descs, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plan.ssim(descs, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    per_r = out.view(len(R_SWEEP), -1).mean(dim=1).tolist()
+    return {"images": n_jobs, "ms_per_batch": ms, "gpx_s": px / (ms / 1e3) / 1e9,
+            "mean_mssim_by_r": {str(r): v for r, v in zip(R_SWEEP, per_r)}}
+
+
+# --------------------------------------------------------------------------
 def mixed_batch_phase(torch, atdct16, synth, dev, n_images, seed=4):
     """1000 mixed-size u8 AR(1) images (sides log-uniform in [128, 4096],
     multiples of 16, rho in [0.8, 0.97]), zonal r = 36: per-image launches of
@@ -566,6 +586,7 @@ def run_ours(args):
         }
         line["cpu_baseline"] = cpu_baseline(batch, args.cpu_seconds) if args.cpu_seconds > 0 else None
         if not args.no_extras:
+            line["ssim"] = ssim_phase(torch, atdct16, plan, sets[0][2], jobs, px_step)
             del sets
             torch.cuda.empty_cache()
             line["quant"] = quant_phase(torch, atdct16, synth, dev, args.quant_frames, 20, 3, peak)

@@ -172,6 +172,20 @@ atdct16_status atdct16_compress_quant(atdct16_plan_t plan, const atdct16_image* 
 atdct16_status atdct16_compress_zonal_noalloc(const atdct16_image* h_images, int32_t n, double* d_psnr,
                                               double* d_sse, cudaStream_t stream);
 
+/* Mean SSIM (Sec. 4, the structural similarity of Wang et al. 2004 that the
+ * paper cites) of n uint8 image pairs: h_images[i].src against
+ * h_images[i].dst (both read; e.g. an original and its reconstruction),
+ * r_or_qp ignored.  Window: 11 x 11 Gaussian of standard deviation 1.5,
+ * normalised; C1 = (0.01 * 255)^2, C2 = (0.03 * 255)^2; the mean over the
+ * (h - 10) x (w - 10) positions where the window lies inside the image; FP32
+ * moments of the centred pixels, FP64 mean.  d_mssim: n device doubles.
+ * Asynchronous on `stream`; the first call on a device uploads the window
+ * weights and synchronises `stream` (make it outside any stream capture).
+ * EINVAL for the argument rules of atdct16_compress_zonal, ENOMEM if the
+ * batch needs more 16 x 64-position tiles than the plan's workspace holds. */
+atdct16_status atdct16_ssim_batch(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n, double* d_mssim,
+                                  cudaStream_t stream);
+
 /* PSNR between two images of the same shape (Sec. 4), exact integer SSE.
  * peak 255.  d_out: one device double.  Allocates nothing: the output slot
  * doubles as the accumulator. */

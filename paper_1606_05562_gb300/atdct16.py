@@ -94,6 +94,7 @@ _SIGS = {
     "atdct16_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_size_t)]),
     "atdct16_server_destroy": (C.c_int, [C.c_void_p]),
+    "atdct16_ssim_batch": (C.c_int, [C.c_void_p, C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p]),
     "atdct16_plan_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "atdct16_plan_profile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
 }
@@ -223,6 +224,12 @@ class Plan:
         arr = _as_array(images)
         _check(lib().atdct16_compress_quant(self._h, arr, len(images), _ptr(levels), _ptr(psnr), _ptr(sse),
                                             _stream(stream)), "compress_quant")
+
+    def ssim(self, images, out, stream=None):
+        """Mean SSIM of each (src, dst) u8 pair of ``images`` into ``out``
+        (float64, one per image)."""
+        arr = _as_array(images)
+        _check(lib().atdct16_ssim_batch(self._h, arr, len(images), _ptr(out), _stream(stream)), "ssim_batch")
 
     def set_profiling(self, on=True):
         _check(lib().atdct16_plan_set_profiling(self._h, 1 if on else 0), "set_profiling")

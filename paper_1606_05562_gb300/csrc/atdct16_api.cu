@@ -114,7 +114,7 @@ atdct16_status check_image(const atdct16_image& im, int elem, bool need_dst) {
 // overlaps the previous call's kernels) and `stream` waits for it.  While
 // `stream` is being captured into a graph the upload goes on `stream` itself.
 atdct16_status stage_jobs(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n, int elem,
-                          cudaStream_t stream, long long* ntiles_out, bool with_level_base) {
+                          cudaStream_t stream, long long* ntiles_out, bool with_level_base, bool ssim_tiles = false) {
   const int b = plan->buf ^ 1;
   if (plan->uploaded_pending[b]) {
     if (cudaEventSynchronize(plan->uploaded[b]) != cudaSuccess) return ATDCT16_ECUDA;
@@ -131,10 +131,15 @@ atdct16_status stage_jobs(atdct16_plan_t plan, const atdct16_image* h_images, in
     J.dst_pitch = im.dst_pitch;
     J.width = im.width;
     J.height = im.height;
-    J.tiles_x = (im.width + kTileW - 1) / kTileW;
     J.param = im.r_or_qp;
     J.tile_begin = tiles;
-    tiles += (long long)J.tiles_x * (im.height / kTileH);
+    if (ssim_tiles) {  // tiles of the (h - 10) x (w - 10) map of window positions
+      J.tiles_x = (im.width - 10 + kSsimTileCols - 1) / kSsimTileCols;
+      tiles += (long long)J.tiles_x * ((im.height - 10 + kSsimTileRows - 1) / kSsimTileRows);
+    } else {
+      J.tiles_x = (im.width + kTileW - 1) / kTileW;
+      tiles += (long long)J.tiles_x * (im.height / kTileH);
+    }
     J.level_base = with_level_base ? blocks * 256 : 0;
     blocks += (long long)(im.width / 16) * (im.height / 16);
   }
@@ -377,6 +382,23 @@ atdct16_status atdct16_compress_quant(atdct16_plan_t plan, const atdct16_image* 
   prof_end(plan, pk, stream);
   if (e == cudaSuccess)
     e = launch_psnr_finalize(plan->d_jobs, n, ntiles, plan->d_tile_sse, 255.0, d_psnr, d_sse, stream);
+  if (e == cudaSuccess) jobs_consumed(plan, stream);
+  return from_cuda(e);
+}
+
+atdct16_status atdct16_ssim_batch(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n, double* d_mssim,
+                                  cudaStream_t stream) {
+  if (!plan || !h_images || !d_mssim || n < 1 || n > plan->max_images) return ATDCT16_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_mssim) & 7) != 0) return ATDCT16_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    const atdct16_status s = check_image(h_images[i], 1, true);
+    if (s != ATDCT16_OK) return s;
+  }
+  long long ntiles = 0;
+  atdct16_status s = stage_jobs(plan, h_images, n, 1, stream, &ntiles, false, true);
+  if (s != ATDCT16_OK) return s;
+  cudaError_t e = launch_ssim(plan->d_jobs, n, ntiles, plan->d_tile_sse, d_mssim, plan->d_status, plan->num_sms,
+                              stream);
   if (e == cudaSuccess) jobs_consumed(plan, stream);
   return from_cuda(e);
 }

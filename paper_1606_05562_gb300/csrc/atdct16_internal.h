@@ -65,6 +65,10 @@ cudaError_t launch_quant(const ImageJob* d_jobs, int njobs, long long ntiles, co
 cudaError_t launch_psnr_finalize(const ImageJob* d_jobs, int njobs, long long ntiles,
                                  const float* d_tile_sse, double peak, double* d_psnr,
                                  double* d_sse, cudaStream_t stream);
+// SSIM tiles: 16 x 64 window positions of an image's (h - 10) x (w - 10) map.
+constexpr int kSsimTileRows = 16, kSsimTileCols = 64;
+cudaError_t launch_ssim(const ImageJob* d_jobs, int njobs, long long ntiles, float* d_tile_sum, double* d_out,
+                        int* d_status, int num_sms, cudaStream_t stream);
 cudaError_t launch_forward(int dtype, const void* d_src, long long pitch, int w, int h,
                            int32_t* d_coef, cudaStream_t stream);
 cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void* d_dst,

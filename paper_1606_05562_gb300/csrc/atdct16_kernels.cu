@@ -26,6 +26,8 @@
 #include "atdct16_butterfly.cuh"
 #include "atdct16_internal.h"
 
+#include <atomic>
+#include <cmath>
 #include <type_traits>
 
 namespace atdct16 {
@@ -1184,6 +1186,124 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
 }
 
 // --------------------------------------------------------------------------
+// SSIM (Sec. 4, the measure of Wang et al. 2004): mean over the valid
+// positions of the 11x11 Gaussian window (sigma 1.5) of
+//   (2 mu_a mu_b + C1)(2 s_ab + C2) / ((mu_a^2 + mu_b^2 + C1)(s_a^2 + s_b^2 + C2)).
+// One CTA per tile of 16 x 64 window positions: the 26 x 74 input pixels of
+// both images go to shared memory centred (x - 128, which keeps the moment
+// form E[xy] - E[x]E[y] well conditioned in FP32) together with their
+// products; a horizontal pass filters the five moments of every input row,
+// a vertical pass finishes them per position; the tile's sum of SSIM values
+// goes to tile_sum.  The window is separable: the 2-D normalised Gaussian is
+// the outer product of the 1-D normalised one (kSsimW).
+// --------------------------------------------------------------------------
+constexpr int kSsimTileH = 16, kSsimTileW = 64;
+constexpr int kSsimInH = kSsimTileH + 10, kSsimInW = kSsimTileW + 10;
+__constant__ float kSsimW[11];
+
+struct alignas(16) SsimSmem {
+  float in[5][kSsimInH][kSsimInW];        // a, b, a^2, b^2, ab (centred)
+  float hor[5][kSsimInH][kSsimTileW];     // horizontally filtered
+  float red[8];
+};
+
+__global__ void __launch_bounds__(256)
+ssim_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles, float* __restrict__ tile_sum,
+            int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char ssmem[];
+  SsimSmem& sm = *reinterpret_cast<SsimSmem*>(ssmem);
+  const int tid = threadIdx.x;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int job = 0;
+    warp_find_job(jobs, njobs, t, job);
+    const ImageJob* J = jobs + job;
+    const long long tb = __ldg(&J->tile_begin);
+    const int w = __ldg(&J->width), h = __ldg(&J->height), tiles_x = __ldg(&J->tiles_x);
+    const int mh = h - 10, mw = w - 10;  // window positions
+    if (t < tb || t >= tb + (long long)tiles_x * ((mh + kSsimTileH - 1) / kSsimTileH)) {
+      if (tid == 0) set_status(status, kDevBadJob);
+      if (tid == 0) tile_sum[t] = 0.f;
+      continue;
+    }
+    const int lt = (int)(t - tb), ty = lt / tiles_x, tx = lt - ty * tiles_x;
+    const int y0 = ty * kSsimTileH, x0 = tx * kSsimTileW;
+    const uint8_t* pa = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->src)));
+    const uint8_t* pb = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->dst)));
+    const long long ps = __ldg(&J->src_pitch), pd = __ldg(&J->dst_pitch);
+    __syncthreads();  // the previous tile's reads of sm are done
+    for (int i = tid; i < kSsimInH * kSsimInW; i += blockDim.x) {
+      const int r = i / kSsimInW, c = i - r * kSsimInW;
+      const int y = y0 + r, x = x0 + c;
+      float a = 0.f, b = 0.f;
+      if (y < h && x < w) {
+        a = (float)__ldg(pa + y * ps + x) - 128.f;
+        b = (float)__ldg(pb + y * pd + x) - 128.f;
+      }
+      sm.in[0][r][c] = a;
+      sm.in[1][r][c] = b;
+      sm.in[2][r][c] = a * a;
+      sm.in[3][r][c] = b * b;
+      sm.in[4][r][c] = a * b;
+    }
+    __syncthreads();
+    for (int i = tid; i < kSsimInH * kSsimTileW; i += blockDim.x) {
+      const int r = i / kSsimTileW, c = i - r * kSsimTileW;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) s = fmaf(kSsimW[k], sm.in[m][r][c + k], s);
+        sm.hor[m][r][c] = s;
+      }
+    }
+    __syncthreads();
+    float part = 0.f;
+    for (int i = tid; i < kSsimTileH * kSsimTileW; i += blockDim.x) {
+      const int r = i / kSsimTileW, c = i - r * kSsimTileW;
+      if (y0 + r >= mh || x0 + c >= mw) continue;
+      float mo[5];
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) s = fmaf(kSsimW[k], sm.hor[m][r + k][c], s);
+        mo[m] = s;
+      }
+      // back from the centred values: mu = mu' + 128; variances and covariance unchanged
+      const float ma = mo[0] + 128.f, mb = mo[1] + 128.f;
+      const float saa = mo[2] - mo[0] * mo[0], sbb = mo[3] - mo[1] * mo[1], sab = mo[4] - mo[0] * mo[1];
+      const float c1 = 6.5025f, c2 = 58.5225f;  // (0.01 * 255)^2, (0.03 * 255)^2
+      part += ((2.f * ma * mb + c1) * (2.f * sab + c2)) / ((ma * ma + mb * mb + c1) * (saa + sbb + c2));
+    }
+    part = warp_sum(part);
+    if ((tid & 31) == 0) sm.red[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+      float s = 0.f;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sm.red[k];
+      tile_sum[t] = s;
+    }
+  }
+}
+
+// MSSIM per image: the tile sums in a fixed order (FP64) over the number of
+// window positions.
+__global__ void ssim_finalize_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
+                                     const float* __restrict__ tile_sum, double* __restrict__ out) {
+  pdl_wait_primary();
+  const int lane = threadIdx.x & 31;
+  const int job = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (job >= njobs) return;
+  const long long b = jobs[job].tile_begin;
+  const long long e = (job + 1 < njobs) ? jobs[job + 1].tile_begin : ntiles;
+  double s = 0.0;
+  for (long long t = b + lane; t < e; t += 32) s += (double)tile_sum[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[job] = s / ((double)(jobs[job].width - 10) * (double)(jobs[job].height - 10));
+}
+
+// --------------------------------------------------------------------------
 // Per-image PSNR from the per-tile SSE partials (FP64, fixed summation order).
 // --------------------------------------------------------------------------
 __global__ void psnr_finalize_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
@@ -1499,6 +1619,44 @@ cudaError_t launch_psnr_pair(int dtype, const void* d_a, long long pitch_a, cons
 }
 
 int zonal_ctas_per_sm() { return zonal_config_max_ctas_per_sm(default_zonal_config()); }
+cudaError_t launch_ssim(const ImageJob* d_jobs, int njobs, long long ntiles, float* d_tile_sum, double* d_out,
+                        int* d_status, int num_sms, cudaStream_t stream) {
+  if (ntiles <= 0 || njobs <= 0) return cudaSuccess;
+  static std::atomic<bool> weights_ready[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64 || !weights_ready[dev].load()) {
+    // the 1-D normalised Gaussian of standard deviation 1.5 on -5 .. 5
+    double g[11], sum = 0.0;
+    for (int k = 0; k < 11; ++k) sum += (g[k] = std::exp(-(k - 5.0) * (k - 5.0) / 4.5));
+    float w[11];
+    for (int k = 0; k < 11; ++k) w[k] = (float)(g[k] / sum);
+    e = cudaMemcpyToSymbolAsync(kSsimW, w, sizeof(w), 0, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) weights_ready[dev].store(true);
+  }
+  const int smem = (int)sizeof(SsimSmem);
+  int per_sm = 0;
+  e = occupancy_with_smem(&per_sm, ssim_kernel, 256, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<long long>(ntiles, (long long)num_sms * std::max(1, per_sm));
+  e = launch_with_smem(ssim_kernel, grid, 256, smem, stream, d_jobs, njobs, ntiles, d_tile_sum, d_status);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((njobs + 7) / 8);
+  cfg.blockDim = dim3(256);
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, ssim_finalize_kernel, d_jobs, njobs, ntiles, (const float*)d_tile_sum, d_out);
+}
+
 int quant_ctas_per_sm() {
   int n = 0;
   if (occupancy_with_smem(&n, quant_kernel<false>, 128, 4 * kQuantWarpSmemBytes) != cudaSuccess || n < 1) n = 1;
