@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
@@ -297,6 +298,54 @@ def ssim_phase(torch, atdct16, plan, descs, n_jobs, px, reps=5):
     per_r = out.view(len(R_SWEEP), -1).mean(dim=1).tolist()
     return {"images": n_jobs, "ms_per_batch": ms, "gpx_s": px / (ms / 1e3) / 1e9,
             "mean_mssim_by_r": {str(r): v for r, v in zip(R_SWEEP, per_r)}}
+
+
+# --------------------------------------------------------------------------
+def dct_baseline_phase(torch, atdct16, plan, sets, n_jobs, px, psnr_approx, steps=200):
+    """The exact-DCT baseline (dense FP32 DCT-II through the same zonal
+    procedure) on the bench workload: throughput against the multiplierless
+    kernel, and the APE (Sec. 4) of the approximation's mean PSNR and MSSIM
+    per r with respect to the exact DCT's."""
+    psnr = torch.empty(n_jobs, dtype=torch.float64, device="cuda")
+    for w in range(3):
+        plan.compress_zonal_dct(sets[w % len(sets)][2], psnr)
+    torch.cuda.synchronize()
+    plan.set_profiling(True)
+    plan.profile()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(steps):
+        plan.compress_zonal_dct(sets[k % len(sets)][2], psnr)
+    e1.record()
+    torch.cuda.synchronize()
+    n, kms = plan.profile()
+    plan.set_profiling(False)
+    ms = e0.elapsed_time(e1) / steps
+    # quality: the last call wrote set (steps - 1) % 3; compare on that set
+    last = sets[(steps - 1) % len(sets)][2]
+    dct_psnr = psnr.clone()
+    ssim_dct = torch.empty(n_jobs, dtype=torch.float64, device="cuda")
+    plan.ssim(last, ssim_dct)
+    approx_psnr = torch.empty(n_jobs, dtype=torch.float64, device="cuda")
+    plan.compress_zonal(last, approx_psnr)
+    ssim_approx = torch.empty(n_jobs, dtype=torch.float64, device="cuda")
+    plan.ssim(last, ssim_approx)
+    torch.cuda.synchronize()
+    nr = len(R_SWEEP)
+    ape = {}
+    for k, r in enumerate(R_SWEEP):
+        sl = slice(k * n_jobs // nr, (k + 1) * n_jobs // nr)
+        pa, pd = approx_psnr[sl], dct_psnr[sl]
+        fin = ~(pa.isinf() | pd.isinf())
+        mp_a = float(pa[fin].mean()) if bool(fin.any()) else float("inf")
+        mp_d = float(pd[fin].mean()) if bool(fin.any()) else float("inf")
+        ms_a, ms_d = float(ssim_approx[sl].mean()), float(ssim_dct[sl].mean())
+        ape[str(r)] = {"mean_psnr_approx": mp_a, "mean_psnr_dct": mp_d,
+                       "ape_psnr_pct": 100.0 * abs(mp_a - mp_d) / mp_d if math.isfinite(mp_d) else 0.0,
+                       "mean_mssim_approx": ms_a, "mean_mssim_dct": ms_d,
+                       "ape_mssim_pct": 100.0 * abs(ms_a - ms_d) / ms_d}
+    return {"ms_per_step": ms, "kernel_ms": kms / max(n, 1), "gpx_s": px / (ms / 1e3) / 1e9,
+            "kernel_gbs": 2 * px / (kms / max(n, 1) / 1e3) / 1e9, "ape_by_r": ape}
 
 
 # --------------------------------------------------------------------------
@@ -587,6 +636,7 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(batch, args.cpu_seconds) if args.cpu_seconds > 0 else None
         if not args.no_extras:
             line["ssim"] = ssim_phase(torch, atdct16, plan, sets[0][2], jobs, px_step)
+            line["dct_baseline"] = dct_baseline_phase(torch, atdct16, plan, sets, jobs, px_step, None)
             del sets
             torch.cuda.empty_cache()
             line["quant"] = quant_phase(torch, atdct16, synth, dev, args.quant_frames, 20, 3, peak)

@@ -172,6 +172,18 @@ atdct16_status atdct16_compress_quant(atdct16_plan_t plan, const atdct16_image* 
 atdct16_status atdct16_compress_zonal_noalloc(const atdct16_image* h_images, int32_t n, double* d_psnr,
                                               double* d_sse, cudaStream_t stream);
 
+/* Exact-DCT baseline of atdct16_compress_zonal: the same Sec. 4 procedure
+ * with the orthonormal 16-point DCT-II (Sec. 3.2, the transform the paper
+ * measures its approximation against) as dense FP32 products: B = C A C^T,
+ * the first r zig-zag coefficients kept, A' = C^T B' C, stored pixels
+ * clamp(rint(A'), 0, 255) (FP32; they may differ from an exact evaluation
+ * where A' lies within FP32 error of a half-integer), PSNR of the unrounded
+ * A' (the dropped energy, C being orthonormal).  Arguments, ownership and
+ * errors as atdct16_compress_zonal; the first call on a device uploads C and
+ * synchronises `stream` (make it outside any stream capture). */
+atdct16_status atdct16_compress_zonal_dct(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n,
+                                          double* d_psnr, double* d_sse, cudaStream_t stream);
+
 /* Mean SSIM (Sec. 4, the structural similarity of Wang et al. 2004 that the
  * paper cites) of n uint8 image pairs: h_images[i].src against
  * h_images[i].dst (both read; e.g. an original and its reconstruction),

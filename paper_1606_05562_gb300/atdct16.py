@@ -95,6 +95,8 @@ _SIGS = {
                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_size_t)]),
     "atdct16_server_destroy": (C.c_int, [C.c_void_p]),
     "atdct16_ssim_batch": (C.c_int, [C.c_void_p, C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p]),
+    "atdct16_compress_zonal_dct": (C.c_int, [C.c_void_p, C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p,
+                                            C.c_void_p]),
     "atdct16_plan_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "atdct16_plan_profile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
 }
@@ -224,6 +226,12 @@ class Plan:
         arr = _as_array(images)
         _check(lib().atdct16_compress_quant(self._h, arr, len(images), _ptr(levels), _ptr(psnr), _ptr(sse),
                                             _stream(stream)), "compress_quant")
+
+    def compress_zonal_dct(self, images, psnr, sse=None, stream=None):
+        """The exact-DCT baseline of ``compress_zonal`` (FP32 dense DCT-II)."""
+        arr = _as_array(images)
+        _check(lib().atdct16_compress_zonal_dct(self._h, arr, len(images), _ptr(psnr), _ptr(sse), _stream(stream)),
+               "compress_zonal_dct")
 
     def ssim(self, images, out, stream=None):
         """Mean SSIM of each (src, dst) u8 pair of ``images`` into ``out``

@@ -386,6 +386,27 @@ atdct16_status atdct16_compress_quant(atdct16_plan_t plan, const atdct16_image* 
   return from_cuda(e);
 }
 
+atdct16_status atdct16_compress_zonal_dct(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n,
+                                          double* d_psnr, double* d_sse, cudaStream_t stream) {
+  if (!plan || !h_images || !d_psnr || n < 1 || n > plan->max_images) return ATDCT16_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    const atdct16_status s = check_image(h_images[i], 1, true);
+    if (s != ATDCT16_OK) return s;
+    if (h_images[i].r_or_qp < 0 || h_images[i].r_or_qp > 256) return ATDCT16_EINVAL;
+  }
+  long long ntiles = 0;
+  atdct16_status s = stage_jobs(plan, h_images, n, 1, stream, &ntiles, false);
+  if (s != ATDCT16_OK) return s;
+  const int pk = prof_begin(plan, stream);
+  cudaError_t e = launch_zonal_dct(plan->d_jobs, n, ntiles, plan->d_wtab, plan->d_tile_sse, plan->d_status,
+                                   plan->num_sms, stream);
+  prof_end(plan, pk, stream);
+  if (e == cudaSuccess)
+    e = launch_psnr_finalize(plan->d_jobs, n, ntiles, plan->d_tile_sse, 255.0, d_psnr, d_sse, stream);
+  if (e == cudaSuccess) jobs_consumed(plan, stream);
+  return from_cuda(e);
+}
+
 atdct16_status atdct16_ssim_batch(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n, double* d_mssim,
                                   cudaStream_t stream) {
   if (!plan || !h_images || !d_mssim || n < 1 || n > plan->max_images) return ATDCT16_EINVAL;

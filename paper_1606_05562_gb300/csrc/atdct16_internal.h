@@ -65,6 +65,9 @@ cudaError_t launch_quant(const ImageJob* d_jobs, int njobs, long long ntiles, co
 cudaError_t launch_psnr_finalize(const ImageJob* d_jobs, int njobs, long long ntiles,
                                  const float* d_tile_sse, double peak, double* d_psnr,
                                  double* d_sse, cudaStream_t stream);
+// Exact-DCT baseline of the fused zonal path (same tiles and table as zonal).
+cudaError_t launch_zonal_dct(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
+                             float* d_tile_sse, int* d_status, int num_sms, cudaStream_t stream);
 // SSIM tiles: 16 x 64 window positions of an image's (h - 10) x (w - 10) map.
 constexpr int kSsimTileRows = 16, kSsimTileCols = 64;
 cudaError_t launch_ssim(const ImageJob* d_jobs, int njobs, long long ntiles, float* d_tile_sum, double* d_out,

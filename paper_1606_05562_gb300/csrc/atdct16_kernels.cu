@@ -1304,6 +1304,255 @@ __global__ void ssim_finalize_kernel(const ImageJob* __restrict__ jobs, int njob
 }
 
 // --------------------------------------------------------------------------
+// Exact-DCT baseline of the zonal path: the same Sec. 4 procedure with the
+// orthonormal 16-point DCT-II matrix C (Sec. 3.2) in place of C_hat, as
+// dense FP32 products (16 multiply-adds per output), for comparison with
+// the multiplierless transform.  Per block: B = C A C^T, keep the first r
+// zig-zag coefficients, A' = C^T B' C, rint (ties to even) and clamp to
+// 0..255; the dropped energy is the SSE of the unrounded reconstruction
+// (C is orthonormal).  Same tiling, staging and in-place line-per-column
+// transpose as the quantisation kernel.
+// --------------------------------------------------------------------------
+__constant__ float kDctC[16][16];  // C[k][j], FP32 of the FP64 values
+
+__device__ __forceinline__ void dct16_fwd(const float2 (&x)[16], float2 (&y)[16]) {
+#pragma unroll 4
+  for (int k = 0; k < 16; ++k) {
+    float sx = 0.f, sy = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      sx = fmaf(kDctC[k][j], x[j].x, sx);
+      sy = fmaf(kDctC[k][j], x[j].y, sy);
+    }
+    y[k] = make_float2(sx, sy);
+  }
+}
+__device__ __forceinline__ void dct16_inv(const float2 (&y)[16], float2 (&x)[16]) {
+#pragma unroll 4
+  for (int j = 0; j < 16; ++j) {
+    float sx = 0.f, sy = 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      sx = fmaf(kDctC[k][j], y[k].x, sx);
+      sy = fmaf(kDctC[k][j], y[k].y, sy);
+    }
+    x[j] = make_float2(sx, sy);
+  }
+}
+
+constexpr int kDStageUnits = 2 * 4 * 32;
+constexpr int kDctWarpSmemBytes = 16 * (kZT2Units + kDStageUnits);
+
+__global__ void __launch_bounds__(128, 3)
+dct_zonal_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
+                 const float2* __restrict__ wtab, float* __restrict__ tile_sse, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char dsmem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = lane & 3, j = lane >> 2, jb1 = (j >> 1) & 1;
+  float4* const tb = reinterpret_cast<float4*>(dsmem + warp * kDctWarpSmemBytes);
+  uint4* const stg = reinterpret_cast<uint4*>(tb + kZT2Units) + lane;  // + 128 s + 32 k
+  const int ntiles = (int)ntiles_ll;
+  pdl_launch_dependents();
+  constexpr int kWarps = 4;
+  const int nwarps = gridDim.x * kWarps;
+  const int per_warp = (ntiles + nwarps - 1) / nwarps;
+  const int t_first = (blockIdx.x * kWarps + warp) * per_warp;
+  const int t_stop = min(ntiles, t_first + per_warp);
+  if (t_first >= t_stop) return;
+
+  int c_t = 0, c_end = 0, tiles_x = 1, tx = 0, nb_last = 8, r_job = 0, src_pitch = 0, dst_pitch = 0;
+  const uint8_t* src_band = nullptr;
+  uint8_t* dst_band = nullptr;
+  auto enter = [&](int t) -> bool {
+    int job;
+    warp_find_job(jobs, njobs, t, job);
+    const ImageJob* J = jobs + job;
+    const long long tb0 = __ldg(&J->tile_begin);
+    tiles_x = __ldg(&J->tiles_x);
+    const long long te = tb0 + (long long)tiles_x * (__ldg(&J->height) >> 4);
+    if (t < tb0 || t >= te || tiles_x < 1) return false;
+    c_end = (int)min(te, (long long)t_stop);
+    const int lt = (int)(t - tb0);
+    const int ty = lt / tiles_x;
+    tx = lt - ty * tiles_x;
+    src_pitch = (int)__ldg(&J->src_pitch);
+    dst_pitch = (int)__ldg(&J->dst_pitch);
+    const long long row = (long long)ty * kTileH + 2 * j;
+    src_band = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->src))) +
+               row * src_pitch + 16 * p;
+    dst_band = reinterpret_cast<uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->dst))) +
+               row * dst_pitch + 16 * p;
+    nb_last = min(8, (__ldg(&J->width) - (tiles_x - 1) * kTileW) >> 4);
+    r_job = __ldg(&J->param);
+    c_t = t;
+    return true;
+  };
+  auto take = [&](ZonalTile& z) {
+    z.src = src_band + tx * kTileW;
+    z.dst = dst_band + tx * kTileW;
+    z.src_pitch = src_pitch;
+    z.dst_pitch = dst_pitch;
+    z.nb = tx == tiles_x - 1 ? nb_last : 8;
+    z.t = c_t;
+    z.r = r_job;
+  };
+  auto advance = [&]() -> bool {
+    ++c_t;
+    if (++tx == tiles_x) {
+      tx = 0;
+      src_band += (long long)kTileH * src_pitch;
+      dst_band += (long long)kTileH * dst_pitch;
+    }
+    return c_t >= t_stop || c_t < c_end || enter(c_t);
+  };
+  auto issue = [&](const ZonalTile& z, int st) {
+    uint4* d = stg + 128 * st;
+    if (p < z.nb) {
+      cp_async16(d, z.src);
+      cp_async16(d + 32, z.src + z.src_pitch);
+    }
+    if (p + 4 < z.nb) {
+      cp_async16(d + 64, z.src + 64);
+      cp_async16(d + 96, z.src + 64 + z.src_pitch);
+    }
+    cp_async_commit();
+  };
+
+  if (!enter(t_first)) {
+    if (lane == 0) set_status(status, kDevBadJob);
+    return;
+  }
+  bool ok = true;
+  int wr = -1;
+  unsigned keep = 0;  // bit 16 i + u: coefficient (u, column 2j + i) is kept
+  ZonalTile cur, nxt;
+  take(cur);
+  ok = advance();
+  issue(cur, 0);
+  bool have_nxt = ok && c_t < t_stop;
+  if (have_nxt) {
+    take(nxt);
+    ok = advance();
+    issue(nxt, 1);
+  } else {
+    cp_async_commit();
+  }
+  int st = 0;
+  while (true) {
+    cp_async_wait<1>();
+    if (cur.r != wr) {  // the zig-zag mask of r from the zonal table (kept <=> weight != 0)
+      keep = 0;
+      const float2* w = wtab + (long long)cur.r * 256;
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (__ldg(w + (2 * j + i) * 16 + u).x != 0.f) keep |= 1u << (16 * i + u);
+      wr = cur.r;
+    }
+    uint4 X[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) X[k] = stg[128 * st + 32 * k];
+    const bool va = p < cur.nb, vb = p + 4 < cur.nb;
+
+    // ---- row pass: 2^23 + x by a byte permute, minus 2^23, then C
+    {
+      float2* const half = reinterpret_cast<float2*>(tb + 138 * p + j);
+#pragma unroll
+      for (int tr = 0; tr < 2; ++tr) {
+        float2 xv[16], rv[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) {
+          const float2 m = make_float2(__uint_as_float(__byte_perm(word_of(X[tr], n >> 2), 0x4B000000u, 0x7440u | (n & 3))),
+                                       __uint_as_float(__byte_perm(word_of(X[2 + tr], n >> 2), 0x4B000000u, 0x7440u | (n & 3))));
+          xv[n] = __fadd2_rn(m, make_float2(-8388608.0f, -8388608.0f));
+        }
+        dct16_fwd(xv, rv);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) half[2 * (8 * k + (k >> 1)) + tr] = rv[k];
+      }
+    }
+    __syncwarp();
+
+    ZonalTile fut;
+    const bool have_fut = have_nxt && ok && c_t < t_stop;
+    if (have_fut) {
+      take(fut);
+      ok = advance();
+      issue(fut, st);
+    } else {
+      cp_async_commit();
+    }
+
+    // ---- columns: C, mask, dropped energy, C^T, in place
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      float4* const line = tb + 138 * p + 17 * j + 8 * i;
+      float2 cv[16], y[16], uo[16];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 v = line[q];
+        cv[2 * q] = make_float2(v.x, v.y);
+        cv[2 * q + 1] = make_float2(v.z, v.w);
+      }
+      dct16_fwd(cv, y);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        if (!((keep >> (16 * i + u)) & 1u)) {
+          acc = __ffma2_rn(y[u], y[u], acc);
+          y[u] = make_float2(0.f, 0.f);
+        }
+      }
+      dct16_inv(y, uo);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) line[q] = make_float4(uo[2 * q].x, uo[2 * q].y, uo[2 * q + 1].x, uo[2 * q + 1].y);
+    }
+    __syncwarp();
+
+    // ---- rows: C^T, rint, clamp, pack, store
+#pragma unroll
+    for (int tr = 0; tr < 2; ++tr) {
+      const int rr = tr ^ jb1;
+      const float2* const fin = reinterpret_cast<const float2*>(tb + 138 * p + j) + rr;
+      float2 v[16], z[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v[c] = fin[2 * (8 * c + (c >> 1))];
+      dct16_inv(v, z);
+      unsigned oa[4], ob[4];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        int qa[4], qb[4];
+#pragma unroll
+        for (int e4 = 0; e4 < 4; ++e4) {
+          // rint by the magic add 1.5 * 2^23, then the saturating u8 pack
+          const float2 m = __fadd2_rn(z[4 * g + e4], make_float2(12582912.0f, 12582912.0f));
+          qa[e4] = (int)(__float_as_uint(m.x) - 0x4B400000u);
+          qb[e4] = (int)(__float_as_uint(m.y) - 0x4B400000u);
+        }
+        oa[g] = pack_u8(qa[1], qa[0], pack_u8(qa[3], qa[2], 0u));
+        ob[g] = pack_u8(qb[1], qb[0], pack_u8(qb[3], qb[2], 0u));
+      }
+      uint8_t* d = cur.dst + rr * cur.dst_pitch;
+      if (va) __stcs(reinterpret_cast<uint4*>(d), make_uint4(oa[0], oa[1], oa[2], oa[3]));
+      if (vb) __stcs(reinterpret_cast<uint4*>(d + 64), make_uint4(ob[0], ob[1], ob[2], ob[3]));
+    }
+
+    const float tot = warp_sum((va ? acc.x : 0.f) + (vb ? acc.y : 0.f));
+    if (lane == 0) tile_sse[cur.t] = tot;
+    __syncwarp();
+
+    if (!have_nxt) break;
+    cur = nxt;
+    nxt = fut;
+    have_nxt = have_fut;
+    st ^= 1;
+  }
+  cp_async_wait<0>();
+  if (!ok && lane == 0) set_status(status, kDevBadJob);
+}
+
+// --------------------------------------------------------------------------
 // Per-image PSNR from the per-tile SSE partials (FP64, fixed summation order).
 // --------------------------------------------------------------------------
 __global__ void psnr_finalize_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles,
@@ -1655,6 +1904,36 @@ cudaError_t launch_ssim(const ImageJob* d_jobs, int njobs, long long ntiles, flo
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, ssim_finalize_kernel, d_jobs, njobs, ntiles, (const float*)d_tile_sum, d_out);
+}
+
+cudaError_t launch_zonal_dct(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
+                             float* d_tile_sse, int* d_status, int num_sms, cudaStream_t stream) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (ntiles >= (1LL << 30)) return cudaErrorInvalidValue;
+  static std::atomic<bool> ready[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64 || !ready[dev].load()) {
+    // the orthonormal DCT-II matrix, FP64 -> FP32
+    float c[16][16];
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < 16; ++k)
+      for (int jj = 0; jj < 16; ++jj)
+        c[k][jj] = (float)((k == 0 ? std::sqrt(1.0 / 16.0) : std::sqrt(2.0 / 16.0)) *
+                           std::cos(pi * (2 * jj + 1) * k / 32.0));
+    e = cudaMemcpyToSymbolAsync(kDctC, c, sizeof(c), 0, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) ready[dev].store(true);
+  }
+  int per_sm = 0;
+  e = occupancy_with_smem(&per_sm, dct_zonal_kernel, 128, 4 * kDctWarpSmemBytes);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<long long>((long long)num_sms * std::max(1, per_sm), (ntiles + 3) / 4);
+  return launch_with_smem(dct_zonal_kernel, grid, 128, 4 * kDctWarpSmemBytes, stream, d_jobs, njobs, ntiles, d_wtab,
+                          d_tile_sse, d_status);
 }
 
 int quant_ctas_per_sm() {

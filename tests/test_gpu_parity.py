@@ -294,3 +294,31 @@ def test_in_tree_library_loaded(torch):
     assert os.path.dirname(path) == os.path.dirname(os.path.abspath(atdct16.__file__))
     maps = open("/proc/self/maps").read()
     assert path in maps
+
+
+# --------------------------------------------------------------------------
+# Exact-DCT baseline (FP32 dense DCT-II through the same zonal procedure).
+# Stored pixels equal the FP64 route's except where the FP64 reconstruction
+# lies within 2e-3 of a half-integer (FP32 products carry ~1e-5 error).
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(16, 16), (48, 272), (96, 160)])
+def test_zonal_dct_baseline_matches_fp64(torch, plan, shape):
+    h, w = shape
+    rs = (0, 1, 6, 36, 100, 256)
+    imgs = [synth.ar1_image(h, w, 0.9, 70 + k) for k in range(len(rs))]
+    src = [torch.from_numpy(im).cuda() for im in imgs]
+    dst = [torch.zeros_like(s) for s in src]
+    psnr = torch.empty(len(rs), dtype=torch.float64, device="cuda")
+    plan.compress_zonal_dct([atdct16.image(s, d, r) for s, d, r in zip(src, dst, rs)], psnr)
+    torch.cuda.synchronize()
+    for im, r, d, p in zip(imgs, rs, dst, psnr.cpu().tolist()):
+        ref = O.compress_zonal_fp64(im, r, "dct")
+        rec = ref["recon"]
+        want = np.clip(np.rint(rec), 0, 255)
+        near_tie = np.abs(np.abs(rec - np.floor(rec)) - 0.5) < 2e-3
+        got = d.cpu().numpy().astype(np.float64)
+        assert np.array_equal(got[~near_tie], want[~near_tie]), r
+        if r == 256:  # nothing dropped: +inf here, FP64 rounding residue (> 200 dB) in the route
+            assert math.isinf(p) and ref["psnr"] > 200.0
+        else:
+            assert p == pytest.approx(ref["psnr"], rel=PSNR_RTOL, abs=PSNR_ATOL)
