@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--quant-only", action="store_true",
                     help="run only the quantisation phase (--steps/--warmup apply) and print its JSON")
     ap.add_argument("--quant-frames", type=int, default=24)
+    ap.add_argument("--coef-only", action="store_true",
+                    help="run only the coefficient-pipeline phase (--steps applies) and print its JSON")
     ap.add_argument("--mixed-images", type=int, default=1000)
     ap.add_argument("--serve-rates", default="100,250,500,1000,2000,5000")
     return ap.parse_args()
@@ -243,7 +245,7 @@ def quant_phase(torch, atdct16, synth, dev, n_frames, steps, warmup, peak_gbs):
     240-frame sequence, one input copy per QP.  Reports throughput and the
     HBM fraction of the quantisation kernel (4 bytes per sample: int16 in,
     int16 out), without and with the optional level output (+2 bytes per
-    sample)."""
+    sample), row-major and zig-zag."""
     frames = synth.residual_frames(n_frames)
     planes = [torch.from_numpy(p).to(dev) for fr in frames for p in fr]
     qps = synth.QUANT_QP_SWEEP
@@ -252,12 +254,13 @@ def quant_phase(torch, atdct16, synth, dev, n_frames, steps, warmup, peak_gbs):
     outs = [[torch.empty_like(p) for p in planes] for _ in qps]
     descs = atdct16.descriptors([atdct16.image(p, o, qp) for qp, ii, oo in zip(qps, ins, outs) for p, o in zip(ii, oo)])
     samples = sum(p.numel() for p in planes) * len(qps)
-    plan = atdct16.Plan(atdct16.I16, max_images=len(descs), workspace_bytes=1 << 30)
+    rplan = atdct16.Plan(atdct16.I16, max_images=len(descs), workspace_bytes=1 << 30)
+    zplan = atdct16.Plan(atdct16.I16, max_images=len(descs), workspace_bytes=1 << 30, zigzag=True)
     psnr = torch.empty(len(descs), dtype=torch.float64, device=dev)
     levels = torch.empty(samples, dtype=torch.int16, device=dev)
     res = {"frames": n_frames, "planes_per_qp": len(planes), "qps": list(qps), "samples_per_step": samples,
            "steps": steps}
-    for tag, lv in (("no_levels", None), ("levels", levels)):
+    for tag, lv, plan in (("no_levels", None, rplan), ("levels", levels, rplan), ("levels_zigzag", levels, zplan)):
         for _ in range(max(warmup, 3)):
             plan.compress_quant(descs, psnr, levels=lv)
         torch.cuda.synchronize()
@@ -277,6 +280,65 @@ def quant_phase(torch, atdct16, synth, dev, n_frames, steps, warmup, peak_gbs):
         res[tag] = {"ms_per_step": ms, "kernel_ms": k, "gsamples_s": samples / (ms / 1e3) / 1e9,
                     "kernel_gbs": byts / (k / 1e3) / 1e9, "kernel_frac_hbm": byts / (k / 1e3) / 1e9 / peak_gbs}
     res["mean_psnr_db"] = float(psnr.mean().item())
+    rplan.close()
+    zplan.close()
+    return res
+
+
+# --------------------------------------------------------------------------
+def coef_phase(torch, atdct16, batch, dev, peak_gbs, reps=50):
+    """The standalone coefficient pipeline on one 4096 x 8192 u8 image (the
+    64 bench images tiled 8 x 8, beside its mirror image; 33.5 Mpx): 2-D
+    forward and exact inverse with row-major and zig-zag block layouts, and
+    the 1-D forward / inverse of the same bytes as 16-sample vectors.  Two
+    rotating input / coefficient / output sets; every call moves 168 MB
+    (> L2).  Algorithmic bytes: 1 per pixel plus 4 per coefficient.  Each
+    inverse must reproduce its forward's input exactly (checked)."""
+    import numpy as np
+
+    n, side = batch.shape[0], batch.shape[1]
+    g = int(round(math.sqrt(n)))
+    grid = batch[: g * g].reshape(g, g, side, side).transpose(0, 2, 1, 3).reshape(g * side, g * side)
+    img = torch.from_numpy(np.ascontiguousarray(np.concatenate([grid, grid[:, ::-1]], axis=1))).to(dev)
+    h, w = img.shape
+    px = h * w
+    ins = [img, torch.flip(img, dims=[0]).contiguous()]
+    coef = [torch.empty(px, dtype=torch.int32, device=dev) for _ in range(2)]
+    outs = [torch.empty_like(img) for _ in range(2)]
+    byts = 5.0 * px
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for k in range(4):
+            fn(k)
+        torch.cuda.synchronize()
+        e0.record()
+        for k in range(reps):
+            fn(k)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = byts / (ms / 1e3) / 1e9
+        return {"ms": ms, "gpx_s": px / (ms / 1e3) / 1e9, "gbs": gbs, "frac_hbm": gbs / peak_gbs}
+
+    res = {"image": f"{h}x{w} u8", "pixels": px, "bytes_per_call": byts, "reps": reps}
+    exact = True
+    for zig in (False, True):
+        plan = atdct16.Plan(atdct16.U8, max_images=1, zigzag=zig)
+        tag = "zigzag" if zig else "rowmajor"
+        res["forward_2d_" + tag] = timed(lambda k: plan.forward(ins[k % 2], coef[k % 2]))
+        res["inverse_2d_" + tag] = timed(lambda k: plan.inverse(coef[k % 2], outs[k % 2]))
+        torch.cuda.synchronize()
+        exact = exact and all(torch.equal(o, i) for o, i in zip(outs, ins))
+        if not zig:
+            res["forward_1d"] = timed(lambda k: plan.forward_1d(ins[k % 2], coef[k % 2]))
+            res["inverse_1d"] = timed(lambda k: plan.inverse_1d(coef[k % 2], outs[k % 2]))
+            torch.cuda.synchronize()
+            exact = exact and all(torch.equal(o, i) for o, i in zip(outs, ins))
+        if plan.last_device_status() != atdct16.OK:
+            raise RuntimeError("device-side status error in the coefficient phase")
+        plan.close()
+    res["round_trips_exact"] = bool(exact)
     return res
 
 
@@ -635,6 +697,7 @@ def run_ours(args):
         }
         line["cpu_baseline"] = cpu_baseline(batch, args.cpu_seconds) if args.cpu_seconds > 0 else None
         if not args.no_extras:
+            line["coefficients"] = coef_phase(torch, atdct16, batch, dev, peak)
             line["ssim"] = ssim_phase(torch, atdct16, plan, sets[0][2], jobs, px_step)
             line["dct_baseline"] = dct_baseline_phase(torch, atdct16, plan, sets, jobs, px_step, None)
             del sets
@@ -668,12 +731,31 @@ def run_quant_only(args):
     return 0
 
 
+def run_coef_only(args):
+    """The coefficient-pipeline phase alone, on one GPU (profiling entry)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_1606_05562_gb300 import atdct16, synth
+    from paper_1606_05562_gb300 import build as b
+
+    b.build()
+    peak, _ = measured_peak_hbm()
+    batch = synth.image_batch_512(N_IMAGES, SIDE, first_seed=100)
+    print(json.dumps({"coefficients": coef_phase(torch, atdct16, batch, torch.device("cuda", 0), peak,
+                                                 reps=max(args.steps, 1))}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.quant_only:
         return run_quant_only(args)
+    if args.coef_only:
+        return run_coef_only(args)
     return run_ours(args)
 
 

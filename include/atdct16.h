@@ -88,9 +88,18 @@ const char* atdct16_status_string(atdct16_status s);
  *                  (0 = a default of 256 MiB).  The plan sizes its per-tile
  *                  partial-sum buffer from it; calls whose batches need more
  *                  tiles than fit return ATDCT16_ENOMEM.
- *   flags          0 (reserved)
+ *   flags          0, or ATDCT16_PLAN_ZIGZAG: the 256 coefficients of every
+ *                  block in atdct16_forward / atdct16_inverse and the 256
+ *                  levels of every block in atdct16_compress_quant are stored
+ *                  in the zig-zag scan of Sec. 4 (entry k of a block is the
+ *                  coefficient (u, v) at scan position k: anti-diagonals
+ *                  s = u + v in increasing order, even s with u decreasing,
+ *                  odd s with v decreasing), the order an entropy coder reads
+ *                  them in; without it they are row-major in (u, v).  Other
+ *                  bits: ATDCT16_EINVAL.
  * Allocates the plan's workspace (device tables, descriptor ring, partials)
  * with cudaMalloc and pinned host staging with cudaHostAlloc. */
+#define ATDCT16_PLAN_ZIGZAG 1u
 atdct16_status atdct16_plan_create(atdct16_plan_t* plan, atdct16_dtype dtype, int32_t max_images,
                                    size_t workspace_budget_bytes, uint32_t flags);
 
@@ -101,8 +110,11 @@ atdct16_status atdct16_plan_destroy(atdct16_plan_t plan);
  * the image into disjoint 16x16 blocks).  S is not applied.
  *   d_src   image of `dtype` (U8 or I16) with pitch `pitch` bytes, w x h
  *   d_coef  output, block-major: block b = by*(w/16)+bx occupies
- *           d_coef[256*b .. 256*b+255], row-major in (u, v).  Exact int32
- *           (|Y| <= 65280 for U8 input, <= 256*32768 for I16 input). */
+ *           d_coef[256*b .. 256*b+255], row-major in (u, v), or in zig-zag
+ *           order if the plan was created with ATDCT16_PLAN_ZIGZAG.  Exact
+ *           int32 (|Y| <= 65280 for U8 input, <= 256*32768 for I16 input).
+ * w, h multiples of 16; d_src, d_coef and pitch 16-byte aligned (EINVAL
+ * otherwise).  Asynchronous on `stream`; reads d_src once, writes d_coef once. */
 atdct16_status atdct16_forward(atdct16_plan_t plan, atdct16_dtype dtype, const void* d_src,
                                int64_t pitch, int32_t w, int32_t h, int32_t* d_coef,
                                cudaStream_t stream);
@@ -111,11 +123,36 @@ atdct16_status atdct16_forward(atdct16_plan_t plan, atdct16_dtype dtype, const v
  * computed exactly: Z = T^T (W Y W) T with the integer W = 48 S^2, then
  * X_hat = Z / 2304 rounded half to even (decided exactly from Z) and
  * clamped to the range of `dtype`.  Coefficients produced by atdct16_forward reconstruct the input
- * bit-exactly.  Layout of d_coef as for atdct16_forward.  Integer
- * arithmetic is 64-bit, so any int32 coefficients are accepted. */
+ * bit-exactly.  Layout of d_coef as for atdct16_forward (the plan's order).
+ * Any int32 coefficients are accepted and give the exact result: tiles whose
+ * coefficients all satisfy |Y| <= 2^18 run in 32-bit integers (|Z| < 2^31),
+ * others in two 32-bit halves combined in 64 bits.  d_coef, d_dst and pitch
+ * 16-byte aligned, w, h multiples of 16 (EINVAL otherwise). */
 atdct16_status atdct16_inverse(atdct16_plan_t plan, atdct16_dtype dtype, const int32_t* d_coef,
                                int32_t w, int32_t h, void* d_dst, int64_t pitch,
                                cudaStream_t stream);
+
+/* 1-D forward transform (Sec. 2, y = T x; S is not applied) of `count`
+ * contiguous vectors of 16 samples of `dtype` (U8 or I16): d_src holds
+ * count * 16 samples, d_coef receives count * 16 exact int32 coefficients,
+ * vector i at d_coef[16 i .. 16 i + 15] in frequency order u = 0..15
+ * (|y| <= 16 * 255 for U8, <= 16 * 32768 for I16).  A packed image of width
+ * w (a multiple of 16) is w / 16 vectors per row, so one call transforms
+ * all its 16-sample row segments.  count = 0 does nothing; d_src and d_coef
+ * 16-byte aligned (EINVAL otherwise).  Asynchronous on `stream`. */
+atdct16_status atdct16_forward_1d(atdct16_plan_t plan, atdct16_dtype dtype, const void* d_src, int64_t count,
+                                  int32_t* d_coef, cudaStream_t stream);
+
+/* 1-D exact inverse (C_hat^T C_hat = T^T S^2 T = I, Sec. 2): for each of
+ * `count` vectors of 16 int32 coefficients,
+ *     x_n = round_half_even( sum_u T[u][n] W_u y_u / 48 ),  W = 48 S^2,
+ * clamped to the range of `dtype` and stored as 16 samples of `dtype` at
+ * d_dst[16 i ..].  Exact for any int32 input (64-bit arithmetic for vectors
+ * with a coefficient of magnitude >= 2^24).  atdct16_forward_1d output
+ * reconstructs its input bit-exactly.  Alignment and count rules as
+ * atdct16_forward_1d. */
+atdct16_status atdct16_inverse_1d(atdct16_plan_t plan, atdct16_dtype dtype, const int32_t* d_coef, int64_t count,
+                                  void* d_dst, cudaStream_t stream);
 
 /* Fused zonal compression of a batch of uint8 images (Sec. 4 procedure):
  * forward transform, keep the first r zig-zag coefficients of every block
@@ -141,8 +178,10 @@ atdct16_status atdct16_compress_zonal(atdct16_plan_t plan, const atdct16_image* 
  * is taken in FP32 as fp32(|Y| * fp32(s_u s_v / Qstep)) + 0.5 (no fused
  * multiply-add).  The inverse runs in FP32.  PSNR (peak 255) of the
  * unrounded reconstruction goes to d_psnr[i].
- *   d_levels  optional (may be NULL): int16 levels, block-major as for
- *             atdct16_forward, images concatenated in batch order. */
+ *   d_levels  optional (may be NULL, else 16-byte aligned): int16 levels,
+ *             block-major as for atdct16_forward (row-major in (u, v), or
+ *             zig-zag order with ATDCT16_PLAN_ZIGZAG), images concatenated
+ *             in batch order. */
 atdct16_status atdct16_compress_quant(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n,
                                       int16_t* d_levels, double* d_psnr, double* d_sse,
                                       cudaStream_t stream);

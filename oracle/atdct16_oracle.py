@@ -290,6 +290,41 @@ def round_half_even_div(num: np.ndarray, den: int) -> np.ndarray:
     return np.where(tie & (q % 2 == 1), q - 1, q)
 
 
+def to_zigzag(coef: np.ndarray) -> np.ndarray:
+    """Blocks ``(..., 16, 16)`` -> ``(..., 256)``: entry k of a block is the
+    coefficient at zig-zag scan position k (Sec. 4 scan), the order in which
+    an entropy coder reads a block."""
+    order = zigzag_order()
+    c = np.asarray(coef)
+    return np.stack([c[..., u, v] for (u, v) in order], axis=-1)
+
+
+def from_zigzag(z: np.ndarray) -> np.ndarray:
+    """Inverse of ``to_zigzag``: ``(..., 256)`` -> ``(..., 16, 16)``."""
+    z = np.asarray(z)
+    out = np.zeros(z.shape[:-1] + (N, N), dtype=z.dtype)
+    for k, (u, v) in enumerate(zigzag_order()):
+        out[..., u, v] = z[..., k]
+    return out
+
+
+def forward_1d(x: np.ndarray) -> np.ndarray:
+    """``y = T x`` (Sec. 2, S left out) for every 16-sample vector along the
+    last axis, exact int64."""
+    return np.einsum("un,...n->...u", T, np.asarray(x).astype(np.int64))
+
+
+def inverse_1d(coef: np.ndarray, out_dtype=np.uint8) -> np.ndarray:
+    """Exact 1-D inverse of integer coefficients along the last axis:
+    ``C_hat^T (S y) = T^T S^2 y = T^T (W y) / 48``, rounded half to even and
+    clamped to the output type."""
+    d = np.asarray(coef).astype(np.int64) * w_diag()
+    z = np.einsum("un,...u->...n", T, d)
+    x = round_half_even_div(z, 48)
+    info = np.iinfo(out_dtype)
+    return np.clip(x, info.min, info.max).astype(out_dtype)
+
+
 def inverse_exact(coef: np.ndarray, out_dtype=np.uint8) -> np.ndarray:
     """Reconstruct an image from integer coefficients (no coefficient dropped
     unless ``coef`` already has zeros): exact round-half-to-even of

@@ -15,6 +15,7 @@ import threading
 from . import build as _build
 
 U8, I16 = 0, 1
+PLAN_ZIGZAG = 1  # ATDCT16_PLAN_ZIGZAG
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EDEVICE = range(7)
 
 
@@ -75,6 +76,8 @@ _SIGS = {
     "atdct16_plan_destroy": (C.c_int, [C.c_void_p]),
     "atdct16_forward": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "atdct16_inverse": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p]),
+    "atdct16_forward_1d": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "atdct16_inverse_1d": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "atdct16_compress_zonal": (C.c_int, [C.c_void_p, C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "atdct16_compress_quant": (C.c_int, [C.c_void_p, C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "atdct16_psnr": (C.c_int, [C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
@@ -184,11 +187,16 @@ def image(src, dst, param, width=None, height=None):
 class Plan:
     """Owns an ``atdct16_plan_t`` (device workspace)."""
 
-    def __init__(self, dtype=U8, max_images=64, workspace_bytes=0):
+    def __init__(self, dtype=U8, max_images=64, workspace_bytes=0, zigzag=False, flags=None):
+        """``zigzag``: block coefficients (forward / inverse) and quantisation
+        levels in the zig-zag scan order; ``flags`` overrides it with raw
+        ``atdct16_plan_create`` flags."""
         self._h = C.c_void_p()
-        _check(lib().atdct16_plan_create(C.byref(self._h), dtype, max_images, workspace_bytes, 0), "plan_create")
+        fl = (PLAN_ZIGZAG if zigzag else 0) if flags is None else flags
+        _check(lib().atdct16_plan_create(C.byref(self._h), dtype, max_images, workspace_bytes, fl), "plan_create")
         self.dtype = dtype
         self.max_images = max_images
+        self.zigzag = bool(fl & PLAN_ZIGZAG)
 
     @property
     def handle(self):
@@ -214,6 +222,15 @@ class Plan:
         h, w = out.shape[-2], out.shape[-1]
         _check(lib().atdct16_inverse(self._h, dtype, _ptr(coef), w, h, _ptr(out),
                                      out.stride(-2) * out.element_size(), _stream(stream)), "inverse")
+
+    def forward_1d(self, x, coef, count=None, dtype=U8, stream=None):
+        """``x``: 16 * count samples (contiguous), ``coef``: 16 * count int32."""
+        n = x.numel() // 16 if count is None else count
+        _check(lib().atdct16_forward_1d(self._h, dtype, _ptr(x), n, _ptr(coef), _stream(stream)), "forward_1d")
+
+    def inverse_1d(self, coef, out, count=None, dtype=U8, stream=None):
+        n = coef.numel() // 16 if count is None else count
+        _check(lib().atdct16_inverse_1d(self._h, dtype, _ptr(coef), n, _ptr(out), _stream(stream)), "inverse_1d")
 
     def compress_zonal(self, images, psnr, sse=None, stream=None):
         """``images``: list of Image descriptors (param = r), or an array from

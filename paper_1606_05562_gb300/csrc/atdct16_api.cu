@@ -16,6 +16,7 @@ using namespace atdct16;
 struct atdct16_plan_st {
   int device = 0;
   atdct16_dtype dtype = ATDCT16_U8;
+  bool zigzag = false;                  // ATDCT16_PLAN_ZIGZAG: block coefficients / levels in zig-zag order
   int max_images = 0;
   long long max_tiles = 0;
   int num_sms = 0;
@@ -247,11 +248,13 @@ atdct16_status atdct16_plan_destroy(atdct16_plan_t plan) {
 
 atdct16_status atdct16_plan_create(atdct16_plan_t* out, atdct16_dtype dtype, int32_t max_images,
                                    size_t workspace_budget_bytes, uint32_t flags) {
-  if (!out || max_images < 1 || flags != 0 || (dtype != ATDCT16_U8 && dtype != ATDCT16_I16)) return ATDCT16_EINVAL;
+  if (!out || max_images < 1 || (flags & ~ATDCT16_PLAN_ZIGZAG) != 0 || (dtype != ATDCT16_U8 && dtype != ATDCT16_I16))
+    return ATDCT16_EINVAL;
   *out = nullptr;
   atdct16_plan_st* plan = new (std::nothrow) atdct16_plan_st();
   if (!plan) return ATDCT16_ENOMEM;
   plan->dtype = dtype;
+  plan->zigzag = (flags & ATDCT16_PLAN_ZIGZAG) != 0;
   plan->max_images = max_images;
   if (cudaGetDevice(&plan->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device) != cudaSuccess) {
@@ -329,17 +332,35 @@ atdct16_status atdct16_forward(atdct16_plan_t plan, atdct16_dtype dtype, const v
   if (w <= 0 || h <= 0 || (w & 15) || (h & 15) || pitch < (int64_t)w * elem || (pitch & 15)) return ATDCT16_EINVAL;
   if (!aligned16(d_src) || !aligned16(d_coef)) return ATDCT16_EINVAL;
   plan->last_stream = stream;
-  return from_cuda(launch_forward(dtype, d_src, pitch, w, h, d_coef, stream));
+  return from_cuda(launch_forward(dtype, d_src, pitch, w, h, d_coef, plan->zigzag, plan->num_sms, stream));
 }
 
 atdct16_status atdct16_inverse(atdct16_plan_t plan, atdct16_dtype dtype, const int32_t* d_coef, int32_t w,
                                int32_t h, void* d_dst, int64_t pitch, cudaStream_t stream) {
   if (!plan || !d_dst || !d_coef || (dtype != ATDCT16_U8 && dtype != ATDCT16_I16)) return ATDCT16_EINVAL;
   const int elem = dtype == ATDCT16_U8 ? 1 : 2;
-  if (w <= 0 || h <= 0 || (w & 15) || (h & 15) || pitch < (int64_t)w * elem) return ATDCT16_EINVAL;
-  if (dtype == ATDCT16_I16 && ((pitch & 1) || (reinterpret_cast<uintptr_t>(d_dst) & 1))) return ATDCT16_EINVAL;
+  if (w <= 0 || h <= 0 || (w & 15) || (h & 15) || pitch < (int64_t)w * elem || (pitch & 15)) return ATDCT16_EINVAL;
+  if (!aligned16(d_dst) || !aligned16(d_coef)) return ATDCT16_EINVAL;
   plan->last_stream = stream;
-  return from_cuda(launch_inverse(dtype, d_coef, w, h, d_dst, pitch, stream));
+  return from_cuda(launch_inverse(dtype, d_coef, w, h, d_dst, pitch, plan->zigzag, plan->num_sms, stream));
+}
+
+atdct16_status atdct16_forward_1d(atdct16_plan_t plan, atdct16_dtype dtype, const void* d_src, int64_t count,
+                                  int32_t* d_coef, cudaStream_t stream) {
+  if (!plan || count < 0 || (dtype != ATDCT16_U8 && dtype != ATDCT16_I16)) return ATDCT16_EINVAL;
+  if (count == 0) return ATDCT16_OK;
+  if (!d_src || !d_coef || !aligned16(d_src) || !aligned16(d_coef)) return ATDCT16_EINVAL;
+  plan->last_stream = stream;
+  return from_cuda(launch_forward_1d(dtype, d_src, count, d_coef, plan->num_sms, stream));
+}
+
+atdct16_status atdct16_inverse_1d(atdct16_plan_t plan, atdct16_dtype dtype, const int32_t* d_coef, int64_t count,
+                                  void* d_dst, cudaStream_t stream) {
+  if (!plan || count < 0 || (dtype != ATDCT16_U8 && dtype != ATDCT16_I16)) return ATDCT16_EINVAL;
+  if (count == 0) return ATDCT16_OK;
+  if (!d_coef || !d_dst || !aligned16(d_coef) || !aligned16(d_dst)) return ATDCT16_EINVAL;
+  plan->last_stream = stream;
+  return from_cuda(launch_inverse_1d(dtype, d_coef, count, d_dst, plan->num_sms, stream));
 }
 
 atdct16_status atdct16_compress_zonal(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n,
@@ -377,7 +398,7 @@ atdct16_status atdct16_compress_quant(atdct16_plan_t plan, const atdct16_image* 
   if (s != ATDCT16_OK) return s;
   const int grid = (int)std::min<long long>(plan->quant_grid, (ntiles + kZonalWarps - 1) / kZonalWarps);
   const int pk = prof_begin(plan, stream);
-  cudaError_t e = launch_quant(plan->d_jobs, n, ntiles, plan->d_qtab, d_levels, plan->d_tile_sse,
+  cudaError_t e = launch_quant(plan->d_jobs, n, ntiles, plan->d_qtab, d_levels, plan->zigzag, plan->d_tile_sse,
                                plan->d_status, grid, stream);
   prof_end(plan, pk, stream);
   if (e == cudaSuccess)

@@ -1,0 +1,703 @@
+// Coefficient pipeline of the multiplierless 16-point transform (Sec. 2,
+// Sec. 4): the forward and the exact inverse on their own, for callers that
+// process the coefficients themselves (an entropy coder, an external
+// quantiser).
+//
+//   2-D forward   Y = T X T^T per 16x16 block, exact int32
+//   2-D inverse   X_hat = T^T (W Y W) T / 2304 (W = 48 S^2, S from Sec. 2),
+//                 rounded half to even, clamped to the pixel type; exact for
+//                 any int32 Y
+//   1-D forward   y = T x per 16-sample vector
+//   1-D inverse   x_hat = T^T (W y) / 48, rounded half to even, clamped
+//
+// Block coefficients are stored row-major in (u, v) or, with the zig-zag
+// option, in the scan order of Sec. 4 (entry k of a block is coefficient
+// (u, v) of scan position k), the order an entropy coder reads them in.
+//
+// 2-D organisation (as in the fused kernels): persistent 4-warp CTAs, one
+// warp per 16 x 128 tile (eight blocks, which are consecutive in the
+// block-major coefficient array, so a tile's coefficients are one 8 KB
+// range).  Lane (p, j) = (lane & 3, lane >> 2) owns rows (and later
+// columns) 2j, 2j+1 of blocks p and p + 4.  Every global access moves whole
+// 32-byte sectors: image rows as 16-byte segments, coefficients as 512-byte
+// runs per warp instruction; the transposition and the reordering go
+// through shared memory:
+//   line buffer  unit(p, c, q) = 138 p + 8 c + (c >> 1) + q (16-byte units):
+//                rows 2q, 2q+1 of column c of blocks p, p + 4;
+//   block stage  8 blocks x 256 int32, word (16 u + v) of block b stored at
+//                (16 u + v) ^ bswz(b), bswz(b) = (b & 1) | ((b & 2) << 3),
+//                which spreads the four blocks of a lane quad over all 32
+//                banks for the per-column accesses and keeps 16-byte
+//                chunks whole (XOR 16 moves a chunk, XOR 1 swaps within it).
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "atdct16_butterfly.cuh"
+#include "atdct16_internal.h"
+
+namespace atdct16 {
+namespace {
+
+constexpr int kCWarps = 4;
+constexpr int kCLineUnits = 549;
+constexpr int kCStageUnits = 512;
+constexpr int kCWarpSmemBytes = 16 * (kCLineUnits + kCStageUnits);
+
+// W_u = 48 S_u^2 = 48 / nnz_u for rows u = 0..15 of T: nnz_u in {16, 12, 8},
+// i.e. W_u in {3, 4, 6}, coded 0, 1, 2 in two bits per row.
+__host__ __device__ constexpr int w_of(int u) {
+  return 3 + ((0x56945290u >> (2 * u)) & 3u) + (((0x56945290u >> (2 * u)) & 3u) >> 1);
+}
+static_assert(w_of(0) == 3 && w_of(2) == 4 && w_of(3) == 6 && w_of(15) == 4, "W = 48 S^2");
+
+__device__ __forceinline__ int bswz(int b) { return (b & 1) | ((b & 2) << 3); }
+
+// (16 u + v) of scan position k of the zig-zag order of Sec. 4 (JPEG
+// convention extended to 16x16): anti-diagonal s = u + v, even s walked
+// with u decreasing, odd s with v decreasing.
+__device__ int zz_word(int k) {
+  int s = 0, base = 0;
+  while (s < 30) {
+    const int len = s < 16 ? s + 1 : 31 - s;
+    if (k < base + len) break;
+    base += len;
+    ++s;
+  }
+  const int off = k - base, hi = s < 16 ? s : 15;
+  const int a = hi - off, b = s - a;
+  return (s & 1) ? 16 * b + a : 16 * a + b;
+}
+// Four consecutive scan positions k .. k+3, one byte each.
+__device__ unsigned zz_pack4(int k) {
+  return (unsigned)zz_word(k) | ((unsigned)zz_word(k + 1) << 8) | ((unsigned)zz_word(k + 2) << 16) |
+         ((unsigned)zz_word(k + 3) << 24);
+}
+__device__ __forceinline__ int zz_byte(unsigned packed, int e) { return (packed >> (8 * e)) & 0xff; }
+
+__device__ __forceinline__ unsigned word_at(const uint4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+// 16-byte loads and stores that bypass L1 allocation / mark the line
+// evict-first: every byte is touched once.
+__device__ __forceinline__ uint4 ldg_stream(const void* ptr) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(ptr));
+  return v;
+}
+__device__ __forceinline__ void stg_stream(void* ptr, uint4 v) { __stcs(reinterpret_cast<uint4*>(ptr), v); }
+
+// 2^23 + 256 * (byte k of w), exact, one byte permute.
+__device__ __forceinline__ float u8_x256(unsigned w, int k) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7404u | ((unsigned)k << 4)));
+}
+// int16 field -> 2^23 + 32768 + v as an exact float (offset binary in the mantissa).
+__device__ __forceinline__ float i16_lo_f(unsigned w) { return __uint_as_float(((w & 0xffffu) ^ 0x8000u) | 0x4B000000u); }
+__device__ __forceinline__ float i16_hi_f(unsigned w) { return __uint_as_float(__byte_perm(w, 0x4B00u, 0x5432u) ^ 0x8000u); }
+
+// d = (c << 16) | (sat_u8(a) << 8) | sat_u8(b)
+__device__ __forceinline__ unsigned pack_sat_u8(unsigned a, unsigned b, unsigned c) {
+  unsigned d;
+  asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// Round half to even of n / kDen for 0 <= n < 2^31 - 1 (exact integer
+// division by a constant, remainder test for the tie).
+template <unsigned kDen>
+__device__ __forceinline__ int rne_div_u(unsigned n) {
+  const unsigned shifted = n + kDen / 2;
+  unsigned q = shifted / kDen;
+  if (shifted - q * kDen == 0u) q &= ~1u;  // exact tie: q - 0.5 and q are equally near; keep the even one
+  return (int)q;
+}
+
+// Exact round-half-even of z / kDen clamped to the output type's range
+// [lo, hi]: with n = z - lo kDen, every n <= 0 gives lo and every
+// n >= (hi - lo) kDen gives hi, so n is clamped to that interval first and
+// the quotient taken in unsigned 32-bit arithmetic.  Z is int (callers
+// guarantee |z| + 2^15 kDen < 2^31) or long long.
+template <int kDtype, unsigned kDen, class Z>
+__device__ __forceinline__ int round_clamp(Z z) {
+  constexpr int kLo = kDtype == 0 ? 0 : -32768, kHi = kDtype == 0 ? 255 : 32767;
+  constexpr Z kTop = (Z)(kHi - kLo) * (Z)kDen;
+  Z n = z - (Z)kLo * (Z)kDen;
+  n = n < (Z)0 ? (Z)0 : (n > kTop ? kTop : n);
+  return rne_div_u<kDen>((unsigned)n) + kLo;
+}
+
+template <class K, class... Args>
+cudaError_t launch_dyn(K kernel, int grid, int threads, int smem, cudaStream_t stream, Args... args) {
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  kernel<<<grid, threads, smem, stream>>>(args...);
+  return cudaGetLastError();
+}
+
+template <class K>
+int persistent_grid(K kernel, int threads, int smem, int num_sms, long long work_items_per_cta_round,
+                    long long work_items) {
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const long long need = (work_items + work_items_per_cta_round - 1) / work_items_per_cta_round;
+  long long g = (long long)num_sms * per_sm;
+  if (g > need) g = need;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// ---------------------------------------------------------------------------
+// 2-D forward: Y = T X T^T per block, exact in FP32.  U8: the row pass
+// carries the inputs as 2^23 + 256 x (one byte permute each), so every node
+// is a multiple of 256 below 2^28 and the offsets cancel in all rows but the
+// DC, which subtracts 16 * 2^23; the column nodes are 256 Y, |256 Y| < 2^24.
+// I16: the inputs themselves; every node is an integer of magnitude <= 2^23.
+// ---------------------------------------------------------------------------
+template <int kDtype, bool kZigzag>
+__global__ void __launch_bounds__(32 * kCWarps, 3)
+coef_forward_kernel(const uint8_t* __restrict__ src, long long pitch, int w, int h, int32_t* __restrict__ coef) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = lane & 3, j = lane >> 2;
+  float4* const line = reinterpret_cast<float4*>(csm + warp * kCWarpSmemBytes);
+  int* const stage = reinterpret_cast<int*>(line + kCLineUnits);
+  const int swz = bswz(p);
+  unsigned zz[2] = {0u, 0u};
+  if (kZigzag) {
+    zz[0] = zz_pack4(4 * lane);
+    zz[1] = zz_pack4(128 + 4 * lane);
+  }
+  constexpr int kElem = kDtype == 0 ? 1 : 2;
+  const int tiles_x = (w + kTileW - 1) / kTileW;
+  const int ntiles = tiles_x * (h >> 4);  // the launcher checks it fits
+  const int bpr = w >> 4;
+  for (int t = blockIdx.x * kCWarps + warp; t < ntiles; t += gridDim.x * kCWarps) {
+    const int ty = t / tiles_x, tx = t - ty * tiles_x;
+    const int nb = min(8, (w - tx * kTileW) >> 4);
+    const bool va = p < nb, vb = p + 4 < nb;
+    const uint8_t* s = src + (long long)(ty * kTileH + 2 * j) * pitch + (long long)(tx * kTileW + 16 * p) * kElem;
+    // ---- row pass on rows 2j, 2j+1 into the line buffer
+    float2* const half = reinterpret_cast<float2*>(line + 138 * p + j);
+    if (kDtype == 0) {
+      uint4 a[2], b[2];
+      a[0] = a[1] = b[0] = b[1] = make_uint4(0u, 0u, 0u, 0u);
+      if (va) {
+        a[0] = ldg_stream(s);
+        a[1] = ldg_stream(s + pitch);
+      }
+      if (vb) {
+        b[0] = ldg_stream(s + 64);
+        b[1] = ldg_stream(s + 64 + pitch);
+      }
+#pragma unroll
+      for (int tr = 0; tr < 2; ++tr) {
+        float2 xv[16], rv[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n)
+          xv[n] = make_float2(u8_x256(word_at(a[tr], n >> 2), n & 3), u8_x256(word_at(b[tr], n >> 2), n & 3));
+        fwd16(xv, rv);
+        rv[0] = bsub(rv[0], make_float2(134217728.0f, 134217728.0f));  // 16 * 2^23 of the offsets
+#pragma unroll
+        for (int k = 0; k < 16; ++k) half[2 * (8 * k + (k >> 1)) + tr] = rv[k];
+      }
+    } else {
+      uint4 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = b[i] = make_uint4(0u, 0u, 0u, 0u);
+      if (va) {
+        a[0] = ldg_stream(s);
+        a[1] = ldg_stream(s + 16);
+        a[2] = ldg_stream(s + pitch);
+        a[3] = ldg_stream(s + pitch + 16);
+      }
+      if (vb) {
+        b[0] = ldg_stream(s + 128);
+        b[1] = ldg_stream(s + 144);
+        b[2] = ldg_stream(s + pitch + 128);
+        b[3] = ldg_stream(s + pitch + 144);
+      }
+#pragma unroll
+      for (int tr = 0; tr < 2; ++tr) {
+        float2 xv[16], rv[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) {
+          const unsigned wa = word_at(a[2 * tr + (n >> 3)], (n & 7) >> 1);
+          const unsigned wb = word_at(b[2 * tr + (n >> 3)], (n & 7) >> 1);
+          const float2 m = (n & 1) ? make_float2(i16_hi_f(wa), i16_hi_f(wb)) : make_float2(i16_lo_f(wa), i16_lo_f(wb));
+          xv[n] = __fadd2_rn(m, make_float2(-8421376.0f, -8421376.0f));  // exact sample value
+        }
+        fwd16(xv, rv);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) half[2 * (8 * k + (k >> 1)) + tr] = rv[k];
+      }
+    }
+    __syncwarp();
+    // ---- column pass on columns 2j, 2j+1 into the block stage
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int c = 2 * j + i;
+      const float4* const ln = line + 138 * p + 17 * j + 8 * i;
+      float2 cv[16], y[16];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 v = ln[q];
+        cv[2 * q] = make_float2(v.x, v.y);
+        cv[2 * q + 1] = make_float2(v.z, v.w);
+      }
+      fwd16(cv, y);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        int ya, yb;
+        if (kDtype == 0) {
+          // Y = y / 256 exactly; 1.5 * 2^23 + Y puts Y in the low mantissa bits
+          const float2 m = __ffma2_rn(y[u], make_float2(0.00390625f, 0.00390625f), make_float2(12582912.0f, 12582912.0f));
+          ya = (int)(__float_as_uint(m.x) - 0x4B400000u);
+          yb = (int)(__float_as_uint(m.y) - 0x4B400000u);
+        } else {
+          ya = __float2int_rn(y[u].x);
+          yb = __float2int_rn(y[u].y);
+        }
+        const int wd = (16 * u + c) ^ swz;
+        stage[256 * p + wd] = ya;
+        stage[256 * (p + 4) + wd] = yb;
+      }
+    }
+    __syncwarp();
+    // ---- the tile's blocks as 512-byte runs, row-major or zig-zag
+    int32_t* const out = coef + ((long long)ty * bpr + tx * 8) * 256;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      if (b >= nb) break;
+      const int* const sb = stage + 256 * b;
+      const int bs = bswz(b);
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        uint4 v;
+        if (!kZigzag) {
+          v = reinterpret_cast<const uint4*>(sb)[(32 * hh + lane) ^ (bs >> 2)];
+          if (b & 1) v = make_uint4(v.y, v.x, v.w, v.z);
+        } else {
+          v.x = (unsigned)sb[zz_byte(zz[hh], 0) ^ bs];
+          v.y = (unsigned)sb[zz_byte(zz[hh], 1) ^ bs];
+          v.z = (unsigned)sb[zz_byte(zz[hh], 2) ^ bs];
+          v.w = (unsigned)sb[zz_byte(zz[hh], 3) ^ bs];
+        }
+        stg_stream(out + 256 * b + 4 * (32 * hh + lane), v);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2-D exact inverse: Z = T^T (W Y W) T, X_hat = Z / 2304 (Sec. 4 with
+// S^2 = W / 48 folded in), round half to even, clamp.
+//
+// A tile whose coefficients all satisfy |Y| <= 2^18 runs in int32: |Z| <=
+// (sum_u W_u)^2 2^18 = 68^2 2^18 < 2^31.  Any other tile (checked per warp)
+// splits Y = 2^16 Y_h + Y_l (|Y_h| <= 2^15, 0 <= Y_l < 2^16), transforms both
+// halves exactly in int32 and forms Z = 2^16 Z_h + Z_l in 64 bits.  The
+// low-half column results go to the block stage, into the words their lane
+// has just read (each lane reads and writes only its own 64 words there).
+// ---------------------------------------------------------------------------
+template <int kDtype>
+__device__ __forceinline__ void store_row(uint8_t* d, bool va, bool vb, const int (&qa)[16], const int (&qb)[16]) {
+  if (kDtype == 0) {
+    unsigned oa[4], ob[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      oa[g] = pack_sat_u8(qa[4 * g + 1], qa[4 * g], pack_sat_u8(qa[4 * g + 3], qa[4 * g + 2], 0u));
+      ob[g] = pack_sat_u8(qb[4 * g + 1], qb[4 * g], pack_sat_u8(qb[4 * g + 3], qb[4 * g + 2], 0u));
+    }
+    if (va) stg_stream(d, make_uint4(oa[0], oa[1], oa[2], oa[3]));
+    if (vb) stg_stream(d + 64, make_uint4(ob[0], ob[1], ob[2], ob[3]));
+  } else {
+    unsigned oa[8], ob[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      oa[g] = ((unsigned)qa[2 * g] & 0xffffu) | ((unsigned)qa[2 * g + 1] << 16);
+      ob[g] = ((unsigned)qb[2 * g] & 0xffffu) | ((unsigned)qb[2 * g + 1] << 16);
+    }
+    if (va) {
+      stg_stream(d, make_uint4(oa[0], oa[1], oa[2], oa[3]));
+      stg_stream(d + 16, make_uint4(oa[4], oa[5], oa[6], oa[7]));
+    }
+    if (vb) {
+      stg_stream(d + 128, make_uint4(ob[0], ob[1], ob[2], ob[3]));
+      stg_stream(d + 144, make_uint4(ob[4], ob[5], ob[6], ob[7]));
+    }
+  }
+}
+
+// Z (|Z| < 2^31) of two blocks -> rounded, clamped outputs.  U8: the exact
+// float Z (after clamping to [-1153, 589825], where the result is already
+// decided) times fp32(1/2304) equals Z / 2304 exactly at every half-integer
+// and is within 6e-5 of it elsewhere, far inside the 1/2304 gap to the next
+// half-integer; its round-half-even is read off the denormal bits of
+// fl(t * 2^-149) and saturated by the pack.  I16: integer division.
+template <int kDtype>
+__device__ __forceinline__ void round_pair(int za, int zb, int& qa, int& qb) {
+  if (kDtype == 0) {
+    const int ca = min(max(za, -1153), 589825), cb = min(max(zb, -1153), 589825);
+    float2 f = make_float2(__int_as_float(ca + 0x4B400000), __int_as_float(cb + 0x4B400000));
+    f = __fadd2_rn(f, make_float2(-12582912.0f, -12582912.0f));
+    f = __fmul2_rn(f, make_float2(1.0f / 2304.0f, 1.0f / 2304.0f));
+    f = __fmul2_rn(f, make_float2(__uint_as_float(1u), __uint_as_float(1u)));
+    qa = (int)__float_as_uint(f.x);
+    qb = (int)__float_as_uint(f.y);
+  } else {
+    qa = round_clamp<1, 2304u>(za);
+    qb = round_clamp<1, 2304u>(zb);
+  }
+}
+
+template <int kDtype, bool kZigzag>
+__global__ void __launch_bounds__(32 * kCWarps, 3)
+coef_inverse_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __restrict__ dst, long long pitch) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = lane & 3, j = lane >> 2, jb1 = (j >> 1) & 1;
+  float4* const line = reinterpret_cast<float4*>(csm + warp * kCWarpSmemBytes);
+  int* const stage = reinterpret_cast<int*>(line + kCLineUnits);
+  const int swz = bswz(p);
+  unsigned zz[2] = {0u, 0u};
+  if (kZigzag) {
+    zz[0] = zz_pack4(4 * lane);
+    zz[1] = zz_pack4(128 + 4 * lane);
+  }
+  const int wc[2] = {w_of(2 * j), w_of(2 * j + 1)};
+  constexpr int kElem = kDtype == 0 ? 1 : 2;
+  const int tiles_x = (w + kTileW - 1) / kTileW;
+  const int ntiles = tiles_x * (h >> 4);
+  const int bpr = w >> 4;
+  for (int t = blockIdx.x * kCWarps + warp; t < ntiles; t += gridDim.x * kCWarps) {
+    const int ty = t / tiles_x, tx = t - ty * tiles_x;
+    const int nb = min(8, (w - tx * kTileW) >> 4);
+    const bool va = p < nb, vb = p + 4 < nb;
+    // ---- the tile's coefficients (8 KB) into the block stage
+    const int32_t* const in = coef + ((long long)ty * bpr + tx * 8) * 256;
+    uint4 v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+      v[m] = (m >> 1) < nb ? ldg_stream(in + 256 * (m >> 1) + 4 * (32 * (m & 1) + lane)) : make_uint4(0u, 0u, 0u, 0u);
+    unsigned big = 0u;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int b = m >> 1, hh = m & 1, bs = bswz(b);
+      big |= ((unsigned)((int)v[m].x ^ ((int)v[m].x >> 31))) | ((unsigned)((int)v[m].y ^ ((int)v[m].y >> 31))) |
+             ((unsigned)((int)v[m].z ^ ((int)v[m].z >> 31))) | ((unsigned)((int)v[m].w ^ ((int)v[m].w >> 31)));
+      int* const sb = stage + 256 * b;
+      if (!kZigzag) {
+        const uint4 x = (b & 1) ? make_uint4(v[m].y, v[m].x, v[m].w, v[m].z) : v[m];
+        reinterpret_cast<uint4*>(sb)[(32 * hh + lane) ^ (bs >> 2)] = x;
+      } else {
+        sb[zz_byte(zz[hh], 0) ^ bs] = (int)v[m].x;
+        sb[zz_byte(zz[hh], 1) ^ bs] = (int)v[m].y;
+        sb[zz_byte(zz[hh], 2) ^ bs] = (int)v[m].z;
+        sb[zz_byte(zz[hh], 3) ^ bs] = (int)v[m].w;
+      }
+    }
+    const bool wide = __any_sync(0xffffffffu, big >= (1u << 18));
+    __syncwarp();
+    uint8_t* const drow = dst + (long long)(ty * kTileH + 2 * j) * pitch + (long long)(tx * kTileW + 16 * p) * kElem;
+    if (!wide) {
+      // ---- column pass (int32): U(:, c) = T^T (W_u W_c Y(:, c))
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int c = 2 * j + i;
+        int da[16], db[16], ua[16], ub[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int wd = (16 * u + c) ^ swz, f = w_of(u) * wc[i];
+          da[u] = stage[256 * p + wd] * f;
+          db[u] = stage[256 * (p + 4) + wd] * f;
+        }
+        inv16(da, ua);
+        inv16(db, ub);
+        float4* const ln = line + 138 * p + 17 * j + 8 * i;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          ln[q] = make_float4(__int_as_float(ua[2 * q]), __int_as_float(ub[2 * q]), __int_as_float(ua[2 * q + 1]),
+                              __int_as_float(ub[2 * q + 1]));
+      }
+      __syncwarp();
+      // ---- row pass (int32) on rows 2j + rr, round, store
+#pragma unroll
+      for (int tr = 0; tr < 2; ++tr) {
+        const int rr = tr ^ jb1;
+        const float2* const fin = reinterpret_cast<const float2*>(line + 138 * p + j) + rr;
+        int ra[16], rb[16], za[16], zb[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float2 x = fin[2 * (8 * c + (c >> 1))];
+          ra[c] = __float_as_int(x.x);
+          rb[c] = __float_as_int(x.y);
+        }
+        inv16(ra, za);
+        inv16(rb, zb);
+        int qa[16], qb[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) round_pair<kDtype>(za[n], zb[n], qa[n], qb[n]);
+        store_row<kDtype>(drow + rr * pitch, va, vb, qa, qb);
+      }
+    } else {
+      // ---- split path: high halves through the line buffer, low halves
+      // through the lane's own words of the block stage
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int c = 2 * j + i;
+        int ha[16], hb[16], la[16], lb[16], ua[16], ub[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int wd = (16 * u + c) ^ swz, f = w_of(u) * wc[i];
+          const int ya = stage[256 * p + wd], yb = stage[256 * (p + 4) + wd];
+          ha[u] = (ya >> 16) * f;
+          hb[u] = (yb >> 16) * f;
+          la[u] = (ya & 0xffff) * f;
+          lb[u] = (yb & 0xffff) * f;
+        }
+        inv16(ha, ua);
+        inv16(hb, ub);
+        float4* const ln = line + 138 * p + 17 * j + 8 * i;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          ln[q] = make_float4(__int_as_float(ua[2 * q]), __int_as_float(ub[2 * q]), __int_as_float(ua[2 * q + 1]),
+                              __int_as_float(ub[2 * q + 1]));
+        inv16(la, ua);
+        inv16(lb, ub);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const int wd = (16 * m + c) ^ swz;
+          stage[256 * p + wd] = ua[m];
+          stage[256 * (p + 4) + wd] = ub[m];
+        }
+      }
+      __syncwarp();
+#pragma unroll 1
+      for (int rr = 0; rr < 2; ++rr) {
+        const int m = 2 * j + rr;
+        const float2* const fin = reinterpret_cast<const float2*>(line + 138 * p + j) + rr;
+        int ra[16], rb[16], zha[16], zhb[16], zla[16], zlb[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float2 x = fin[2 * (8 * c + (c >> 1))];
+          ra[c] = __float_as_int(x.x);
+          rb[c] = __float_as_int(x.y);
+        }
+        inv16(ra, zha);
+        inv16(rb, zhb);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int wd = (16 * m + c) ^ swz;
+          ra[c] = stage[256 * p + wd];
+          rb[c] = stage[256 * (p + 4) + wd];
+        }
+        inv16(ra, zla);
+        inv16(rb, zlb);
+        int qa[16], qb[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) {
+          qa[n] = round_clamp<kDtype, 2304u>((long long)zha[n] * 65536 + zla[n]);
+          qb[n] = round_clamp<kDtype, 2304u>((long long)zhb[n] * 65536 + zlb[n]);
+        }
+        store_row<kDtype>(drow + rr * pitch, va, vb, qa, qb);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 1-D transforms over contiguous 16-sample vectors, one vector per lane,
+// 32 vectors per warp step; the 64-byte coefficient vectors pass through a
+// per-warp shared buffer so that global accesses are 512-byte runs.  Chunk k
+// of vector r sits at 4 r + (k ^ ((r >> 1) & 3)) (conflict-free both ways).
+// ---------------------------------------------------------------------------
+constexpr int k1dWarps = 8;
+
+__device__ __forceinline__ int chunk_1d(int r, int k) { return 4 * r + (k ^ ((r >> 1) & 3)); }
+
+template <int kDtype>
+__global__ void __launch_bounds__(32 * k1dWarps)
+fwd1d_kernel(const uint8_t* __restrict__ src, long long count, int32_t* __restrict__ out) {
+  __shared__ uint4 buf[k1dWarps][128];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint4* const sb = buf[warp];
+  const long long steps = (count + 31) / 32;
+  for (long long g = (long long)blockIdx.x * k1dWarps + warp; g < steps; g += (long long)gridDim.x * k1dWarps) {
+    const long long vec = 32 * g + lane;
+    const int nvalid = (int)min(32LL, count - 32 * g);
+    int x[16], y[16];
+    if (kDtype == 0) {
+      const uint4 a = vec < count ? ldg_stream(src + 16 * vec) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int n = 0; n < 16; ++n) x[n] = (int)((word_at(a, n >> 2) >> (8 * (n & 3))) & 0xffu);
+    } else {
+      uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a;
+      if (vec < count) {
+        a = ldg_stream(src + 32 * vec);
+        b = ldg_stream(src + 32 * vec + 16);
+      }
+#pragma unroll
+      for (int n = 0; n < 16; ++n) {
+        const unsigned wd = word_at(n < 8 ? a : b, (n & 7) >> 1);
+        x[n] = (n & 1) ? ((int)wd >> 16) : (int)(short)(wd & 0xffffu);
+      }
+    }
+    fwd16(x, y);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      sb[chunk_1d(lane, k)] = make_uint4((unsigned)y[4 * k], (unsigned)y[4 * k + 1], (unsigned)y[4 * k + 2],
+                                         (unsigned)y[4 * k + 3]);
+    __syncwarp();
+    int32_t* const o = out + 32 * 16 * g;
+#pragma unroll
+    for (int hh = 0; hh < 4; ++hh) {
+      const int q = 32 * hh + lane;
+      if (q < 4 * nvalid) stg_stream(o + 4 * q, sb[chunk_1d(q >> 2, q & 3)]);
+    }
+    __syncwarp();
+  }
+}
+
+// x_hat = T^T (W y) / 48 (C_hat^T C_hat = T^T S^2 T with S^2 = W / 48).  The
+// numerator sum_u T_un W_u y_u fits int32 when every |y_u| < 2^24, as
+// sum_u W_u = 68 and 68 * 2^24 < 2^31; a lane holding a larger coefficient
+// takes the 64-bit route.
+template <int kDtype>
+__global__ void __launch_bounds__(32 * k1dWarps)
+inv1d_kernel(const int32_t* __restrict__ coef, long long count, uint8_t* __restrict__ dst) {
+  __shared__ uint4 buf[k1dWarps][128];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint4* const sb = buf[warp];
+  const long long steps = (count + 31) / 32;
+  for (long long g = (long long)blockIdx.x * k1dWarps + warp; g < steps; g += (long long)gridDim.x * k1dWarps) {
+    const long long vec = 32 * g + lane;
+    const int nvalid = (int)min(32LL, count - 32 * g);
+    const int32_t* const in = coef + 32 * 16 * g;
+#pragma unroll
+    for (int hh = 0; hh < 4; ++hh) {
+      const int q = 32 * hh + lane;
+      sb[chunk_1d(q >> 2, q & 3)] = q < 4 * nvalid ? ldg_stream(in + 4 * q) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncwarp();
+    int y[16];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint4 c = sb[chunk_1d(lane, k)];
+      y[4 * k] = (int)c.x;
+      y[4 * k + 1] = (int)c.y;
+      y[4 * k + 2] = (int)c.z;
+      y[4 * k + 3] = (int)c.w;
+    }
+    __syncwarp();
+    unsigned big = 0u;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) big |= (unsigned)(y[u] ^ (y[u] >> 31));
+    int q[16];
+    if (big < (1u << 24)) {
+      int d[16], z[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) d[u] = y[u] * w_of(u);
+      inv16(d, z);
+#pragma unroll
+      for (int n = 0; n < 16; ++n) q[n] = round_clamp<kDtype, 48u>(z[n]);
+    } else {
+      long long d[16], z[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) d[u] = (long long)y[u] * w_of(u);
+      inv16(d, z);
+#pragma unroll
+      for (int n = 0; n < 16; ++n) q[n] = round_clamp<kDtype, 48u>(z[n]);
+    }
+    if (vec < count) {
+      if (kDtype == 0) {
+        unsigned o[4];
+#pragma unroll
+        for (int g4 = 0; g4 < 4; ++g4)
+          o[g4] = (unsigned)q[4 * g4] | ((unsigned)q[4 * g4 + 1] << 8) | ((unsigned)q[4 * g4 + 2] << 16) |
+                  ((unsigned)q[4 * g4 + 3] << 24);
+        stg_stream(dst + 16 * vec, make_uint4(o[0], o[1], o[2], o[3]));
+      } else {
+        unsigned o[8];
+#pragma unroll
+        for (int g2 = 0; g2 < 8; ++g2) o[g2] = ((unsigned)q[2 * g2] & 0xffffu) | ((unsigned)q[2 * g2 + 1] << 16);
+        stg_stream(dst + 32 * vec, make_uint4(o[0], o[1], o[2], o[3]));
+        stg_stream(dst + 32 * vec + 16, make_uint4(o[4], o[5], o[6], o[7]));
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_forward(int dtype, const void* d_src, long long pitch, int w, int h, int32_t* d_coef,
+                           bool zigzag, int num_sms, cudaStream_t stream) {
+  const long long ntiles = (long long)((w + kTileW - 1) / kTileW) * (h >> 4);
+  if (ntiles <= 0) return cudaSuccess;
+  if (ntiles >= (1LL << 31) - 4096) return cudaErrorInvalidValue;  // tile indices are 32-bit in the kernel
+  const int smem = kCWarps * kCWarpSmemBytes, threads = 32 * kCWarps;
+  const uint8_t* s = static_cast<const uint8_t*>(d_src);
+#define ATDCT16_FWD(D, Z)                                                                                \
+  return launch_dyn(coef_forward_kernel<D, Z>,                                                           \
+                    persistent_grid(coef_forward_kernel<D, Z>, threads, smem, num_sms, kCWarps, ntiles), \
+                    threads, smem, stream, s, pitch, w, h, d_coef)
+  if (dtype == 0) {
+    if (zigzag) ATDCT16_FWD(0, true);
+    ATDCT16_FWD(0, false);
+  }
+  if (zigzag) ATDCT16_FWD(1, true);
+  ATDCT16_FWD(1, false);
+#undef ATDCT16_FWD
+}
+
+cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void* d_dst, long long pitch,
+                           bool zigzag, int num_sms, cudaStream_t stream) {
+  const long long ntiles = (long long)((w + kTileW - 1) / kTileW) * (h >> 4);
+  if (ntiles <= 0) return cudaSuccess;
+  if (ntiles >= (1LL << 31) - 4096) return cudaErrorInvalidValue;
+  const int smem = kCWarps * kCWarpSmemBytes, threads = 32 * kCWarps;
+  uint8_t* d = static_cast<uint8_t*>(d_dst);
+#define ATDCT16_INV(D, Z)                                                                                \
+  return launch_dyn(coef_inverse_kernel<D, Z>,                                                           \
+                    persistent_grid(coef_inverse_kernel<D, Z>, threads, smem, num_sms, kCWarps, ntiles), \
+                    threads, smem, stream, d_coef, w, h, d, pitch)
+  if (dtype == 0) {
+    if (zigzag) ATDCT16_INV(0, true);
+    ATDCT16_INV(0, false);
+  }
+  if (zigzag) ATDCT16_INV(1, true);
+  ATDCT16_INV(1, false);
+#undef ATDCT16_INV
+}
+
+cudaError_t launch_forward_1d(int dtype, const void* d_src, long long count, int32_t* d_coef, int num_sms,
+                              cudaStream_t stream) {
+  if (count <= 0) return cudaSuccess;
+  const long long steps = (count + 31) / 32;
+  const uint8_t* s = static_cast<const uint8_t*>(d_src);
+  if (dtype == 0)
+    return launch_dyn(fwd1d_kernel<0>, persistent_grid(fwd1d_kernel<0>, 32 * k1dWarps, 0, num_sms, k1dWarps, steps),
+                      32 * k1dWarps, 0, stream, s, count, d_coef);
+  return launch_dyn(fwd1d_kernel<1>, persistent_grid(fwd1d_kernel<1>, 32 * k1dWarps, 0, num_sms, k1dWarps, steps),
+                    32 * k1dWarps, 0, stream, s, count, d_coef);
+}
+
+cudaError_t launch_inverse_1d(int dtype, const int32_t* d_coef, long long count, void* d_dst, int num_sms,
+                              cudaStream_t stream) {
+  if (count <= 0) return cudaSuccess;
+  const long long steps = (count + 31) / 32;
+  uint8_t* d = static_cast<uint8_t*>(d_dst);
+  if (dtype == 0)
+    return launch_dyn(inv1d_kernel<0>, persistent_grid(inv1d_kernel<0>, 32 * k1dWarps, 0, num_sms, k1dWarps, steps),
+                      32 * k1dWarps, 0, stream, d_coef, count, d);
+  return launch_dyn(inv1d_kernel<1>, persistent_grid(inv1d_kernel<1>, 32 * k1dWarps, 0, num_sms, k1dWarps, steps),
+                    32 * k1dWarps, 0, stream, d_coef, count, d);
+}
+
+}  // namespace atdct16

@@ -10,8 +10,6 @@ namespace atdct16 {
 // processes one tile at a time; the last tile of a row may hold fewer blocks.
 constexpr int kTileW = 128;
 constexpr int kTileH = 16;
-constexpr int kWarpsPerCta = 8;
-constexpr int kThreadsPerCta = 32 * kWarpsPerCta;
 constexpr int kZonalWarps = 4;  // warps per CTA of the fused zonal and quantisation kernels
 
 // One image of a batch, as the kernels see it (64 bytes).
@@ -59,8 +57,10 @@ int zonal_config_max_ctas_per_sm(const ZonalConfig& c);
 cudaError_t launch_zonal_config(const ZonalConfig& cfg, const ImageJob* d_jobs, int njobs, long long ntiles,
                                 const float2* d_wtab, float* d_tile_sse, int* d_status, int grid,
                                 cudaStream_t stream);
+// d_levels (optional, 16-byte aligned): int16 levels per block, row-major
+// in (u, v) or, with zigzag, in zig-zag order.
 cudaError_t launch_quant(const ImageJob* d_jobs, int njobs, long long ntiles, const float4* d_qtab,
-                         int16_t* d_levels, float* d_tile_sse, int* d_status, int grid,
+                         int16_t* d_levels, bool zigzag, float* d_tile_sse, int* d_status, int grid,
                          cudaStream_t stream);
 cudaError_t launch_psnr_finalize(const ImageJob* d_jobs, int njobs, long long ntiles,
                                  const float* d_tile_sse, double peak, double* d_psnr,
@@ -72,10 +72,17 @@ cudaError_t launch_zonal_dct(const ImageJob* d_jobs, int njobs, long long ntiles
 constexpr int kSsimTileRows = 16, kSsimTileCols = 64;
 cudaError_t launch_ssim(const ImageJob* d_jobs, int njobs, long long ntiles, float* d_tile_sum, double* d_out,
                         int* d_status, int num_sms, cudaStream_t stream);
-cudaError_t launch_forward(int dtype, const void* d_src, long long pitch, int w, int h,
-                           int32_t* d_coef, cudaStream_t stream);
-cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void* d_dst,
-                           long long pitch, cudaStream_t stream);
+// Coefficient pipeline (atdct16_coef.cu): 2-D forward / exact inverse over
+// 16x16 blocks (coefficients row-major in (u, v) or in zig-zag order) and
+// 1-D forward / exact inverse over 16-sample vectors.
+cudaError_t launch_forward(int dtype, const void* d_src, long long pitch, int w, int h, int32_t* d_coef,
+                           bool zigzag, int num_sms, cudaStream_t stream);
+cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void* d_dst, long long pitch,
+                           bool zigzag, int num_sms, cudaStream_t stream);
+cudaError_t launch_forward_1d(int dtype, const void* d_src, long long count, int32_t* d_coef, int num_sms,
+                              cudaStream_t stream);
+cudaError_t launch_inverse_1d(int dtype, const int32_t* d_coef, long long count, void* d_dst, int num_sms,
+                              cudaStream_t stream);
 cudaError_t launch_psnr_pair(int dtype, const void* d_a, long long pitch_a, const void* d_b,
                              long long pitch_b, int w, int h, double* d_out, cudaStream_t stream);
 int zonal_ctas_per_sm();

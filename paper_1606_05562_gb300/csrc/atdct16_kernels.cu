@@ -41,11 +41,6 @@ __device__ __forceinline__ unsigned word_of(const uint4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
-// 2^23 + 256 * (byte k of w): exact float built by one byte permute.
-__device__ __forceinline__ float u8_scaled(unsigned w, int k) {
-  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7404u | ((unsigned)k << 4)));
-}
-
 // SwarRow word (fields f_lo, f_hi, each value + 4096 < 2^13) -> the exact
 // floats 2^23 + 256 f = 2^23 + 2^20 + 256 value, one byte permute each.
 __device__ __forceinline__ float2 swar_row_f2(unsigned w) {
@@ -98,54 +93,6 @@ __device__ __forceinline__ void warp_find_job(const ImageJob* __restrict__ jobs,
 
 __device__ __forceinline__ void set_status(int* status, int code) {
   atomicCAS(status, kDevOk, code);
-}
-
-// Warp-private transpose buffer: 4 block pairs x 16 lines x 8 chunks of 16 B.
-struct alignas(16) WarpBuf {
-  float4 c[4 * 16 * 8];
-};
-
-// Row-stage values (rows 2j, 2j+1, all 16 positions) -> column-stage values
-// (columns 2j, 2j+1, all 16 positions).  Chunk (line, q) holds two float2
-// entries of one line; the chunk slot is XOR-swizzled by (line >> 1) & 7.
-__device__ __forceinline__ void transpose_rows_to_cols(float4* buf, int p, int j,
-                                                       const float2 (&r0)[16], const float2 (&r1)[16],
-                                                       float2 (&c0)[16], float2 (&c1)[16]) {
-#pragma unroll
-  for (int k = 0; k < 16; ++k)
-    buf[(p * 16 + k) * 8 + (j ^ ((k >> 1) & 7))] = make_float4(r0[k].x, r0[k].y, r1[k].x, r1[k].y);
-  __syncwarp();
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const float4 v0 = buf[(p * 16 + 2 * j) * 8 + (q ^ j)];
-    const float4 v1 = buf[(p * 16 + 2 * j + 1) * 8 + (q ^ j)];
-    c0[2 * q] = make_float2(v0.x, v0.y);
-    c0[2 * q + 1] = make_float2(v0.z, v0.w);
-    c1[2 * q] = make_float2(v1.x, v1.y);
-    c1[2 * q + 1] = make_float2(v1.z, v1.w);
-  }
-  __syncwarp();
-}
-
-// Column-stage values (columns 2j, 2j+1 over all rows m) -> row-stage values
-// (rows 2j, 2j+1 over all columns).
-__device__ __forceinline__ void transpose_cols_to_rows(float4* buf, int p, int j,
-                                                       const float2 (&u0)[16], const float2 (&u1)[16],
-                                                       float2 (&v0)[16], float2 (&v1)[16]) {
-#pragma unroll
-  for (int m = 0; m < 16; ++m)
-    buf[(p * 16 + m) * 8 + (j ^ ((m >> 1) & 7))] = make_float4(u0[m].x, u0[m].y, u1[m].x, u1[m].y);
-  __syncwarp();
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const float4 a = buf[(p * 16 + 2 * j) * 8 + (q ^ j)];
-    const float4 b = buf[(p * 16 + 2 * j + 1) * 8 + (q ^ j)];
-    v0[2 * q] = make_float2(a.x, a.y);
-    v0[2 * q + 1] = make_float2(a.z, a.w);
-    v1[2 * q] = make_float2(b.x, b.y);
-    v1[2 * q + 1] = make_float2(b.z, b.w);
-  }
-  __syncwarp();
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -894,8 +841,6 @@ zonal_mma_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
 constexpr int kQStageUnits = 2 * 8 * 32;  // two tiles of input rows, 8 x 16 bytes per lane
 constexpr int kQuantWarpSmemBytes = 16 * (kZT2Units + kQStageUnits);
 
-__device__ __forceinline__ float i16_lo(unsigned w) { return (float)(short)(w & 0xffffu); }
-__device__ __forceinline__ float i16_hi(unsigned w) { return (float)(short)(w >> 16); }
 // int16 field of a word -> 2^23 + 32768 + v as an exact float (offset binary
 // placed in the mantissa): one logic op (low field) or a permute plus a logic
 // op (high field), on the integer pipe.
@@ -937,7 +882,27 @@ struct QuantTile {
   long long lvl;       // level index of (u, v) = (0, 0) of block p of this tile
 };
 
-template <bool kLevels>
+// Levels leave through the input staging slot of the current tile (free
+// once its rows are in registers): the column pass writes the tile's 8 x 256
+// int16 levels there, row-major in (u, v) with halfword (16 u + v) of block b
+// at (16 u + v) ^ (16 (b & 3)) (conflict-free for the per-column writes),
+// and the warp stores each block as one 512-byte run, gathered in zig-zag
+// order (Sec. 4 scan) when kZigzag.  The copy of the tile after next into
+// that slot starts after the levels have left.
+__device__ int zz_word16(int k) {  // (16 u + v) of zig-zag scan position k
+  int s = 0, base = 0;
+  while (s < 30) {
+    const int len = s < 16 ? s + 1 : 31 - s;
+    if (k < base + len) break;
+    base += len;
+    ++s;
+  }
+  const int off = k - base, hi = s < 16 ? s : 15;
+  const int a = hi - off, b = s - a;  // even s: u = a (decreasing); odd s: v = a (decreasing)
+  return (s & 1) ? 16 * b + a : 16 * a + b;
+}
+
+template <bool kLevels, bool kZigzag>
 __global__ void __launch_bounds__(128, 3)
 quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
              const float4* __restrict__ qtab, int16_t* __restrict__ levels, float* __restrict__ tile_sse,
@@ -1050,6 +1015,12 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
   int wq = -1;
   float kq[2][3], gq[2][3], qstep = 1.f;
   int st = 0;
+  // zig-zag scan positions 8 lane .. 8 lane + 7, one byte each
+  unsigned zzl[2] = {0u, 0u};
+  if (kLevels && kZigzag) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) zzl[e >> 2] |= (unsigned)zz_word16(8 * lane + e) << (8 * (e & 3));
+  }
   while (true) {
     cp_async_wait<1>();
     if (cur.qp != wq) {
@@ -1094,10 +1065,12 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
     if (have_fut) {
       take(fut);
       ok = advance();
-      issue(fut, st);
-    } else {
-      cp_async_commit();
     }
+    if (!kLevels) {
+      if (have_fut) issue(fut, st);
+      else cp_async_commit();
+    }
+    int16_t* const lvs = reinterpret_cast<int16_t*>(reinterpret_cast<uint4*>(tb + kZT2Units) + 256 * st);
 
     // ---- per column c = 2j + i: column pass (exact Y), quantise, error
     // energy, dequantise, inverse column pass, back into the same line
@@ -1128,8 +1101,9 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
         sacc = __ffma2_rn(e, e, sacc);
         if (kLevels) {
           const int la = (int)(__float_as_uint(f.x) - 0x4B000000u), lb = (int)(__float_as_uint(f.y) - 0x4B000000u);
-          if (va) levels[cur.lvl + u * 16 + c] = (int16_t)(y[u].x < 0.f ? -la : la);
-          if (vb) levels[cur.lvl + 4 * 256 + u * 16 + c] = (int16_t)(y[u].y < 0.f ? -lb : lb);
+          const int hw = (16 * u + c) ^ (16 * p);
+          lvs[256 * p + hw] = (int16_t)(y[u].x < 0.f ? -la : la);
+          lvs[256 * (p + 4) + hw] = (int16_t)(y[u].y < 0.f ? -lb : lb);
         }
         y[u] = f2copysign(__fmul2_rn(L, make_float2(g, g)), y[u]);
       }
@@ -1139,6 +1113,29 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
       for (int q = 0; q < 8; ++q) line[q] = make_float4(uo[2 * q].x, uo[2 * q].y, uo[2 * q + 1].x, uo[2 * q + 1].y);
     }
     __syncwarp();
+    if (kLevels) {
+      // the tile's levels, one 512-byte run per block, then refill the slot
+      int16_t* const gl = levels + (cur.lvl - 256 * p);
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        if (b >= cur.nb) break;
+        uint4 v;
+        if (!kZigzag) {
+          v = reinterpret_cast<const uint4*>(lvs + 256 * b)[lane ^ (2 * (b & 3))];
+        } else {
+          const int16_t* const lb = lvs + 256 * b;
+          unsigned hw[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            hw[e] = (unsigned short)lb[((zzl[e >> 2] >> (8 * (e & 3))) & 0xffu) ^ (16 * (b & 3))];
+          v = make_uint4(hw[0] | (hw[1] << 16), hw[2] | (hw[3] << 16), hw[4] | (hw[5] << 16), hw[6] | (hw[7] << 16));
+        }
+        __stcs(reinterpret_cast<uint4*>(gl + 256 * b + 8 * lane), v);
+      }
+      __syncwarp();
+      if (have_fut) issue(fut, st);
+      else cp_async_commit();
+    }
 
     // ---- per row 2j + rr: gather (8-byte halves, conflict-free with the
     // row-order swap of the zonal kernel), inverse row pass, rint, pack, store
@@ -1576,134 +1573,6 @@ __global__ void psnr_finalize_kernel(const ImageJob* __restrict__ jobs, int njob
 }
 
 // --------------------------------------------------------------------------
-// Forward transform to exact int32 coefficients (block-major, (u, v) row-major).
-// --------------------------------------------------------------------------
-template <int kDtype>  // 0: u8, 1: i16
-__global__ void __launch_bounds__(kThreadsPerCta)
-forward_kernel(const uint8_t* __restrict__ src, long long pitch, int w, int h, int32_t* __restrict__ coef) {
-  __shared__ WarpBuf sbuf[kWarpsPerCta];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int p = lane >> 3, j = lane & 7;
-  float4* buf = sbuf[warp].c;
-  const int tiles_x = (w + kTileW - 1) / kTileW;
-  const long long t = (long long)blockIdx.x * kWarpsPerCta + warp;
-  if (t >= (long long)tiles_x * (h >> 4)) return;
-  const int ty = (int)(t / tiles_x), tx = (int)(t - (long long)ty * tiles_x);
-  const int x0 = tx * kTileW, y0 = ty * kTileH;
-  const int nb = min(8, (w - x0) >> 4);
-  const bool va = p < nb, vb = p + 4 < nb;
-  float2 x0v[16], x1v[16], r0[16], r1[16];
-  if (kDtype == 0) {
-    const uint8_t* s = src + (long long)(y0 + 2 * j) * pitch + x0 + 16 * p;
-    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
-    if (va) { a0 = *reinterpret_cast<const uint4*>(s); a1 = *reinterpret_cast<const uint4*>(s + pitch); }
-    if (vb) { b0 = *reinterpret_cast<const uint4*>(s + 64); b1 = *reinterpret_cast<const uint4*>(s + 64 + pitch); }
-#pragma unroll
-    for (int n = 0; n < 16; ++n) {
-      x0v[n] = make_float2(u8_scaled(word_of(a0, n >> 2), n & 3), u8_scaled(word_of(b0, n >> 2), n & 3));
-      x1v[n] = make_float2(u8_scaled(word_of(a1, n >> 2), n & 3), u8_scaled(word_of(b1, n >> 2), n & 3));
-    }
-  } else {
-    const uint8_t* s = src + (long long)(y0 + 2 * j) * pitch + 2 * (x0 + 16 * p);
-    uint4 a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = b[i] = make_uint4(0, 0, 0, 0);
-    if (va) {
-      a[0] = *reinterpret_cast<const uint4*>(s); a[1] = *reinterpret_cast<const uint4*>(s + 16);
-      a[2] = *reinterpret_cast<const uint4*>(s + pitch); a[3] = *reinterpret_cast<const uint4*>(s + pitch + 16);
-    }
-    if (vb) {
-      b[0] = *reinterpret_cast<const uint4*>(s + 128); b[1] = *reinterpret_cast<const uint4*>(s + 144);
-      b[2] = *reinterpret_cast<const uint4*>(s + pitch + 128); b[3] = *reinterpret_cast<const uint4*>(s + pitch + 144);
-    }
-#pragma unroll
-    for (int n = 0; n < 16; ++n) {
-      const int wi = (n >> 1) & 3, hi = n & 1, part = n >> 3;
-      const unsigned wa0 = word_of(a[part], wi), wb0 = word_of(b[part], wi);
-      const unsigned wa1 = word_of(a[2 + part], wi), wb1 = word_of(b[2 + part], wi);
-      x0v[n] = make_float2(hi ? i16_hi(wa0) : i16_lo(wa0), hi ? i16_hi(wb0) : i16_lo(wb0));
-      x1v[n] = make_float2(hi ? i16_hi(wa1) : i16_lo(wa1), hi ? i16_hi(wb1) : i16_lo(wb1));
-    }
-  }
-  fwd16(x0v, r0);
-  fwd16(x1v, r1);
-  if (kDtype == 0) {
-    r0[0] = bsub(r0[0], make_float2(134217728.0f, 134217728.0f));
-    r1[0] = bsub(r1[0], make_float2(134217728.0f, 134217728.0f));
-  }
-  float2 c0[16], c1[16], y0v[16], y1v[16];
-  transpose_rows_to_cols(buf, p, j, r0, r1, c0, c1);
-  fwd16(c0, y0v);
-  fwd16(c1, y1v);
-  const float sc = kDtype == 0 ? (1.0f / 256.0f) : 1.0f;
-  const int bpr = w >> 4;
-  const long long blk = (long long)(y0 >> 4) * bpr + (x0 >> 4) + p;
-#pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    if (va)
-      *reinterpret_cast<int2*>(coef + blk * 256 + u * 16 + 2 * j) =
-          make_int2(__float2int_rn(y0v[u].x * sc), __float2int_rn(y1v[u].x * sc));
-    if (vb)
-      *reinterpret_cast<int2*>(coef + (blk + 4) * 256 + u * 16 + 2 * j) =
-          make_int2(__float2int_rn(y0v[u].y * sc), __float2int_rn(y1v[u].y * sc));
-  }
-}
-
-// --------------------------------------------------------------------------
-// Exact inverse in 64-bit integers: Z = T^T (W Y W) T, X_hat = Z / 2304,
-// round half to even, clamp.  16 threads per block, 16 blocks per CTA.
-// --------------------------------------------------------------------------
-__device__ __forceinline__ long long rne_div(long long z, long long d) {
-  // floor((z + d/2) / d), then ties (remainder 0 after the shift) to even
-  const long long n = z + d / 2;
-  long long q = n >= 0 ? n / d : -((-n + d - 1) / d);
-  if (n - q * d == 0 && (q & 1)) q -= 1;
-  return q;
-}
-
-template <int kDtype>
-__global__ void __launch_bounds__(256)
-inverse_exact_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __restrict__ dst, long long pitch) {
-  __shared__ long long su[16][16][17];
-  // W = 48 S^2 from the printed S of Sec. 2: S^2 = 1/16, 1/12 or 1/8.
-  const int Wd[16] = {3, 3, 4, 6, 6, 3, 4, 4, 3, 4, 4, 6, 6, 4, 4, 4};
-  const int bl = threadIdx.x >> 4, t = threadIdx.x & 15;
-  const int bpr = w >> 4;
-  const long long nblk = (long long)bpr * (h >> 4);
-  const long long b = (long long)blockIdx.x * 16 + bl;
-  const bool valid = b < nblk;
-  long long d[16], u[16];
-#pragma unroll
-  for (int k = 0; k < 16; ++k)
-    d[k] = valid ? (long long)Wd[k] * Wd[t] * (long long)coef[b * 256 + k * 16 + t] : 0;
-  inv16(d, u);  // column t: U[m][t]
-#pragma unroll
-  for (int m = 0; m < 16; ++m) su[bl][m][t] = u[m];
-  __syncthreads();
-  long long v[16], z[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) v[c] = su[bl][t][c];
-  inv16(v, z);  // row t: Z[t][n]
-  if (!valid) return;
-  const long long by = b / bpr, bx = b - by * bpr;
-  uint8_t* o = dst + (by * 16 + t) * pitch;
-  if (kDtype == 0) {
-#pragma unroll
-    for (int n = 0; n < 16; ++n) {
-      const long long q = rne_div(z[n], 2304);
-      o[bx * 16 + n] = (uint8_t)(q < 0 ? 0 : (q > 255 ? 255 : q));
-    }
-  } else {
-    int16_t* o16 = reinterpret_cast<int16_t*>(o);
-#pragma unroll
-    for (int n = 0; n < 16; ++n) {
-      const long long q = rne_div(z[n], 2304);
-      o16[bx * 16 + n] = (int16_t)(q < -32768 ? -32768 : (q > 32767 ? 32767 : q));
-    }
-  }
-}
-
-// --------------------------------------------------------------------------
 // PSNR of two images, exact integer SSE accumulated in the output slot.
 // --------------------------------------------------------------------------
 template <int kDtype>
@@ -1799,15 +1668,18 @@ cudaError_t launch_zonal(const ImageJob* d_jobs, int njobs, long long ntiles, co
 }
 
 cudaError_t launch_quant(const ImageJob* d_jobs, int njobs, long long ntiles, const float4* d_qtab,
-                         int16_t* d_levels, float* d_tile_sse, int* d_status, int grid,
+                         int16_t* d_levels, bool zigzag, float* d_tile_sse, int* d_status, int grid,
                          cudaStream_t stream) {
   if (ntiles <= 0) return cudaSuccess;
   if (ntiles >= (1LL << 30)) return cudaErrorInvalidValue;  // tile indices are 32-bit in the kernel
+  if (d_levels && zigzag)
+    return launch_with_smem(quant_kernel<true, true>, grid, 128, 4 * kQuantWarpSmemBytes, stream, d_jobs, njobs,
+                            ntiles, d_qtab, d_levels, d_tile_sse, d_status);
   if (d_levels)
-    return launch_with_smem(quant_kernel<true>, grid, 128, 4 * kQuantWarpSmemBytes, stream, d_jobs, njobs, ntiles,
-                            d_qtab, d_levels, d_tile_sse, d_status);
-  return launch_with_smem(quant_kernel<false>, grid, 128, 4 * kQuantWarpSmemBytes, stream, d_jobs, njobs, ntiles,
-                          d_qtab, d_levels, d_tile_sse, d_status);
+    return launch_with_smem(quant_kernel<true, false>, grid, 128, 4 * kQuantWarpSmemBytes, stream, d_jobs, njobs,
+                            ntiles, d_qtab, d_levels, d_tile_sse, d_status);
+  return launch_with_smem(quant_kernel<false, false>, grid, 128, 4 * kQuantWarpSmemBytes, stream, d_jobs, njobs,
+                          ntiles, d_qtab, d_levels, d_tile_sse, d_status);
 }
 
 cudaError_t launch_psnr_finalize(const ImageJob* d_jobs, int njobs, long long ntiles, const float* d_tile_sse,
@@ -1825,28 +1697,6 @@ cudaError_t launch_psnr_finalize(const ImageJob* d_jobs, int njobs, long long nt
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, psnr_finalize_kernel, d_jobs, njobs, ntiles, d_tile_sse, peak, d_psnr, d_sse);
-}
-
-cudaError_t launch_forward(int dtype, const void* d_src, long long pitch, int w, int h, int32_t* d_coef,
-                           cudaStream_t stream) {
-  const long long tiles = (long long)((w + kTileW - 1) / kTileW) * (h >> 4);
-  const int grid = (int)((tiles + kWarpsPerCta - 1) / kWarpsPerCta);
-  if (dtype == 0)
-    forward_kernel<0><<<grid, kThreadsPerCta, 0, stream>>>((const uint8_t*)d_src, pitch, w, h, d_coef);
-  else
-    forward_kernel<1><<<grid, kThreadsPerCta, 0, stream>>>((const uint8_t*)d_src, pitch, w, h, d_coef);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void* d_dst, long long pitch,
-                           cudaStream_t stream) {
-  const long long nblk = (long long)(w >> 4) * (h >> 4);
-  const int grid = (int)((nblk + 15) / 16);
-  if (dtype == 0)
-    inverse_exact_kernel<0><<<grid, 256, 0, stream>>>(d_coef, w, h, (uint8_t*)d_dst, pitch);
-  else
-    inverse_exact_kernel<1><<<grid, 256, 0, stream>>>(d_coef, w, h, (uint8_t*)d_dst, pitch);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_psnr_pair(int dtype, const void* d_a, long long pitch_a, const void* d_b, long long pitch_b,
@@ -1938,7 +1788,7 @@ cudaError_t launch_zonal_dct(const ImageJob* d_jobs, int njobs, long long ntiles
 
 int quant_ctas_per_sm() {
   int n = 0;
-  if (occupancy_with_smem(&n, quant_kernel<false>, 128, 4 * kQuantWarpSmemBytes) != cudaSuccess || n < 1) n = 1;
+  if (occupancy_with_smem(&n, quant_kernel<false, false>, 128, 4 * kQuantWarpSmemBytes) != cudaSuccess || n < 1) n = 1;
   return n;
 }
 

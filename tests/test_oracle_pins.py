@@ -277,6 +277,61 @@ def test_zigzag_matches_walk_and_invariants():
     assert O.zonal_mask(256).all() and O.zonal_mask(150).sum() == 150
 
 
+# ------------------------------------------ 1-D transforms, zig-zag layout ---
+def test_forward_1d_is_the_separable_factor_of_forward_int():
+    # the 2-D forward is the 1-D forward of every row, then of every column
+    rng = np.random.default_rng(41)
+    img = rng.integers(-32768, 32768, size=(32, 48))
+    rows = O.forward_1d(O.to_blocks(img))                      # R[m, v]
+    y = np.swapaxes(O.forward_1d(np.swapaxes(rows, -1, -2)), -1, -2)
+    assert np.array_equal(y, O.forward_int(img))
+    for j in range(16):  # unit vectors give the columns of T
+        e = np.zeros(16, dtype=np.int64)
+        e[j] = 1
+        assert np.array_equal(O.forward_1d(e), O.T[:, j])
+
+
+def test_inverse_1d_matches_fractions_with_printed_s(golden_dir):
+    # x_n = sum_u T[u, n] S_u^2 y_u with S_u^2 = 1 / den_u as printed in Sec. 2,
+    # rounded half to even (Python's round of a Fraction) and clamped
+    den = [int(v) for v in _golden_lines(golden_dir, "s_printed.txt")]
+    rng = np.random.default_rng(43)
+    cases = [rng.integers(-70000, 70000, size=16), rng.integers(-2**31, 2**31, size=16),
+             rng.integers(-3000, 3000, size=16)]
+    for k in (8, 24, -8, -24, 40):  # DC alone: x = k / 16, ties at odd multiples of 8
+        e = np.zeros(16, dtype=np.int64)
+        e[0] = k
+        cases.append(e)
+    for y in cases:
+        for dt in (np.uint8, np.int16):
+            info = np.iinfo(dt)
+            got = O.inverse_1d(y, dt)
+            for n in range(16):
+                f = sum(Fraction(int(O.T[u, n]) * int(y[u]), den[u]) for u in range(16))
+                assert got[n] == min(max(round(f), info.min), info.max)
+
+
+def test_inverse_1d_reconstructs_forward_1d():
+    rng = np.random.default_rng(44)
+    x8 = rng.integers(0, 256, size=(50, 16)).astype(np.uint8)
+    x16 = rng.integers(-32768, 32768, size=(50, 16)).astype(np.int16)
+    assert np.array_equal(O.inverse_1d(O.forward_1d(x8), np.uint8), x8)
+    assert np.array_equal(O.inverse_1d(O.forward_1d(x16), np.int16), x16)
+
+
+def test_zigzag_layout_round_trip_and_scan():
+    assert np.array_equal(O.to_zigzag(O.zigzag_rank()), np.arange(256))
+    rng = np.random.default_rng(45)
+    c = rng.integers(-1000, 1000, size=(3, 2, 16, 16))
+    assert np.array_equal(O.from_zigzag(O.to_zigzag(c)), c)
+    for r in (1, 6, 100, 256):
+        z = O.to_zigzag(O.zonal_mask(r).astype(np.int64))
+        assert z[:r].all() and not z[r:].any()
+    # first entries follow the walk of Sec. 4: DC, then (0,1), (1,0), (2,0)
+    b = np.arange(256).reshape(16, 16)
+    assert list(O.to_zigzag(b)[:4]) == [0, 1, 16, 32]
+
+
 # ---------------------------------------------------------- quantiser ---
 def test_quantiser_fp32_decision_close_to_fp64():
     from paper_1606_05562_gb300 import synth
