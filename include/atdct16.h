@@ -125,7 +125,7 @@ atdct16_status atdct16_forward(atdct16_plan_t plan, atdct16_dtype dtype, const v
  * clamped to the range of `dtype`.  Coefficients produced by atdct16_forward reconstruct the input
  * bit-exactly.  Layout of d_coef as for atdct16_forward (the plan's order).
  * Any int32 coefficients are accepted and give the exact result: tiles whose
- * coefficients all satisfy |Y| <= 2^18 run in 32-bit integers (|Z| < 2^31),
+ * coefficients all satisfy |Y| < 2^18 run in 32-bit integers (|Z| < 2^31),
  * others in two 32-bit halves combined in 64 bits.  d_coef, d_dst and pitch
  * 16-byte aligned, w, h multiples of 16 (EINVAL otherwise). */
 atdct16_status atdct16_inverse(atdct16_plan_t plan, atdct16_dtype dtype, const int32_t* d_coef,

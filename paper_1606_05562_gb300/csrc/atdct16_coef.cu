@@ -176,66 +176,79 @@ coef_forward_kernel(const uint8_t* __restrict__ src, long long pitch, int w, int
   const int tiles_x = (w + kTileW - 1) / kTileW;
   const int ntiles = tiles_x * (h >> 4);  // the launcher checks it fits
   const int bpr = w >> 4;
-  for (int t = blockIdx.x * kCWarps + warp; t < ntiles; t += gridDim.x * kCWarps) {
+  // The input rows of the warp's next tile are loaded while the current one
+  // is transformed (register double buffer: U8 4, I16 8 16-byte words).
+  constexpr int kLoads = kDtype == 0 ? 4 : 8;
+  const int stride = gridDim.x * kCWarps;
+  auto load = [&](int t, uint4 (&r)[kLoads]) {
+#pragma unroll
+    for (int i = 0; i < kLoads; ++i) r[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (t >= ntiles) return;
     const int ty = t / tiles_x, tx = t - ty * tiles_x;
     const int nb = min(8, (w - tx * kTileW) >> 4);
-    const bool va = p < nb, vb = p + 4 < nb;
     const uint8_t* s = src + (long long)(ty * kTileH + 2 * j) * pitch + (long long)(tx * kTileW + 16 * p) * kElem;
-    // ---- row pass on rows 2j, 2j+1 into the line buffer
-    float2* const half = reinterpret_cast<float2*>(line + 138 * p + j);
     if (kDtype == 0) {
-      uint4 a[2], b[2];
-      a[0] = a[1] = b[0] = b[1] = make_uint4(0u, 0u, 0u, 0u);
-      if (va) {
-        a[0] = ldg_stream(s);
-        a[1] = ldg_stream(s + pitch);
+      if (p < nb) {
+        r[0] = ldg_stream(s);
+        r[1] = ldg_stream(s + pitch);
       }
-      if (vb) {
-        b[0] = ldg_stream(s + 64);
-        b[1] = ldg_stream(s + 64 + pitch);
-      }
-#pragma unroll
-      for (int tr = 0; tr < 2; ++tr) {
-        float2 xv[16], rv[16];
-#pragma unroll
-        for (int n = 0; n < 16; ++n)
-          xv[n] = make_float2(u8_x256(word_at(a[tr], n >> 2), n & 3), u8_x256(word_at(b[tr], n >> 2), n & 3));
-        fwd16(xv, rv);
-        rv[0] = bsub(rv[0], make_float2(134217728.0f, 134217728.0f));  // 16 * 2^23 of the offsets
-#pragma unroll
-        for (int k = 0; k < 16; ++k) half[2 * (8 * k + (k >> 1)) + tr] = rv[k];
+      if (p + 4 < nb) {
+        r[2] = ldg_stream(s + 64);
+        r[3] = ldg_stream(s + 64 + pitch);
       }
     } else {
-      uint4 a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = b[i] = make_uint4(0u, 0u, 0u, 0u);
-      if (va) {
-        a[0] = ldg_stream(s);
-        a[1] = ldg_stream(s + 16);
-        a[2] = ldg_stream(s + pitch);
-        a[3] = ldg_stream(s + pitch + 16);
+      if (p < nb) {
+        r[0] = ldg_stream(s);
+        r[1] = ldg_stream(s + 16);
+        r[2] = ldg_stream(s + pitch);
+        r[3] = ldg_stream(s + pitch + 16);
       }
-      if (vb) {
-        b[0] = ldg_stream(s + 128);
-        b[1] = ldg_stream(s + 144);
-        b[2] = ldg_stream(s + pitch + 128);
-        b[3] = ldg_stream(s + pitch + 144);
+      if (p + 4 < nb) {
+        r[4] = ldg_stream(s + 128);
+        r[5] = ldg_stream(s + 144);
+        r[6] = ldg_stream(s + pitch + 128);
+        r[7] = ldg_stream(s + pitch + 144);
       }
+    }
+  };
+  uint4 cur[kLoads], nxt[kLoads];
+  load(blockIdx.x * kCWarps + warp, cur);
+  for (int t = blockIdx.x * kCWarps + warp; t < ntiles; t += stride) {
+    const int ty = t / tiles_x, tx = t - ty * tiles_x;
+    const int nb = min(8, (w - tx * kTileW) >> 4);
+    load(t + stride, nxt);
+    // ---- row pass on rows 2j, 2j+1; both rows of column k go to the line
+    // buffer as one 16-byte unit (138 p + 8 k + (k >> 1) + j), conflict-free
+    float2 rv[2][16];
+    if (kDtype == 0) {
 #pragma unroll
       for (int tr = 0; tr < 2; ++tr) {
-        float2 xv[16], rv[16];
+        float2 xv[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n)
+          xv[n] = make_float2(u8_x256(word_at(cur[tr], n >> 2), n & 3), u8_x256(word_at(cur[2 + tr], n >> 2), n & 3));
+        fwd16(xv, rv[tr]);
+        rv[tr][0] = bsub(rv[tr][0], make_float2(134217728.0f, 134217728.0f));  // 16 * 2^23 of the offsets
+      }
+    } else {
+#pragma unroll
+      for (int tr = 0; tr < 2; ++tr) {
+        float2 xv[16];
 #pragma unroll
         for (int n = 0; n < 16; ++n) {
-          const unsigned wa = word_at(a[2 * tr + (n >> 3)], (n & 7) >> 1);
-          const unsigned wb = word_at(b[2 * tr + (n >> 3)], (n & 7) >> 1);
+          const unsigned wa = word_at(cur[2 * tr + (n >> 3)], (n & 7) >> 1);
+          const unsigned wb = word_at(cur[4 + 2 * tr + (n >> 3)], (n & 7) >> 1);
           const float2 m = (n & 1) ? make_float2(i16_hi_f(wa), i16_hi_f(wb)) : make_float2(i16_lo_f(wa), i16_lo_f(wb));
           xv[n] = __fadd2_rn(m, make_float2(-8421376.0f, -8421376.0f));  // exact sample value
         }
-        fwd16(xv, rv);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) half[2 * (8 * k + (k >> 1)) + tr] = rv[k];
+        fwd16(xv, rv[tr]);
       }
     }
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      line[138 * p + 8 * k + (k >> 1) + j] = make_float4(rv[0][k].x, rv[0][k].y, rv[1][k].x, rv[1][k].y);
+#pragma unroll
+    for (int i = 0; i < kLoads; ++i) cur[i] = nxt[i];
     __syncwarp();
     // ---- column pass on columns 2j, 2j+1 into the block stage
 #pragma unroll
@@ -298,8 +311,8 @@ coef_forward_kernel(const uint8_t* __restrict__ src, long long pitch, int w, int
 // 2-D exact inverse: Z = T^T (W Y W) T, X_hat = Z / 2304 (Sec. 4 with
 // S^2 = W / 48 folded in), round half to even, clamp.
 //
-// A tile whose coefficients all satisfy |Y| <= 2^18 runs in int32: |Z| <=
-// (sum_u W_u)^2 2^18 = 68^2 2^18 < 2^31.  Any other tile (checked per warp)
+// A tile whose coefficients all satisfy -2^18 <= Y < 2^18 runs in int32:
+// |Z| <= (sum_u W_u)^2 2^18 = 68^2 2^18 < 2^31.  Any other tile (checked per warp)
 // splits Y = 2^16 Y_h + Y_l (|Y_h| <= 2^15, 0 <= Y_l < 2^16), transforms both
 // halves exactly in int32 and forms Z = 2^16 Z_h + Z_l in 64 bits.  The
 // low-half column results go to the block stage, into the words their lane
@@ -334,18 +347,18 @@ __device__ __forceinline__ void store_row(uint8_t* d, bool va, bool vb, const in
   }
 }
 
-// Z (|Z| < 2^31) of two blocks -> rounded, clamped outputs.  U8: the exact
-// float Z (after clamping to [-1153, 589825], where the result is already
-// decided) times fp32(1/2304) equals Z / 2304 exactly at every half-integer
-// and is within 6e-5 of it elsewhere, far inside the 1/2304 gap to the next
-// half-integer; its round-half-even is read off the denormal bits of
-// fl(t * 2^-149) and saturated by the pack.  I16: integer division.
+// Z (|Z| < 2^31) of two blocks -> rounded, clamped outputs.  U8: for
+// |Z| < 2^24 the float Z is exact, and fl(Z * fp32(1/2304)) equals Z / 2304
+// exactly at every half-integer and is within 6e-5 of it elsewhere, far
+// inside the 1/2304 gap to the next half-integer; its round-half-even is
+// read off the denormal bits of fl(t * 2^-149) (|t| < 2^23 keeps it
+// denormal) and saturated by the pack.  Any Z outside [-1152, 589824] gives
+// a t beyond -0.5 or 256 whatever the rounding of float(Z), so it saturates
+// correctly too.  I16: integer division.
 template <int kDtype>
 __device__ __forceinline__ void round_pair(int za, int zb, int& qa, int& qb) {
   if (kDtype == 0) {
-    const int ca = min(max(za, -1153), 589825), cb = min(max(zb, -1153), 589825);
-    float2 f = make_float2(__int_as_float(ca + 0x4B400000), __int_as_float(cb + 0x4B400000));
-    f = __fadd2_rn(f, make_float2(-12582912.0f, -12582912.0f));
+    float2 f = make_float2((float)za, (float)zb);
     f = __fmul2_rn(f, make_float2(1.0f / 2304.0f, 1.0f / 2304.0f));
     f = __fmul2_rn(f, make_float2(__uint_as_float(1u), __uint_as_float(1u)));
     qa = (int)__float_as_uint(f.x);
@@ -385,12 +398,12 @@ coef_inverse_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __r
 #pragma unroll
     for (int m = 0; m < 16; ++m)
       v[m] = (m >> 1) < nb ? ldg_stream(in + 256 * (m >> 1) + 4 * (32 * (m & 1) + lane)) : make_uint4(0u, 0u, 0u, 0u);
+    // range test: Y + 2^18 < 2^19 (as unsigned) for every Y of the tile
     unsigned big = 0u;
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int b = m >> 1, hh = m & 1, bs = bswz(b);
-      big |= ((unsigned)((int)v[m].x ^ ((int)v[m].x >> 31))) | ((unsigned)((int)v[m].y ^ ((int)v[m].y >> 31))) |
-             ((unsigned)((int)v[m].z ^ ((int)v[m].z >> 31))) | ((unsigned)((int)v[m].w ^ ((int)v[m].w >> 31)));
+      big |= (v[m].x + (1u << 18)) | (v[m].y + (1u << 18)) | (v[m].z + (1u << 18)) | (v[m].w + (1u << 18));
       int* const sb = stage + 256 * b;
       if (!kZigzag) {
         const uint4 x = (b & 1) ? make_uint4(v[m].y, v[m].x, v[m].w, v[m].z) : v[m];
@@ -402,7 +415,7 @@ coef_inverse_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __r
         sb[zz_byte(zz[hh], 3) ^ bs] = (int)v[m].w;
       }
     }
-    const bool wide = __any_sync(0xffffffffu, big >= (1u << 18));
+    const bool wide = __any_sync(0xffffffffu, big >= (1u << 19));
     __syncwarp();
     uint8_t* const drow = dst + (long long)(ty * kTileH + 2 * j) * pitch + (long long)(tx * kTileW + 16 * p) * kElem;
     if (!wide) {

@@ -1186,30 +1186,41 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
 // SSIM (Sec. 4, the measure of Wang et al. 2004): mean over the valid
 // positions of the 11x11 Gaussian window (sigma 1.5) of
 //   (2 mu_a mu_b + C1)(2 s_ab + C2) / ((mu_a^2 + mu_b^2 + C1)(s_a^2 + s_b^2 + C2)).
-// One CTA per tile of 16 x 64 window positions: the 26 x 74 input pixels of
-// both images go to shared memory centred (x - 128, which keeps the moment
-// form E[xy] - E[x]E[y] well conditioned in FP32) together with their
-// products; a horizontal pass filters the five moments of every input row,
-// a vertical pass finishes them per position; the tile's sum of SSIM values
-// goes to tile_sum.  The window is separable: the 2-D normalised Gaussian is
-// the outer product of the 1-D normalised one (kSsimW).
+// The window is separable: the 2-D normalised Gaussian is the outer product
+// of the 1-D normalised one (kSsimW).  One CTA per tile of 30 x 128 window
+// positions, in two passes over the five moments of the centred pixels
+// (a, b, a^2, b^2, ab with a = x - 128, which keeps the moment form
+// E[xy] - E[x]E[y] well conditioned in FP32):
+//   vertical    thread c (< 138) walks column x0 + c down the 40 input rows
+//               with 11 running sums per moment in registers (row r adds
+//               w_k f(r) to output row r - k; output row r - 10 is then
+//               complete), into the moment planes in shared memory;
+//   horizontal  a thread takes 8 consecutive positions of one row, reads
+//               the 18 vertical moments it needs as 16-byte loads and
+//               finishes the 11 taps and the SSIM value in registers.
+// The tile's sum of SSIM values goes to tile_sum.
 // --------------------------------------------------------------------------
-constexpr int kSsimTileH = 16, kSsimTileW = 64;
-constexpr int kSsimInH = kSsimTileH + 10, kSsimInW = kSsimTileW + 10;
+constexpr int kSsimTR = kSsimTileRows, kSsimTC = kSsimTileCols;
+constexpr int kSsimVC = kSsimTC + 10;  // columns of vertical moments
+constexpr int kSsimVS = 140;           // row stride of a moment plane (floats, a 16-byte multiple)
+constexpr int kSsimThreads = 160;
+static_assert(kSsimTR == 30 && kSsimTC == 128, "the loops below are written for 30 x 128 tiles");
 __constant__ float kSsimW[11];
 
 struct alignas(16) SsimSmem {
-  float in[5][kSsimInH][kSsimInW];        // a, b, a^2, b^2, ab (centred)
-  float hor[5][kSsimInH][kSsimTileW];     // horizontally filtered
-  float red[8];
+  float v[5][kSsimTR][kSsimVS];
+  float red[kSsimThreads / 32];
 };
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kSsimThreads, 2)
 ssim_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles, float* __restrict__ tile_sum,
             int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char ssmem[];
   SsimSmem& sm = *reinterpret_cast<SsimSmem*>(ssmem);
   const int tid = threadIdx.x;
+  float wk[11];
+#pragma unroll
+  for (int k = 0; k < 11; ++k) wk[k] = kSsimW[k];
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int job = 0;
     warp_find_job(jobs, njobs, t, job);
@@ -1217,67 +1228,104 @@ ssim_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles, floa
     const long long tb = __ldg(&J->tile_begin);
     const int w = __ldg(&J->width), h = __ldg(&J->height), tiles_x = __ldg(&J->tiles_x);
     const int mh = h - 10, mw = w - 10;  // window positions
-    if (t < tb || t >= tb + (long long)tiles_x * ((mh + kSsimTileH - 1) / kSsimTileH)) {
+    if (t < tb || t >= tb + (long long)tiles_x * ((mh + kSsimTR - 1) / kSsimTR)) {
       if (tid == 0) set_status(status, kDevBadJob);
       if (tid == 0) tile_sum[t] = 0.f;
       continue;
     }
     const int lt = (int)(t - tb), ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    const int y0 = ty * kSsimTileH, x0 = tx * kSsimTileW;
+    const int y0 = ty * kSsimTR, x0 = tx * kSsimTC;
     const uint8_t* pa = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->src)));
     const uint8_t* pb = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->dst)));
     const long long ps = __ldg(&J->src_pitch), pd = __ldg(&J->dst_pitch);
     __syncthreads();  // the previous tile's reads of sm are done
-    for (int i = tid; i < kSsimInH * kSsimInW; i += blockDim.x) {
-      const int r = i / kSsimInW, c = i - r * kSsimInW;
-      const int y = y0 + r, x = x0 + c;
-      float a = 0.f, b = 0.f;
-      if (y < h && x < w) {
-        a = (float)__ldg(pa + y * ps + x) - 128.f;
-        b = (float)__ldg(pb + y * pd + x) - 128.f;
-      }
-      sm.in[0][r][c] = a;
-      sm.in[1][r][c] = b;
-      sm.in[2][r][c] = a * a;
-      sm.in[3][r][c] = b * b;
-      sm.in[4][r][c] = a * b;
-    }
-    __syncthreads();
-    for (int i = tid; i < kSsimInH * kSsimTileW; i += blockDim.x) {
-      const int r = i / kSsimTileW, c = i - r * kSsimTileW;
+    if (tid < kSsimVC) {
+      const int x = x0 + tid;
+      const bool xin = x < w;
+      float acc[11][5];
 #pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        float s = 0.f;
+      for (int s = 0; s < 11; ++s)
 #pragma unroll
-        for (int k = 0; k < 11; ++k) s = fmaf(kSsimW[k], sm.in[m][r][c + k], s);
-        sm.hor[m][r][c] = s;
+        for (int m = 0; m < 5; ++m) acc[s][m] = 0.f;
+#pragma unroll
+      for (int rb = 0; rb < 4; ++rb) {  // input rows 11 rb .. 11 rb + 10 (40 in all)
+        float la[11], lb[11];
+#pragma unroll
+        for (int kk = 0; kk < 11; ++kk) {
+          const int y = y0 + 11 * rb + kk;
+          la[kk] = lb[kk] = 128.f;
+          if (11 * rb + kk < kSsimTR + 10 && xin && y < h) {
+            la[kk] = (float)__ldg(pa + y * ps + x);
+            lb[kk] = (float)__ldg(pb + y * pd + x);
+          }
+        }
+#pragma unroll
+        for (int kk = 0; kk < 11; ++kk) {
+          const int r = 11 * rb + kk;
+          if (r < kSsimTR + 10) {
+            const float a = la[kk] - 128.f, b = lb[kk] - 128.f;
+            const float f[5] = {a, b, a * a, b * b, a * b};
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+              const int sl = (kk - k + 11) % 11;  // slot of output row r - k
+#pragma unroll
+              for (int m = 0; m < 5; ++m) acc[sl][m] = fmaf(wk[k], f[m], acc[sl][m]);
+            }
+            const int o = r - 10, sl = (kk + 1) % 11;  // output row r - 10 is complete
+            if (o >= 0) {
+#pragma unroll
+              for (int m = 0; m < 5; ++m) sm.v[m][o][tid] = acc[sl][m];
+            }
+#pragma unroll
+            for (int m = 0; m < 5; ++m) acc[sl][m] = 0.f;
+          }
+        }
       }
     }
     __syncthreads();
     float part = 0.f;
-    for (int i = tid; i < kSsimTileH * kSsimTileW; i += blockDim.x) {
-      const int r = i / kSsimTileW, c = i - r * kSsimTileW;
-      if (y0 + r >= mh || x0 + c >= mw) continue;
-      float mo[5];
+    for (int i = tid; i < kSsimTR * (kSsimTC / 8); i += kSsimThreads) {
+      const int row = i >> 4, c0 = 8 * (i & 15);
+      float mo[5][8];
 #pragma unroll
       for (int m = 0; m < 5; ++m) {
-        float s = 0.f;
+        float in[20];
+        const float4* src = reinterpret_cast<const float4*>(&sm.v[m][row][c0]);
 #pragma unroll
-        for (int k = 0; k < 11; ++k) s = fmaf(kSsimW[k], sm.hor[m][r + k][c], s);
-        mo[m] = s;
+        for (int q = 0; q < 5; ++q) {
+          const float4 v = src[q];
+          in[4 * q] = v.x;
+          in[4 * q + 1] = v.y;
+          in[4 * q + 2] = v.z;
+          in[4 * q + 3] = v.w;
+        }
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+          float s = 0.f;
+#pragma unroll
+          for (int k = 0; k < 11; ++k) s = fmaf(wk[k], in[o + k], s);
+          mo[m][o] = s;
+        }
       }
-      // back from the centred values: mu = mu' + 128; variances and covariance unchanged
-      const float ma = mo[0] + 128.f, mb = mo[1] + 128.f;
-      const float saa = mo[2] - mo[0] * mo[0], sbb = mo[3] - mo[1] * mo[1], sab = mo[4] - mo[0] * mo[1];
-      const float c1 = 6.5025f, c2 = 58.5225f;  // (0.01 * 255)^2, (0.03 * 255)^2
-      part += ((2.f * ma * mb + c1) * (2.f * sab + c2)) / ((ma * ma + mb * mb + c1) * (saa + sbb + c2));
+      const bool rin = y0 + row < mh;
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        // back from the centred values: mu = mu' + 128; variances and covariance unchanged
+        const float ma = mo[0][o] + 128.f, mb = mo[1][o] + 128.f;
+        const float saa = mo[2][o] - mo[0][o] * mo[0][o], sbb = mo[3][o] - mo[1][o] * mo[1][o];
+        const float sab = mo[4][o] - mo[0][o] * mo[1][o];
+        const float c1 = 6.5025f, c2 = 58.5225f;  // (0.01 * 255)^2, (0.03 * 255)^2
+        const float v = __fdividef((2.f * ma * mb + c1) * (2.f * sab + c2), (ma * ma + mb * mb + c1) * (saa + sbb + c2));
+        if (rin && x0 + c0 + o < mw) part += v;
+      }
     }
     part = warp_sum(part);
     if ((tid & 31) == 0) sm.red[tid >> 5] = part;
     __syncthreads();
     if (tid == 0) {
       float s = 0.f;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sm.red[k];
+#pragma unroll
+      for (int k = 0; k < kSsimThreads / 32; ++k) s += sm.red[k];
       tile_sum[t] = s;
     }
   }
@@ -1739,10 +1787,10 @@ cudaError_t launch_ssim(const ImageJob* d_jobs, int njobs, long long ntiles, flo
   }
   const int smem = (int)sizeof(SsimSmem);
   int per_sm = 0;
-  e = occupancy_with_smem(&per_sm, ssim_kernel, 256, smem);
+  e = occupancy_with_smem(&per_sm, ssim_kernel, kSsimThreads, smem);
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<long long>(ntiles, (long long)num_sms * std::max(1, per_sm));
-  e = launch_with_smem(ssim_kernel, grid, 256, smem, stream, d_jobs, njobs, ntiles, d_tile_sum, d_status);
+  e = launch_with_smem(ssim_kernel, grid, kSsimThreads, smem, stream, d_jobs, njobs, ntiles, d_tile_sum, d_status);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((njobs + 7) / 8);
