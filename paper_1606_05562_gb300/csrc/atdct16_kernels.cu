@@ -1190,27 +1190,78 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
 // of the 1-D normalised one (kSsimW).  One CTA per tile of 30 x 128 window
 // positions, in two passes over the five moments of the centred pixels
 // (a, b, a^2, b^2, ab with a = x - 128, which keeps the moment form
-// E[xy] - E[x]E[y] well conditioned in FP32):
+// E[xy] - E[x]E[y] well conditioned in FP32), (a, b) and (a^2, b^2) as
+// packed pairs (one f32x2 instruction per pair):
+//   input       the tile's 40 x 138 pixels of both images, copied to shared
+//               memory with cp.async; the next tile's copy starts as soon as
+//               the vertical pass has read this one;
 //   vertical    thread c (< 138) walks column x0 + c down the 40 input rows
 //               with 11 running sums per moment in registers (row r adds
 //               w_k f(r) to output row r - k; output row r - 10 is then
-//               complete), into the moment planes in shared memory;
-//   horizontal  a thread takes 8 consecutive positions of one row, reads
-//               the 18 vertical moments it needs as 16-byte loads and
-//               finishes the 11 taps and the SSIM value in registers.
+//               complete), into the moment planes;
+//   horizontal  a thread takes 8 consecutive positions of one row (lanes on
+//               consecutive rows: odd 16-byte row strides keep the 16-byte
+//               reads conflict-free) and finishes the 11 taps and the SSIM
+//               value in registers.
 // The tile's sum of SSIM values goes to tile_sum.
 // --------------------------------------------------------------------------
 constexpr int kSsimTR = kSsimTileRows, kSsimTC = kSsimTileCols;
-constexpr int kSsimVC = kSsimTC + 10;  // columns of vertical moments
-constexpr int kSsimVS = 140;           // row stride of a moment plane (floats, a 16-byte multiple)
+constexpr int kSsimVC = kSsimTC + 10;   // columns of vertical moments
+constexpr int kSsimIR = kSsimTR + 10;   // input rows of a tile
+constexpr int kSsimIS = 144;            // bytes per staged input row (9 chunks of 16)
+constexpr int kSsimVS2 = 142;           // row stride of a pair plane (float2): 71 chunks
+constexpr int kSsimVS1 = 140;           // row stride of the ab plane (float): 35 chunks
 constexpr int kSsimThreads = 160;
 static_assert(kSsimTR == 30 && kSsimTC == 128, "the loops below are written for 30 x 128 tiles");
 __constant__ float kSsimW[11];
 
 struct alignas(16) SsimSmem {
-  float v[5][kSsimTR][kSsimVS];
+  float2 v2[2][kSsimTR][kSsimVS2];   // vertical (a, b) and (a^2, b^2)
+  float v1[kSsimTR][kSsimVS1];       // vertical ab
+  uint8_t in[2][kSsimIR][kSsimIS];   // input pixels of both images
   float red[kSsimThreads / 32];
 };
+
+struct SsimTile {
+  const uint8_t* pa;
+  const uint8_t* pb;
+  long long ps, pd;
+  int w, h, y0, x0;
+  bool ok;
+};
+
+__device__ __forceinline__ SsimTile ssim_tile(const ImageJob* __restrict__ jobs, int njobs, long long t) {
+  SsimTile T;
+  int job = 0;
+  warp_find_job(jobs, njobs, t, job);
+  const ImageJob* J = jobs + job;
+  const long long tb = __ldg(&J->tile_begin);
+  T.w = __ldg(&J->width);
+  T.h = __ldg(&J->height);
+  const int tiles_x = __ldg(&J->tiles_x);
+  T.ok = t >= tb && t < tb + (long long)tiles_x * ((T.h - 10 + kSsimTR - 1) / kSsimTR) && tiles_x > 0;
+  const int lt = T.ok ? (int)(t - tb) : 0, ty = lt / max(tiles_x, 1), tx = lt - ty * max(tiles_x, 1);
+  T.y0 = ty * kSsimTR;
+  T.x0 = tx * kSsimTC;
+  T.pa = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->src)));
+  T.pb = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->dst)));
+  T.ps = __ldg(&J->src_pitch);
+  T.pd = __ldg(&J->dst_pitch);
+  return T;
+}
+
+// cp.async of a tile's input rows: 2 images x 40 rows x 9 chunks of 16 bytes;
+// chunks past the image (width and pitch are multiples of 16) are zero-filled.
+__device__ __forceinline__ void ssim_issue(SsimSmem& sm, const SsimTile& T, int tid) {
+  for (int i = tid; i < 2 * kSsimIR * 9; i += kSsimThreads) {
+    const int img = i / (kSsimIR * 9), rem = i - img * (kSsimIR * 9), r = rem / 9, k = rem - r * 9;
+    const int y = T.y0 + r, x = T.x0 + 16 * k;
+    const bool in = y < T.h && x < T.w;
+    const uint8_t* g = img ? T.pb + (in ? y * T.pd + x : 0) : T.pa + (in ? y * T.ps + x : 0);
+    cp_async16_zfill(&sm.in[img][r][16 * k], g, in ? 16 : 0);
+  }
+  cp_async_commit();
+}
 
 __global__ void __launch_bounds__(kSsimThreads, 2)
 ssim_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles, float* __restrict__ tile_sum,
@@ -1221,76 +1272,85 @@ ssim_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles, floa
   float wk[11];
 #pragma unroll
   for (int k = 0; k < 11; ++k) wk[k] = kSsimW[k];
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int job = 0;
-    warp_find_job(jobs, njobs, t, job);
-    const ImageJob* J = jobs + job;
-    const long long tb = __ldg(&J->tile_begin);
-    const int w = __ldg(&J->width), h = __ldg(&J->height), tiles_x = __ldg(&J->tiles_x);
-    const int mh = h - 10, mw = w - 10;  // window positions
-    if (t < tb || t >= tb + (long long)tiles_x * ((mh + kSsimTR - 1) / kSsimTR)) {
-      if (tid == 0) set_status(status, kDevBadJob);
-      if (tid == 0) tile_sum[t] = 0.f;
-      continue;
-    }
-    const int lt = (int)(t - tb), ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    const int y0 = ty * kSsimTR, x0 = tx * kSsimTC;
-    const uint8_t* pa = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->src)));
-    const uint8_t* pb = reinterpret_cast<const uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&J->dst)));
-    const long long ps = __ldg(&J->src_pitch), pd = __ldg(&J->dst_pitch);
-    __syncthreads();  // the previous tile's reads of sm are done
-    if (tid < kSsimVC) {
-      const int x = x0 + tid;
-      const bool xin = x < w;
-      float acc[11][5];
+  long long t = blockIdx.x;
+  if (t >= ntiles) return;
+  SsimTile T = ssim_tile(jobs, njobs, t);
+  if (T.ok) ssim_issue(sm, T, tid);
+  for (; t < ntiles; t += gridDim.x) {
+    const long long tn = t + gridDim.x;
+    cp_async_wait<0>();
+    __syncthreads();  // this tile's input is in; the previous tile's moment reads are done
+    if (T.ok && tid < kSsimVC) {
+      float2 acc2[11][2];
+      float acc1[11];
 #pragma unroll
-      for (int s = 0; s < 11; ++s)
+      for (int s = 0; s < 11; ++s) {
+        acc2[s][0] = acc2[s][1] = make_float2(0.f, 0.f);
+        acc1[s] = 0.f;
+      }
 #pragma unroll
-        for (int m = 0; m < 5; ++m) acc[s][m] = 0.f;
+      for (int r = 0; r < kSsimIR; ++r) {
+        const float a = (float)sm.in[0][r][tid] - 128.f, b = (float)sm.in[1][r][tid] - 128.f;
+        const float2 ab = make_float2(a, b), sq = __fmul2_rn(ab, ab);
+        const float x = a * b;
 #pragma unroll
-      for (int rb = 0; rb < 4; ++rb) {  // input rows 11 rb .. 11 rb + 10 (40 in all)
-        float la[11], lb[11];
-#pragma unroll
-        for (int kk = 0; kk < 11; ++kk) {
-          const int y = y0 + 11 * rb + kk;
-          la[kk] = lb[kk] = 128.f;
-          if (11 * rb + kk < kSsimTR + 10 && xin && y < h) {
-            la[kk] = (float)__ldg(pa + y * ps + x);
-            lb[kk] = (float)__ldg(pb + y * pd + x);
-          }
+        for (int k = 0; k < 11; ++k) {
+          const int sl = (r - k + 22) % 11;  // slot of output row r - k
+          const float2 wk2 = make_float2(wk[k], wk[k]);
+          acc2[sl][0] = __ffma2_rn(wk2, ab, acc2[sl][0]);
+          acc2[sl][1] = __ffma2_rn(wk2, sq, acc2[sl][1]);
+          acc1[sl] = fmaf(wk[k], x, acc1[sl]);
         }
-#pragma unroll
-        for (int kk = 0; kk < 11; ++kk) {
-          const int r = 11 * rb + kk;
-          if (r < kSsimTR + 10) {
-            const float a = la[kk] - 128.f, b = lb[kk] - 128.f;
-            const float f[5] = {a, b, a * a, b * b, a * b};
-#pragma unroll
-            for (int k = 0; k < 11; ++k) {
-              const int sl = (kk - k + 11) % 11;  // slot of output row r - k
-#pragma unroll
-              for (int m = 0; m < 5; ++m) acc[sl][m] = fmaf(wk[k], f[m], acc[sl][m]);
-            }
-            const int o = r - 10, sl = (kk + 1) % 11;  // output row r - 10 is complete
-            if (o >= 0) {
-#pragma unroll
-              for (int m = 0; m < 5; ++m) sm.v[m][o][tid] = acc[sl][m];
-            }
-#pragma unroll
-            for (int m = 0; m < 5; ++m) acc[sl][m] = 0.f;
-          }
+        const int o = r - 10, sl = (r + 1) % 11;  // output row r - 10 is complete
+        if (o >= 0) {
+          sm.v2[0][o][tid] = acc2[sl][0];
+          sm.v2[1][o][tid] = acc2[sl][1];
+          sm.v1[o][tid] = acc1[sl];
         }
+        acc2[sl][0] = acc2[sl][1] = make_float2(0.f, 0.f);
+        acc1[sl] = 0.f;
       }
     }
-    __syncthreads();
+    __syncthreads();  // moments complete; the input buffer is free
+    const SsimTile cur = T;
+    if (tn < ntiles) {
+      T = ssim_tile(jobs, njobs, tn);
+      if (T.ok) ssim_issue(sm, T, tid);
+    }
+    if (!cur.ok) {
+      if (tid == 0) {
+        set_status(status, kDevBadJob);
+        tile_sum[t] = 0.f;
+      }
+      continue;
+    }
+    const int mh = cur.h - 10, mw = cur.w - 10;
     float part = 0.f;
     for (int i = tid; i < kSsimTR * (kSsimTC / 8); i += kSsimThreads) {
-      const int row = i >> 4, c0 = 8 * (i & 15);
-      float mo[5][8];
+      const int g = i / kSsimTR, row = i - g * kSsimTR, c0 = 8 * g;
+      float2 m2[2][8];
+      float m1[8];
 #pragma unroll
-      for (int m = 0; m < 5; ++m) {
+      for (int pl = 0; pl < 2; ++pl) {
+        float2 in[18];
+        const float4* src = reinterpret_cast<const float4*>(&sm.v2[pl][row][c0]);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          const float4 v = src[q];
+          in[2 * q] = make_float2(v.x, v.y);
+          in[2 * q + 1] = make_float2(v.z, v.w);
+        }
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+          float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int k = 0; k < 11; ++k) s2 = __ffma2_rn(make_float2(wk[k], wk[k]), in[o + k], s2);
+          m2[pl][o] = s2;
+        }
+      }
+      {
         float in[20];
-        const float4* src = reinterpret_cast<const float4*>(&sm.v[m][row][c0]);
+        const float4* src = reinterpret_cast<const float4*>(&sm.v1[row][c0]);
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
           const float4 v = src[q];
@@ -1301,22 +1361,22 @@ ssim_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles, floa
         }
 #pragma unroll
         for (int o = 0; o < 8; ++o) {
-          float s = 0.f;
+          float s1 = 0.f;
 #pragma unroll
-          for (int k = 0; k < 11; ++k) s = fmaf(wk[k], in[o + k], s);
-          mo[m][o] = s;
+          for (int k = 0; k < 11; ++k) s1 = fmaf(wk[k], in[o + k], s1);
+          m1[o] = s1;
         }
       }
-      const bool rin = y0 + row < mh;
+      const bool rin = cur.y0 + row < mh;
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
         // back from the centred values: mu = mu' + 128; variances and covariance unchanged
-        const float ma = mo[0][o] + 128.f, mb = mo[1][o] + 128.f;
-        const float saa = mo[2][o] - mo[0][o] * mo[0][o], sbb = mo[3][o] - mo[1][o] * mo[1][o];
-        const float sab = mo[4][o] - mo[0][o] * mo[1][o];
+        const float2 mu = m2[0][o], ex2 = m2[1][o];
+        const float ma = mu.x + 128.f, mb = mu.y + 128.f;
+        const float saa = ex2.x - mu.x * mu.x, sbb = ex2.y - mu.y * mu.y, sab = m1[o] - mu.x * mu.y;
         const float c1 = 6.5025f, c2 = 58.5225f;  // (0.01 * 255)^2, (0.03 * 255)^2
         const float v = __fdividef((2.f * ma * mb + c1) * (2.f * sab + c2), (ma * ma + mb * mb + c1) * (saa + sbb + c2));
-        if (rin && x0 + c0 + o < mw) part += v;
+        if (rin && cur.x0 + c0 + o < mw) part += v;
       }
     }
     part = warp_sum(part);
@@ -1329,6 +1389,7 @@ ssim_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles, floa
       tile_sum[t] = s;
     }
   }
+  cp_async_wait<0>();
 }
 
 // MSSIM per image: the tile sums in a fixed order (FP64) over the number of
