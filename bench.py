@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--quant-only", action="store_true",
                     help="run only the quantisation phase (--steps/--warmup apply) and print its JSON")
     ap.add_argument("--quant-frames", type=int, default=24)
+    ap.add_argument("--dct-only", action="store_true",
+                    help="run only the exact-DCT baseline phase (--steps applies) and print its JSON")
     ap.add_argument("--ssim-only", action="store_true",
                     help="run only the SSIM phase on one compressed step (--steps applies) and print its JSON")
     ap.add_argument("--coef-only", action="store_true",
@@ -750,6 +752,33 @@ def run_coef_only(args):
     return 0
 
 
+def run_dct_only(args):
+    """The exact-DCT baseline phase alone, on one GPU (profiling entry)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_1606_05562_gb300 import atdct16, synth
+    from paper_1606_05562_gb300 import build as b
+
+    b.build()
+    batch = synth.image_batch_512(N_IMAGES, SIDE, first_seed=100)
+    nr = len(R_SWEEP)
+    jobs = nr * N_IMAGES
+    base = torch.from_numpy(batch).to(dev)
+    sets = []
+    for _ in range(N_SETS):
+        src = base.unsqueeze(0).repeat(nr, 1, 1, 1).contiguous()
+        dst = torch.empty_like(src)
+        sets.append((src, dst, atdct16.descriptors(
+            [atdct16.image(src[k, i], dst[k, i], r) for k, r in enumerate(R_SWEEP) for i in range(N_IMAGES)])))
+    plan = atdct16.Plan(atdct16.U8, max_images=jobs)
+    res = dct_baseline_phase(torch, atdct16, plan, sets, jobs, jobs * SIDE * SIDE, None, steps=max(args.steps, 1))
+    plan.close()
+    print(json.dumps({"dct_baseline": res}), flush=True)
+    return 0
+
+
 def run_ssim_only(args):
     """The SSIM phase alone, on one GPU (profiling entry): one zonal step of
     the bench workload, then SSIM of its 512 reconstructions."""
@@ -787,6 +816,8 @@ def main():
         return run_coef_only(args)
     if args.ssim_only:
         return run_ssim_only(args)
+    if args.dct_only:
+        return run_dct_only(args)
     return run_ours(args)
 
 

@@ -1421,30 +1421,10 @@ __global__ void ssim_finalize_kernel(const ImageJob* __restrict__ jobs, int njob
 // --------------------------------------------------------------------------
 __constant__ float kDctC[16][16];  // C[k][j], FP32 of the FP64 values
 
-__device__ __forceinline__ void dct16_fwd(const float2 (&x)[16], float2 (&y)[16]) {
-#pragma unroll 4
-  for (int k = 0; k < 16; ++k) {
-    float sx = 0.f, sy = 0.f;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      sx = fmaf(kDctC[k][j], x[j].x, sx);
-      sy = fmaf(kDctC[k][j], x[j].y, sy);
-    }
-    y[k] = make_float2(sx, sy);
-  }
-}
-__device__ __forceinline__ void dct16_inv(const float2 (&y)[16], float2 (&x)[16]) {
-#pragma unroll 4
-  for (int j = 0; j < 16; ++j) {
-    float sx = 0.f, sy = 0.f;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      sx = fmaf(kDctC[k][j], y[k].x, sx);
-      sy = fmaf(kDctC[k][j], y[k].y, sy);
-    }
-    x[j] = make_float2(sx, sy);
-  }
-}
+// Row k of C, broadcast to both halves of a pair (the loops over k stay
+// rolled: k is warp-uniform, so C[k][.] comes through the uniform path and
+// no per-thread array is indexed at run time).
+__device__ __forceinline__ float2 dct_c2(int k, int jj) { return make_float2(kDctC[k][jj], kDctC[k][jj]); }
 
 constexpr int kDStageUnits = 2 * 4 * 32;
 constexpr int kDctWarpSmemBytes = 16 * (kZT2Units + kDStageUnits);
@@ -1566,16 +1546,20 @@ dct_zonal_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
       float2* const half = reinterpret_cast<float2*>(tb + 138 * p + j);
 #pragma unroll
       for (int tr = 0; tr < 2; ++tr) {
-        float2 xv[16], rv[16];
+        float2 xv[16];
 #pragma unroll
         for (int n = 0; n < 16; ++n) {
           const float2 m = make_float2(__uint_as_float(__byte_perm(word_of(X[tr], n >> 2), 0x4B000000u, 0x7440u | (n & 3))),
                                        __uint_as_float(__byte_perm(word_of(X[2 + tr], n >> 2), 0x4B000000u, 0x7440u | (n & 3))));
           xv[n] = __fadd2_rn(m, make_float2(-8388608.0f, -8388608.0f));
         }
-        dct16_fwd(xv, rv);
+#pragma unroll 1
+        for (int k = 0; k < 16; ++k) {
+          float2 y = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) half[2 * (8 * k + (k >> 1)) + tr] = rv[k];
+          for (int jj = 0; jj < 16; ++jj) y = __ffma2_rn(dct_c2(k, jj), xv[jj], y);
+          half[2 * (8 * k + (k >> 1)) + tr] = y;
+        }
       }
     }
     __syncwarp();
@@ -1595,22 +1579,28 @@ dct_zonal_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       float4* const line = tb + 138 * p + 17 * j + 8 * i;
-      float2 cv[16], y[16], uo[16];
+      float2 cv[16], uo[16];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const float4 v = line[q];
         cv[2 * q] = make_float2(v.x, v.y);
         cv[2 * q + 1] = make_float2(v.z, v.w);
+        uo[2 * q] = uo[2 * q + 1] = make_float2(0.f, 0.f);
       }
-      dct16_fwd(cv, y);
-#pragma unroll
+      // per coefficient u: B(u) = C(u, :) . column, the mask, then its
+      // contribution C(u, m) B'(u) to every output m (outer-product form)
+#pragma unroll 1
       for (int u = 0; u < 16; ++u) {
+        float2 y = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) y = __ffma2_rn(dct_c2(u, jj), cv[jj], y);
         if (!((keep >> (16 * i + u)) & 1u)) {
-          acc = __ffma2_rn(y[u], y[u], acc);
-          y[u] = make_float2(0.f, 0.f);
+          acc = __ffma2_rn(y, y, acc);
+          y = make_float2(0.f, 0.f);
         }
+#pragma unroll
+        for (int m = 0; m < 16; ++m) uo[m] = __ffma2_rn(dct_c2(u, m), y, uo[m]);
       }
-      dct16_inv(y, uo);
 #pragma unroll
       for (int q = 0; q < 8; ++q) line[q] = make_float4(uo[2 * q].x, uo[2 * q].y, uo[2 * q + 1].x, uo[2 * q + 1].y);
     }
@@ -1621,10 +1611,15 @@ dct_zonal_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     for (int tr = 0; tr < 2; ++tr) {
       const int rr = tr ^ jb1;
       const float2* const fin = reinterpret_cast<const float2*>(tb + 138 * p + j) + rr;
-      float2 v[16], z[16];
+      float2 z[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) v[c] = fin[2 * (8 * c + (c >> 1))];
-      dct16_inv(v, z);
+      for (int n = 0; n < 16; ++n) z[n] = make_float2(0.f, 0.f);
+#pragma unroll 1
+      for (int c = 0; c < 16; ++c) {
+        const float2 v = fin[2 * (8 * c + (c >> 1))];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) z[n] = __ffma2_rn(dct_c2(c, n), v, z[n]);
+      }
       unsigned oa[4], ob[4];
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
