@@ -195,6 +195,33 @@ def cpu_baseline(batch, budget_s):
             "sample": f"{len(done)} of 64 images x 8 r ({px / 1e6:.1f} Mpx) with the exact-integer oracle, {dt:.1f} s"}
 
 
+def _oracle_image_all_r(img):
+    """One image of the workload through the exact-integer oracle at every r
+    (a worker of cpu_baseline_all_cores)."""
+    import oracle as O
+
+    for r in R_SWEEP:
+        O.compress_zonal_exact(img, r)
+    return img.size * len(R_SWEEP)
+
+
+def cpu_baseline_all_cores(batch):
+    """The same oracle over the whole step (64 images x 8 r) with one process
+    per host core (spawned, each single-threaded), images distributed across
+    them: the oracle itself is unchanged."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_image_all_r, [batch[0]] * cores)  # start-up outside the timing
+        t0 = time.perf_counter()
+        px = sum(pool.imap_unordered(_oracle_image_all_r, list(batch)))
+        dt = time.perf_counter() - t0
+    return {"value": px / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"all {len(batch)} images x 8 r ({px / 1e6:.1f} Mpx), one spawned process per core, {dt:.1f} s"}
+
+
 def run_reference(args):
     """The CPU oracle on the same metric: each step compresses a strip of one
     512x512 image at all eight r, the strip height chosen so that the whole
@@ -250,6 +277,8 @@ def quant_phase(torch, atdct16, synth, dev, n_frames, steps, warmup, peak_gbs):
     HBM fraction of the quantisation kernel (4 bytes per sample: int16 in,
     int16 out), without and with the optional level output (+2 bytes per
     sample), row-major and zig-zag."""
+    import numpy as np
+
     frames = synth.residual_frames(n_frames)
     planes = [torch.from_numpy(p).to(dev) for fr in frames for p in fr]
     qps = synth.QUANT_QP_SWEEP
@@ -264,9 +293,10 @@ def quant_phase(torch, atdct16, synth, dev, n_frames, steps, warmup, peak_gbs):
     levels = torch.empty(samples, dtype=torch.int16, device=dev)
     res = {"frames": n_frames, "planes_per_qp": len(planes), "qps": list(qps), "samples_per_step": samples,
            "steps": steps}
+    sse = torch.empty(len(descs), dtype=torch.float64, device=dev)
     for tag, lv, plan in (("no_levels", None, rplan), ("levels", levels, rplan), ("levels_zigzag", levels, zplan)):
         for _ in range(max(warmup, 3)):
-            plan.compress_quant(descs, psnr, levels=lv)
+            plan.compress_quant(descs, psnr, levels=lv, sse=sse)
         torch.cuda.synchronize()
         plan.set_profiling(True)
         plan.profile()
@@ -284,6 +314,15 @@ def quant_phase(torch, atdct16, synth, dev, n_frames, steps, warmup, peak_gbs):
         res[tag] = {"ms_per_step": ms, "kernel_ms": k, "gsamples_s": samples / (ms / 1e3) / 1e9,
                     "kernel_gbs": byts / (k / 1e3) / 1e9, "kernel_frac_hbm": byts / (k / 1e3) / 1e9 / peak_gbs}
     res["mean_psnr_db"] = float(psnr.mean().item())
+    # residual SNR (signal energy of each plane over its reconstruction error), mean per QP
+    energy = [float(np.sum(p.astype(np.int64) ** 2)) for fr in frames for p in fr]
+    sse_h = sse.cpu().tolist()
+    psnr_h = psnr.cpu().tolist()
+    npl = len(planes)
+    res["by_qp"] = {str(qp): {"mean_psnr_db": sum(psnr_h[q * npl:(q + 1) * npl]) / npl,
+                              "mean_residual_snr_db": sum(10.0 * math.log10(energy[i] / sse_h[q * npl + i])
+                                                          for i in range(npl)) / npl}
+                    for q, qp in enumerate(qps)}
     rplan.close()
     zplan.close()
     return res
@@ -344,6 +383,56 @@ def coef_phase(torch, atdct16, batch, dev, peak_gbs, reps=50):
         plan.close()
     res["round_trips_exact"] = bool(exact)
     return res
+
+
+# --------------------------------------------------------------------------
+def _percentiles(v):
+    v = sorted(v)
+    q = lambda f: v[min(len(v) - 1, int(round(f * (len(v) - 1))))]
+    return {"p10": q(0.1), "p50": q(0.5), "p90": q(0.9)}
+
+
+def config1_phase(torch, atdct16, synth, dev, reps=200):
+    """One 256 x 256 u8 image (256 blocks): per-call latency of the forward to
+    int32 coefficients, the exact inverse and the fused zonal path (r = 36),
+    from CUDA events around each call; the round trip must be exact."""
+    img = synth.single_image_256()
+    x = torch.from_numpy(img).to(dev)
+    coef = torch.empty(img.size, dtype=torch.int32, device=dev)
+    out = torch.empty_like(x)
+    rec = torch.empty_like(x)
+    psnr = torch.empty(1, dtype=torch.float64, device=dev)
+    plan = atdct16.Plan(atdct16.U8, max_images=1)
+    desc = atdct16.descriptors([atdct16.image(x, rec, 36)])
+    calls = {"forward_us": lambda: plan.forward(x, coef), "inverse_us": lambda: plan.inverse(coef, out),
+             "zonal_r36_us": lambda: plan.compress_zonal(desc, psnr)}
+    res = {"image": "256x256 u8", "reps": reps}
+    for name, fn in calls.items():
+        for _ in range(5):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        res[name] = _percentiles([a.elapsed_time(b) * 1e3 for a, b in ev])
+    res["round_trip_exact"] = bool(torch.equal(out, x))
+    plan.close()
+    return res
+
+
+def psnr_u8_by_r(torch, atdct16, src, dst):
+    """PSNR of the stored u8 reconstructions (atdct16_psnr per image), mean per r."""
+    nr, n = src.shape[0], src.shape[1]
+    out = torch.empty(nr * n, dtype=torch.float64, device=src.device)
+    for k in range(nr):
+        for i in range(n):
+            atdct16.psnr(src[k, i], dst[k, i], out[k * n + i:k * n + i + 1])
+    torch.cuda.synchronize()
+    per = out.view(nr, n)
+    return {str(r): (float(per[k][~per[k].isinf()].mean()) if bool((~per[k].isinf()).any()) else float("inf"))
+            for k, r in enumerate(R_SWEEP)}
 
 
 # --------------------------------------------------------------------------
@@ -630,6 +719,14 @@ def run_ours(args):
     ms = e0.elapsed_time(e1) / args.steps
     launches, kernel_ms = plan.profile()
     plan.set_profiling(False)
+    # spread of the step time: 200 more steps with an event pair around each
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(200)]
+    for k, (a, b) in enumerate(evs):
+        a.record(stream)
+        plan.compress_zonal(sets[k % N_SETS][2], psnr)
+        b.record(stream)
+    torch.cuda.synchronize()
+    step_pct = _percentiles([a.elapsed_time(b) for a, b in evs])
     if dist:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -728,9 +825,14 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
+            "step_ms_percentiles": step_pct,
         }
         line["cpu_baseline"] = cpu_baseline(batch, args.cpu_seconds) if args.cpu_seconds > 0 else None
+        if args.cpu_seconds > 0:
+            line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(batch)
         if not args.no_extras:
+            line["config1"] = config1_phase(torch, atdct16, synth, dev)
+            line["psnr_u8_by_r"] = psnr_u8_by_r(torch, atdct16, sets[0][0], sets[0][1])
             line["coefficients"] = coef_phase(torch, atdct16, batch, dev, peak)
             line["ssim"] = ssim_phase(torch, atdct16, plan, sets[0][2], jobs, px_step)
             line["dct_baseline"] = dct_baseline_phase(torch, atdct16, plan, sets, jobs, px_step, None)

@@ -29,6 +29,8 @@
 //                which spreads the four blocks of a lane quad over all 32
 //                banks for the per-column accesses and keeps 16-byte
 //                chunks whole (XOR 16 moves a chunk, XOR 1 swaps within it).
+#include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -128,27 +130,31 @@ __device__ __forceinline__ int round_clamp(Z z) {
   return rne_div_u<kDen>((unsigned)n) + kLo;
 }
 
-template <class K, class... Args>
-cudaError_t launch_dyn(K kernel, int grid, int threads, int smem, cudaStream_t stream, Args... args) {
-  if (smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
+// Launch of a persistent kernel: min(SMs x resident CTAs per SM, CTAs the
+// work needs).  The per-SM residency (and the shared-memory opt-in it needs)
+// is worked out once per kernel and device and then cached, so a call costs
+// one launch on the host.
+template <auto kKernel, class... Args>
+cudaError_t launch_persistent(int threads, int smem, int num_sms, long long items_per_cta, long long items,
+                              cudaStream_t stream, Args... args) {
+  static std::atomic<int> per_sm_cache[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int per_sm = dev < 64 ? per_sm_cache[dev].load(std::memory_order_relaxed) : 0;
+  if (per_sm <= 0) {
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(kKernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kKernel, threads, smem) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    if (dev < 64) per_sm_cache[dev].store(per_sm, std::memory_order_relaxed);
   }
-  kernel<<<grid, threads, smem, stream>>>(args...);
+  const long long need = (items + items_per_cta - 1) / items_per_cta;
+  const long long g = std::max(1LL, std::min((long long)num_sms * per_sm, need));
+  kKernel<<<(int)g, threads, smem, stream>>>(args...);
   return cudaGetLastError();
-}
-
-template <class K>
-int persistent_grid(K kernel, int threads, int smem, int num_sms, long long work_items_per_cta_round,
-                    long long work_items) {
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
-  const long long need = (work_items + work_items_per_cta_round - 1) / work_items_per_cta_round;
-  long long g = (long long)num_sms * per_sm;
-  if (g > need) g = need;
-  return (int)(g < 1 ? 1 : g);
 }
 
 // ---------------------------------------------------------------------------
@@ -656,17 +662,15 @@ cudaError_t launch_forward(int dtype, const void* d_src, long long pitch, int w,
   if (ntiles >= (1LL << 31) - 4096) return cudaErrorInvalidValue;  // tile indices are 32-bit in the kernel
   const int smem = kCWarps * kCWarpSmemBytes, threads = 32 * kCWarps;
   const uint8_t* s = static_cast<const uint8_t*>(d_src);
-#define ATDCT16_FWD(D, Z)                                                                                \
-  return launch_dyn(coef_forward_kernel<D, Z>,                                                           \
-                    persistent_grid(coef_forward_kernel<D, Z>, threads, smem, num_sms, kCWarps, ntiles), \
-                    threads, smem, stream, s, pitch, w, h, d_coef)
-  if (dtype == 0) {
-    if (zigzag) ATDCT16_FWD(0, true);
-    ATDCT16_FWD(0, false);
-  }
-  if (zigzag) ATDCT16_FWD(1, true);
-  ATDCT16_FWD(1, false);
-#undef ATDCT16_FWD
+  if (dtype == 0)
+    return zigzag ? launch_persistent<coef_forward_kernel<0, true>>(threads, smem, num_sms, kCWarps, ntiles, stream, s,
+                                                                    pitch, w, h, d_coef)
+                  : launch_persistent<coef_forward_kernel<0, false>>(threads, smem, num_sms, kCWarps, ntiles, stream,
+                                                                     s, pitch, w, h, d_coef);
+  return zigzag ? launch_persistent<coef_forward_kernel<1, true>>(threads, smem, num_sms, kCWarps, ntiles, stream, s,
+                                                                  pitch, w, h, d_coef)
+                : launch_persistent<coef_forward_kernel<1, false>>(threads, smem, num_sms, kCWarps, ntiles, stream, s,
+                                                                   pitch, w, h, d_coef);
 }
 
 cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void* d_dst, long long pitch,
@@ -676,17 +680,15 @@ cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void*
   if (ntiles >= (1LL << 31) - 4096) return cudaErrorInvalidValue;
   const int smem = kCWarps * kCWarpSmemBytes, threads = 32 * kCWarps;
   uint8_t* d = static_cast<uint8_t*>(d_dst);
-#define ATDCT16_INV(D, Z)                                                                                \
-  return launch_dyn(coef_inverse_kernel<D, Z>,                                                           \
-                    persistent_grid(coef_inverse_kernel<D, Z>, threads, smem, num_sms, kCWarps, ntiles), \
-                    threads, smem, stream, d_coef, w, h, d, pitch)
-  if (dtype == 0) {
-    if (zigzag) ATDCT16_INV(0, true);
-    ATDCT16_INV(0, false);
-  }
-  if (zigzag) ATDCT16_INV(1, true);
-  ATDCT16_INV(1, false);
-#undef ATDCT16_INV
+  if (dtype == 0)
+    return zigzag ? launch_persistent<coef_inverse_kernel<0, true>>(threads, smem, num_sms, kCWarps, ntiles, stream,
+                                                                    d_coef, w, h, d, pitch)
+                  : launch_persistent<coef_inverse_kernel<0, false>>(threads, smem, num_sms, kCWarps, ntiles, stream,
+                                                                     d_coef, w, h, d, pitch);
+  return zigzag ? launch_persistent<coef_inverse_kernel<1, true>>(threads, smem, num_sms, kCWarps, ntiles, stream,
+                                                                  d_coef, w, h, d, pitch)
+                : launch_persistent<coef_inverse_kernel<1, false>>(threads, smem, num_sms, kCWarps, ntiles, stream,
+                                                                   d_coef, w, h, d, pitch);
 }
 
 cudaError_t launch_forward_1d(int dtype, const void* d_src, long long count, int32_t* d_coef, int num_sms,
@@ -695,10 +697,8 @@ cudaError_t launch_forward_1d(int dtype, const void* d_src, long long count, int
   const long long steps = (count + 31) / 32;
   const uint8_t* s = static_cast<const uint8_t*>(d_src);
   if (dtype == 0)
-    return launch_dyn(fwd1d_kernel<0>, persistent_grid(fwd1d_kernel<0>, 32 * k1dWarps, 0, num_sms, k1dWarps, steps),
-                      32 * k1dWarps, 0, stream, s, count, d_coef);
-  return launch_dyn(fwd1d_kernel<1>, persistent_grid(fwd1d_kernel<1>, 32 * k1dWarps, 0, num_sms, k1dWarps, steps),
-                    32 * k1dWarps, 0, stream, s, count, d_coef);
+    return launch_persistent<fwd1d_kernel<0>>(32 * k1dWarps, 0, num_sms, k1dWarps, steps, stream, s, count, d_coef);
+  return launch_persistent<fwd1d_kernel<1>>(32 * k1dWarps, 0, num_sms, k1dWarps, steps, stream, s, count, d_coef);
 }
 
 cudaError_t launch_inverse_1d(int dtype, const int32_t* d_coef, long long count, void* d_dst, int num_sms,
@@ -707,10 +707,8 @@ cudaError_t launch_inverse_1d(int dtype, const int32_t* d_coef, long long count,
   const long long steps = (count + 31) / 32;
   uint8_t* d = static_cast<uint8_t*>(d_dst);
   if (dtype == 0)
-    return launch_dyn(inv1d_kernel<0>, persistent_grid(inv1d_kernel<0>, 32 * k1dWarps, 0, num_sms, k1dWarps, steps),
-                      32 * k1dWarps, 0, stream, d_coef, count, d);
-  return launch_dyn(inv1d_kernel<1>, persistent_grid(inv1d_kernel<1>, 32 * k1dWarps, 0, num_sms, k1dWarps, steps),
-                    32 * k1dWarps, 0, stream, d_coef, count, d);
+    return launch_persistent<inv1d_kernel<0>>(32 * k1dWarps, 0, num_sms, k1dWarps, steps, stream, d_coef, count, d);
+  return launch_persistent<inv1d_kernel<1>>(32 * k1dWarps, 0, num_sms, k1dWarps, steps, stream, d_coef, count, d);
 }
 
 }  // namespace atdct16

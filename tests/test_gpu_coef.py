@@ -165,6 +165,16 @@ def test_large_image_sampled_and_round_trip(torch, cplan):
         assert np.array_equal(c[by, bx], ref)
 
 
+@pytest.mark.parametrize("shape", [(16, 32768), (4096, 16)])
+def test_extreme_shapes(torch, cplan, shape):
+    img = synth.ar1_image(*shape, 0.95, 71)
+    got = run_forward(torch, cplan, img, atdct16.U8)
+    y = O.forward_int(img)
+    assert np.array_equal(got, layout(cplan, y))
+    back = run_inverse(torch, cplan, got, *shape, atdct16.U8)
+    assert np.array_equal(back, img)
+
+
 # ----------------------------------------------------------- 1-D transforms ---
 @pytest.mark.parametrize("count", [1, 31, 33, 1000])
 def test_forward_inverse_1d(torch, cplan, count):

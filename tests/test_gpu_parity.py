@@ -181,6 +181,16 @@ def test_zonal_random_sizes(torch, plan):
         check_zonal(img, r, out, p, s)
 
 
+def test_zonal_extreme_shapes(torch, plan):
+    # one 16-row strip of 256 tiles, one 16-pixel column of 256 one-block tiles,
+    # and a single block, in one call
+    imgs = [synth.ar1_image(16, 32768, 0.95, 61), synth.ar1_image(4096, 16, 0.95, 62), synth.ar1_image(16, 16, 0.9, 63)]
+    rs = [36, 100, 6]
+    outs, psnr, sse = run_zonal(torch, plan, imgs, rs)
+    for img, r, out, p, s in zip(imgs, rs, outs, psnr, sse):
+        check_zonal(img, r, out, p, s)
+
+
 # ------------------------------------------- zonal, full 64 x 512 x 512 ---
 def test_zonal_full_batch_sampled(torch, plan):
     batch = synth.image_batch_512(64)
