@@ -10,6 +10,7 @@
 #include "../../include/atdct16.h"
 #include "atdct16_butterfly.cuh"
 #include "atdct16_internal.h"
+#include "atdct16_zigzag.cuh"
 
 using namespace atdct16;
 
@@ -54,18 +55,11 @@ struct atdct16_plan_st {
 
 namespace {
 
-// Zig-zag rank of (u, v) for 16x16 (Sec. 4, JPEG convention extended):
-// anti-diagonal s = u + v; even s scanned with u decreasing, odd s with v
-// decreasing.
+// Zig-zag rank of every (u, v) (Sec. 4): the inverse of the scan.
 void zigzag_rank16(int rank[16][16]) {
-  int idx = 0;
-  for (int s = 0; s <= 30; ++s) {
-    const int lo = s > 15 ? s - 15 : 0, hi = s < 15 ? s : 15;
-    if (s % 2 == 0) {
-      for (int u = hi; u >= lo; --u) rank[u][s - u] = idx++;
-    } else {
-      for (int v = hi; v >= lo; --v) rank[s - v][v] = idx++;
-    }
+  for (int k = 0; k < 256; ++k) {
+    const int w = zigzag_word(k);
+    rank[w >> 4][w & 15] = k;
   }
 }
 

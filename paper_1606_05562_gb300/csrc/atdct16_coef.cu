@@ -37,6 +37,7 @@
 
 #include "atdct16_butterfly.cuh"
 #include "atdct16_internal.h"
+#include "atdct16_zigzag.cuh"
 
 namespace atdct16 {
 namespace {
@@ -55,25 +56,10 @@ static_assert(w_of(0) == 3 && w_of(2) == 4 && w_of(3) == 6 && w_of(15) == 4, "W 
 
 __device__ __forceinline__ int bswz(int b) { return (b & 1) | ((b & 2) << 3); }
 
-// (16 u + v) of scan position k of the zig-zag order of Sec. 4 (JPEG
-// convention extended to 16x16): anti-diagonal s = u + v, even s walked
-// with u decreasing, odd s with v decreasing.
-__device__ int zz_word(int k) {
-  int s = 0, base = 0;
-  while (s < 30) {
-    const int len = s < 16 ? s + 1 : 31 - s;
-    if (k < base + len) break;
-    base += len;
-    ++s;
-  }
-  const int off = k - base, hi = s < 16 ? s : 15;
-  const int a = hi - off, b = s - a;
-  return (s & 1) ? 16 * b + a : 16 * a + b;
-}
 // Four consecutive scan positions k .. k+3, one byte each.
 __device__ unsigned zz_pack4(int k) {
-  return (unsigned)zz_word(k) | ((unsigned)zz_word(k + 1) << 8) | ((unsigned)zz_word(k + 2) << 16) |
-         ((unsigned)zz_word(k + 3) << 24);
+  return (unsigned)zigzag_word(k) | ((unsigned)zigzag_word(k + 1) << 8) | ((unsigned)zigzag_word(k + 2) << 16) |
+         ((unsigned)zigzag_word(k + 3) << 24);
 }
 __device__ __forceinline__ int zz_byte(unsigned packed, int e) { return (packed >> (8 * e)) & 0xff; }
 

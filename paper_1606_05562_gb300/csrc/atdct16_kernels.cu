@@ -25,6 +25,7 @@
 
 #include "atdct16_butterfly.cuh"
 #include "atdct16_internal.h"
+#include "atdct16_zigzag.cuh"
 
 #include <atomic>
 #include <cmath>
@@ -889,19 +890,6 @@ struct QuantTile {
 // and the warp stores each block as one 512-byte run, gathered in zig-zag
 // order (Sec. 4 scan) when kZigzag.  The copy of the tile after next into
 // that slot starts after the levels have left.
-__device__ int zz_word16(int k) {  // (16 u + v) of zig-zag scan position k
-  int s = 0, base = 0;
-  while (s < 30) {
-    const int len = s < 16 ? s + 1 : 31 - s;
-    if (k < base + len) break;
-    base += len;
-    ++s;
-  }
-  const int off = k - base, hi = s < 16 ? s : 15;
-  const int a = hi - off, b = s - a;  // even s: u = a (decreasing); odd s: v = a (decreasing)
-  return (s & 1) ? 16 * b + a : 16 * a + b;
-}
-
 template <bool kLevels, bool kZigzag>
 __global__ void __launch_bounds__(128, 3)
 quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
@@ -1019,7 +1007,7 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
   unsigned zzl[2] = {0u, 0u};
   if (kLevels && kZigzag) {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) zzl[e >> 2] |= (unsigned)zz_word16(8 * lane + e) << (8 * (e & 3));
+    for (int e = 0; e < 8; ++e) zzl[e >> 2] |= (unsigned)zigzag_word(8 * lane + e) << (8 * (e & 3));
   }
   while (true) {
     cp_async_wait<1>();
