@@ -68,8 +68,8 @@ cudaError_t launch_psnr_finalize(const ImageJob* d_jobs, int njobs, long long nt
 // Exact-DCT baseline of the fused zonal path (same tiles and table as zonal).
 cudaError_t launch_zonal_dct(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
                              float* d_tile_sse, int* d_status, int num_sms, cudaStream_t stream);
-// SSIM tiles: 30 x 128 window positions of an image's (h - 10) x (w - 10) map.
-constexpr int kSsimTileRows = 30, kSsimTileCols = 128;
+// SSIM tiles: 20 x 128 window positions of an image's (h - 10) x (w - 10) map.
+constexpr int kSsimTileRows = 20, kSsimTileCols = 128;
 cudaError_t launch_ssim(const ImageJob* d_jobs, int njobs, long long ntiles, float* d_tile_sum, double* d_out,
                         int* d_status, int num_sms, cudaStream_t stream);
 // Coefficient pipeline (atdct16_coef.cu): 2-D forward / exact inverse over

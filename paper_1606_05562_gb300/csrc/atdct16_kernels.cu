@@ -1175,15 +1175,16 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
 // positions of the 11x11 Gaussian window (sigma 1.5) of
 //   (2 mu_a mu_b + C1)(2 s_ab + C2) / ((mu_a^2 + mu_b^2 + C1)(s_a^2 + s_b^2 + C2)).
 // The window is separable: the 2-D normalised Gaussian is the outer product
-// of the 1-D normalised one (kSsimW).  One CTA per tile of 30 x 128 window
-// positions, in two passes over the five moments of the centred pixels
+// of the 1-D normalised one (kSsimW).  One CTA per tile of 20 x 128 window
+// positions (65 KB of shared memory, three CTAs per SM), in two passes over
+// the five moments of the centred pixels
 // (a, b, a^2, b^2, ab with a = x - 128, which keeps the moment form
 // E[xy] - E[x]E[y] well conditioned in FP32), (a, b) and (a^2, b^2) as
 // packed pairs (one f32x2 instruction per pair):
-//   input       the tile's 40 x 138 pixels of both images, copied to shared
+//   input       the tile's 30 x 138 pixels of both images, copied to shared
 //               memory with cp.async; the next tile's copy starts as soon as
 //               the vertical pass has read this one;
-//   vertical    thread c (< 138) walks column x0 + c down the 40 input rows
+//   vertical    thread c (< 138) walks column x0 + c down the 30 input rows
 //               with 11 running sums per moment in registers (row r adds
 //               w_k f(r) to output row r - k; output row r - 10 is then
 //               complete), into the moment planes;
@@ -1200,7 +1201,7 @@ constexpr int kSsimIS = 144;            // bytes per staged input row (9 chunks 
 constexpr int kSsimVS2 = 142;           // row stride of a pair plane (float2): 71 chunks
 constexpr int kSsimVS1 = 140;           // row stride of the ab plane (float): 35 chunks
 constexpr int kSsimThreads = 160;
-static_assert(kSsimTR == 30 && kSsimTC == 128, "the loops below are written for 30 x 128 tiles");
+static_assert(kSsimTC == 128, "the horizontal pass is written for 128-column tiles");
 __constant__ float kSsimW[11];
 
 struct alignas(16) SsimSmem {
@@ -1238,7 +1239,7 @@ __device__ __forceinline__ SsimTile ssim_tile(const ImageJob* __restrict__ jobs,
   return T;
 }
 
-// cp.async of a tile's input rows: 2 images x 40 rows x 9 chunks of 16 bytes;
+// cp.async of a tile's input rows: 2 images x 30 rows x 9 chunks of 16 bytes;
 // chunks past the image (width and pitch are multiples of 16) are zero-filled.
 __device__ __forceinline__ void ssim_issue(SsimSmem& sm, const SsimTile& T, int tid) {
   for (int i = tid; i < 2 * kSsimIR * 9; i += kSsimThreads) {
@@ -1251,7 +1252,7 @@ __device__ __forceinline__ void ssim_issue(SsimSmem& sm, const SsimTile& T, int 
   cp_async_commit();
 }
 
-__global__ void __launch_bounds__(kSsimThreads, 2)
+__global__ void __launch_bounds__(kSsimThreads, 3)
 ssim_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles, float* __restrict__ tile_sum,
             int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char ssmem[];
