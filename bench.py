@@ -752,7 +752,7 @@ def run_ours(args):
     # are in flight: step k's results go back over the host link while step k+1
     # uploads and computes (separate copy streams, double-buffered device and host
     # buffers, ordered by events).  The serial figure (one step at a time on one
-    # stream) is reported beside it.
+    # stream) and a PSNR-only readback are reported beside it.
     h_src = torch.from_numpy(batch).pin_memory()
     d_src2 = [torch.empty_like(base) for _ in range(2)]
     d_dst2 = [torch.empty((nr, N_IMAGES, SIDE, SIDE), dtype=torch.uint8, device=dev) for _ in range(2)]
@@ -766,7 +766,7 @@ def run_ours(args):
     ev_cmp = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_step(k, pipelined=True):
+    def e2e_step(k, pipelined=True, images_back=True):
         b = k & 1 if pipelined else 0
         si, sc, so = (s_in, s_cmp, s_out) if pipelined else (stream, stream, stream)
         si.wait_event(ev_cmp[b])  # step k - 2's kernel has read d_src2[b]
@@ -779,19 +779,20 @@ def run_ours(args):
         ev_cmp[b].record(sc)
         so.wait_event(ev_cmp[b])
         with torch.cuda.stream(so):
-            h_dst2[b].copy_(d_dst2[b], non_blocking=True)
+            if images_back:
+                h_dst2[b].copy_(d_dst2[b], non_blocking=True)
             h_psnr2[b].copy_(psnr2[b], non_blocking=True)
         ev_out[b].record(so)
 
-    def e2e_run(pipelined):
+    def e2e_run(pipelined, images_back=True):
         for k in range(3):
-            e2e_step(k, pipelined)
+            e2e_step(k, pipelined, images_back)
         torch.cuda.synchronize()
         barrier()
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record(s_in if pipelined else stream)
         for k in range(args.e2e_steps):
-            e2e_step(k, pipelined)
+            e2e_step(k, pipelined, images_back)
         t1.record(s_out if pipelined else stream)
         torch.cuda.synchronize()
         e_ms = t0.elapsed_time(t1) / args.e2e_steps
@@ -804,6 +805,7 @@ def run_ours(args):
     e2e = None
     if args.e2e_steps > 0:
         serial_ms = e2e_run(False)
+        metric_ms = e2e_run(True, images_back=False)
         e2e_ms = e2e_run(True)
         ok = torch.equal(h_dst2[0], h_dst2[1]) and bool((h_psnr2[0] == h_psnr2[1]).all())
         e2e = {"value": world * px_step / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
@@ -811,7 +813,11 @@ def run_ours(args):
                "ms_per_step": e2e_ms, "steps_in_flight": 2, "serial_ms_per_step": serial_ms,
                "serial_value": world * px_step / (serial_ms / 1e3) / 1e9,
                "link_gbs": (h_src.numel() + h_dst2[0].numel() + 8 * jobs) / (e2e_ms / 1e3) / 1e9,
-               "results_consistent": ok}
+               "results_consistent": ok,
+               # the same pipeline reading back only the per-image PSNR (the reconstructions stay
+               # in device memory, e.g. for a following device-side consumer)
+               "psnr_only": {"value": world * px_step / (metric_ms / 1e3) / 1e9, "ms_per_step": metric_ms,
+                             "h2d_bytes_per_step": int(h_src.numel()), "d2h_bytes_per_step": int(8 * jobs)}}
 
     if rank == 0:
         line = {
