@@ -12,7 +12,11 @@ Everything here follows the paper's definitions directly:
   ``A' = C_hat^T B' C_hat`` (Sec. 4, image-compression procedure).
 * ``S`` absorbed into a uniform scalar quantiser (Sec. 2, last paragraph;
   Sec. 5.3 sweeps the HEVC quantisation point).
-* PSNR (Sec. 4), and the similarity / coding measures of Sec. 3 (Table 2).
+* PSNR (Sec. 4), SSIM (Sec. 4, the Wang et al. 2004 measure the paper cites) and the
+  APE of Sec. 4, and the similarity / coding measures of Sec. 3 (Table 2).
+* The 1-D transform ``y = T x`` and its exact inverse ``rne(T^T (W y) / 48)``
+  (Sec. 2), and the zig-zag block layout (entry k of a block = scan position k,
+  Sec. 4) of coefficients and quantisation levels.
 
 The fast factorisation ``T = P2 M4 M3 M2 P1 M1`` (Sec. 2, Eq. of the
 factorisation) is recorded here only so that tests can check that the printed
