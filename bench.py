@@ -269,7 +269,7 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
-def quant_phase(torch, atdct16, synth, dev, n_frames, steps, warmup, peak_gbs):
+def quant_phase(torch, atdct16, synth, dev, n_frames, steps, warmup, peak_gbs, cpu_oracle=False):
     """4:2:0 int16 residual frames (1920x1088 luma + two 960x544 chroma
     planes, Laplace(0, 6) with 30 % zeros, seed 3), every plane quantised at
     each QP in {22, 27, 32, 37} in one call: the first n_frames frames of the
@@ -314,6 +314,15 @@ def quant_phase(torch, atdct16, synth, dev, n_frames, steps, warmup, peak_gbs):
         res[tag] = {"ms_per_step": ms, "kernel_ms": k, "gsamples_s": samples / (ms / 1e3) / 1e9,
                     "kernel_gbs": byts / (k / 1e3) / 1e9, "kernel_frac_hbm": byts / (k / 1e3) / 1e9 / peak_gbs}
     res["mean_psnr_db"] = float(psnr.mean().item())
+    if cpu_oracle:
+        # the oracle (FP32-decision mode) on one 1920x1088 luma plane at QP 27
+        import oracle as O
+
+        t0 = time.perf_counter()
+        O.compress_quant(frames[0][0], 27, precision="fp32")
+        dt = time.perf_counter() - t0
+        res["cpu_oracle"] = {"gsamples_s": frames[0][0].size / dt / 1e9, "cores": 1,
+                             "sample": "one 1920x1088 luma plane at QP 27, FP32-decision oracle"}
     # residual SNR (signal energy of each plane over its reconstruction error), mean per QP
     energy = [float(np.sum(p.astype(np.int64) ** 2)) for fr in frames for p in fr]
     sse_h = sse.cpu().tolist()
@@ -504,7 +513,7 @@ def dct_baseline_phase(torch, atdct16, plan, sets, n_jobs, px, psnr_approx, step
 
 
 # --------------------------------------------------------------------------
-def mixed_batch_phase(torch, atdct16, synth, dev, n_images, seed=4):
+def mixed_batch_phase(torch, atdct16, synth, dev, n_images, seed=4, cpu_oracle=False):
     """1000 mixed-size u8 AR(1) images (sides log-uniform in [128, 4096],
     multiples of 16, rho in [0.8, 0.97]), zonal r = 36: per-image launches of
     the plain entry point against one autotuned CUDA-graph launch of the
@@ -574,6 +583,18 @@ def mixed_batch_phase(torch, atdct16, synth, dev, n_images, seed=4):
            "graph_batch_gpx_s": total / (ms_b / 1e3) / 1e9,
            "graph_batch_gbs": 2.0 * total / (ms_b / 1e3) / 1e9,
            "speedup": ms_a / ms_b, "identical_results": same, "autotune_s": tune_s, "tuned": info}
+    if cpu_oracle:
+        # the exact-integer oracle on the first images of the set, up to about 8 Mpx
+        import oracle as O
+
+        t0, px = time.perf_counter(), 0
+        for s_img in srcs:
+            if px > 8_000_000:
+                break
+            O.compress_zonal_exact(s_img.cpu().numpy(), r)
+            px += s_img.numel()
+        dt = time.perf_counter() - t0
+        out["cpu_oracle"] = {"gpx_s": px / dt / 1e9, "cores": 1, "sample": f"first images of the set, {px / 1e6:.1f} Mpx"}
     del fields, src_all, dst_a, dst_b
     return out
 
@@ -844,9 +865,11 @@ def run_ours(args):
             line["dct_baseline"] = dct_baseline_phase(torch, atdct16, plan, sets, jobs, px_step, None)
             del sets
             torch.cuda.empty_cache()
-            line["quant"] = quant_phase(torch, atdct16, synth, dev, args.quant_frames, 20, 3, peak)
+            line["quant"] = quant_phase(torch, atdct16, synth, dev, args.quant_frames, 20, 3, peak,
+                                        cpu_oracle=args.cpu_seconds > 0)
             torch.cuda.empty_cache()
-            line["mixed_batch"] = mixed_batch_phase(torch, atdct16, synth, dev, args.mixed_images)
+            line["mixed_batch"] = mixed_batch_phase(torch, atdct16, synth, dev, args.mixed_images,
+                                                    cpu_oracle=args.cpu_seconds > 0)
             torch.cuda.empty_cache()
             rates = [float(v) for v in args.serve_rates.split(",") if v]
             line["serving"] = serving_phase(torch, atdct16, synth, rates)
