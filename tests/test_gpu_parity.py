@@ -259,6 +259,39 @@ def test_quant_video_frame_full_size(torch, qplan):
         off += plane.size
 
 
+@pytest.mark.parametrize("zigzag", [False, True], ids=["rowmajor", "zigzag"])
+def test_quant_bench_configuration_sampled(torch, zigzag):
+    # the bench's quantisation call: 24 4:2:0 frames, every plane at QP 22, 27,
+    # 32 and 37 in one launch with levels; sampled planes against the oracle
+    frames = synth.residual_frames(24)
+    planes = [p for fr in frames for p in fr]
+    qps = synth.QUANT_QP_SWEEP
+    dev_in = [torch.from_numpy(p).cuda() for p in planes]
+    outs = [[torch.empty_like(x) for x in dev_in] for _ in qps]
+    descs = [atdct16.image(x, o, qp) for qp, oo in zip(qps, outs) for x, o in zip(dev_in, oo)]
+    plan = atdct16.Plan(atdct16.I16, max_images=len(descs), workspace_bytes=1 << 30, zigzag=zigzag)
+    nlev = sum(p.size for p in planes) * len(qps)
+    levels = torch.empty(nlev, dtype=torch.int16, device="cuda")
+    psnr = torch.empty(len(descs), dtype=torch.float64, device="cuda")
+    plan.compress_quant(descs, psnr, levels=levels)
+    torch.cuda.synchronize()
+    assert plan.last_device_status() == atdct16.OK
+    offs = np.cumsum([0] + [p.size for p in planes] * len(qps))
+    for q, pi in ((0, 0), (3, 34), (2, 69), (1, 70)):
+        k = q * len(planes) + pi
+        plane = planes[pi]
+        ref = O.compress_quant(plane, qps[q], precision="fp32")
+        lev = levels[offs[k]:offs[k + 1]].cpu().numpy()
+        want = O.to_zigzag(ref["levels"]).reshape(-1) if zigzag else ref["levels"].reshape(-1)
+        assert np.array_equal(lev, want), f"plane {pi} QP {qps[q]}: levels differ"
+        rec = ref["recon"]
+        near_tie = np.abs(np.abs(rec - np.floor(rec)) - 0.5) < 2e-3
+        diff = outs[q][pi].cpu().numpy().astype(np.int64) - ref["recon_i16"].astype(np.int64)
+        assert np.all(np.abs(diff) <= 1) and np.all(diff[~near_tie] == 0)
+        assert psnr[k].item() == pytest.approx(ref["psnr"], rel=PSNR_RTOL, abs=PSNR_ATOL)
+    plan.close()
+
+
 # --------------------------------------------------------------- PSNR ---
 def test_psnr_pair(torch):
     a = synth.ar1_image(64, 80, 0.9, 1)
