@@ -3,6 +3,8 @@
 with the CPU oracle, through the C ABI.  Everything here is integer work and
 must match bit for bit."""
 
+import functools
+
 import numpy as np
 import pytest
 
@@ -144,11 +146,17 @@ def test_round_trip(torch, cplan, dtype):
     assert np.array_equal(out.cpu().numpy(), x)
 
 
+@functools.lru_cache(maxsize=1)
+def _big_image():
+    return synth.ar1_image(4096, 8192, 0.95, 21)
+
+
 def test_large_image_sampled_and_round_trip(torch, cplan):
-    # 2048 x 4096 (8 MiB in, 32 MiB of coefficients): sampled blocks against
-    # the oracle, and the exact round trip over the whole image
-    h, w = 2048, 4096
-    x = synth.ar1_image(h, w, 0.95, 21)
+    # the bench's coefficient workload shape, 4096 x 8192 (32 MiB in, 128 MiB
+    # of coefficients): sampled blocks against the oracle, and the exact round
+    # trip over the whole image
+    h, w = 4096, 8192
+    x = _big_image()
     xd = dev(torch, x)
     coef = torch.empty(h * w, dtype=torch.int32, device="cuda")
     cplan.forward(xd, coef)
