@@ -82,12 +82,22 @@ __device__ __forceinline__ float2 rne_denormal(float2 x) {
 // is within 6e-5 of Z / 2304 otherwise, far inside the 1/2304 gap to any .5.
 __constant__ float kInv2304 = 1.0f / 2304.0f;
 
+// The job holding tile t: the last job with tile_begin <= t (tile_begin is
+// increasing and jobs[0].tile_begin = 0).  A 32-way search by the whole warp:
+// each round the lanes probe 32 evenly spaced jobs of the remaining range in
+// parallel, so 512 jobs take two rounds of loads instead of nine dependent
+// ones.  Every lane of the warp must call it; all get the same job.
 __device__ __forceinline__ void warp_find_job(const ImageJob* __restrict__ jobs, int njobs,
                                               long long t, int& job) {
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(&jobs[mid].tile_begin) <= t) lo = mid; else hi = mid - 1;
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = njobs;  // the job is in [lo, hi), jobs[lo].tile_begin <= t
+  while (hi - lo > 1) {
+    const int step = (hi - lo + 31) >> 5;
+    const int idx = lo + lane * step;
+    const bool le = idx < hi && __ldg(&jobs[idx].tile_begin) <= t;
+    const unsigned m = __ballot_sync(0xffffffffu, le);  // bit 0 is always set
+    lo += (31 - __clz(m)) * step;
+    hi = min(hi, lo + step);
   }
   job = lo;
 }
