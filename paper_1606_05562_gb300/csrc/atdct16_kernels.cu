@@ -83,7 +83,17 @@ __device__ __forceinline__ float2 rne_denormal(float2 x) {
 __constant__ float kInv2304 = 1.0f / 2304.0f;
 
 // The job holding tile t: the last job with tile_begin <= t (tile_begin is
-// increasing and jobs[0].tile_begin = 0).  A 32-way search by the whole warp:
+// increasing and jobs[0].tile_begin = 0), by binary search.
+__device__ __forceinline__ void find_job(const ImageJob* __restrict__ jobs, int njobs, long long t, int& job) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&jobs[mid].tile_begin) <= t) lo = mid; else hi = mid - 1;
+  }
+  job = lo;
+}
+
+// The same job as a 32-way search by the whole warp:
 // each round the lanes probe 32 evenly spaced jobs of the remaining range in
 // parallel, so 512 jobs take two rounds of loads instead of nine dependent
 // ones.  Every lane of the warp must call it; all get the same job.
@@ -1232,7 +1242,7 @@ struct SsimTile {
 __device__ __forceinline__ SsimTile ssim_tile(const ImageJob* __restrict__ jobs, int njobs, long long t) {
   SsimTile T;
   int job = 0;
-  warp_find_job(jobs, njobs, t, job);
+  find_job(jobs, njobs, t, job);
   const ImageJob* J = jobs + job;
   const long long tb = __ldg(&J->tile_begin);
   T.w = __ldg(&J->width);
@@ -1450,7 +1460,7 @@ dct_zonal_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
   uint8_t* dst_band = nullptr;
   auto enter = [&](int t) -> bool {
     int job;
-    warp_find_job(jobs, njobs, t, job);
+    find_job(jobs, njobs, t, job);
     const ImageJob* J = jobs + job;
     const long long tb0 = __ldg(&J->tile_begin);
     tiles_x = __ldg(&J->tiles_x);
