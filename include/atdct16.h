@@ -25,7 +25,7 @@
  *   Within a block the coefficient index is (u, v), u = vertical frequency
  *   (row of T applied to the block's columns), v = horizontal frequency:
  *       Y[u][v] = sum_m sum_n T[u][m] X[m][n] T[v][n].
- * - Zig-zag order (Sec. 4, "adapting the zigzag sequence"): the JPEG
+ * - Zig-zag order (Sec. 4 adapts the 8x8 JPEG scan to 16x16): the JPEG
  *   convention extended to 16x16: anti-diagonals s = u + v; on even s the
  *   scan runs with u decreasing, on odd s with v decreasing.
  * - Every compute call is asynchronous on the given stream and allocates

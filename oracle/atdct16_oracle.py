@@ -36,7 +36,7 @@ Readings of points the paper leaves open:
 
 * Block orientation: ``A`` is indexed [row m][column n];
   ``Y[u, v] = sum_m sum_n T[u, m] A[m, n] T[v, n]`` (u = vertical frequency).
-* Zig-zag for 16x16 (Sec. 4 "adapting the zigzag sequence"): the JPEG
+* Zig-zag for 16x16 (Sec. 4 adapts the 8x8 scan without spelling it out): the JPEG
   convention extended to 16x16.  Anti-diagonal s = u + v; on even s the scan
   runs with u decreasing, on odd s with v decreasing.
 * PSNR is computed on the unrounded, unclipped reconstruction; the stored
