@@ -184,8 +184,8 @@ def factor_m4() -> np.ndarray:
 
 
 # The printed cycle notation of P2 is garbled (each cycle repeats its first
-# element).  Reading: the cycles (1 8)(2 4 3 11 10 7 12)(5 9 13 14 6), acting as
-# "row i of T is row p(i) of M4 M3 M2 P1 M1".
+# element).  Reading: the cycles (1 8)(2 4 3 11 10 7 12)(5 9 13 14 6), acting so
+# that row i of T is row p(i) of M4 M3 M2 P1 M1.
 P2_ROW_SOURCE = (0, 8, 4, 11, 3, 9, 5, 12, 1, 13, 7, 10, 2, 14, 6, 15)
 
 
