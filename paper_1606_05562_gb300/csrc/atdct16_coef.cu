@@ -517,6 +517,179 @@ coef_inverse_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __r
   }
 }
 
+// Row-major exact inverse with the next tile's coefficients copied in while
+// the current one is inverted.  The block stage holds the tile's 8 blocks with
+// 16-byte chunk q of block b at q ^ 2 (b & 3) (word XOR 8 (b & 3)), so that
+// cp.async can fill it directly and each lane reads its two columns as 8-byte
+// pairs without bank conflicts.  After a tile's pairs are in registers the
+// stage is free and the next copy starts; a tile that needs the split route
+// keeps the stage for its low halves and starts the copy when it is done.
+__device__ __forceinline__ void cp_async16_rm(void* smem_dst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+
+template <int kDtype>
+__global__ void __launch_bounds__(32 * kCWarps, 3)
+coef_inverse_rm_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __restrict__ dst, long long pitch) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = lane & 3, j = lane >> 2, jb1 = (j >> 1) & 1;
+  float4* const line = reinterpret_cast<float4*>(csm + warp * kCWarpSmemBytes);
+  int* const stage = reinterpret_cast<int*>(line + kCLineUnits);
+  uint4* const stage4 = reinterpret_cast<uint4*>(stage);
+  const int s8 = 8 * p;  // word XOR of blocks p and p + 4
+  const int wc[2] = {w_of(2 * j), w_of(2 * j + 1)};
+  constexpr int kElem = kDtype == 0 ? 1 : 2;
+  const int tiles_x = (w + kTileW - 1) / kTileW;
+  const int ntiles = tiles_x * (h >> 4);
+  const int bpr = w >> 4;
+  const int stride = gridDim.x * kCWarps;
+  auto issue = [&](int t) {
+    if (t < ntiles) {
+      const int ty = t / tiles_x, tx = t - ty * tiles_x;
+      const int nb = min(8, (w - tx * kTileW) >> 4);
+      const int32_t* const in = coef + ((long long)ty * bpr + tx * 8) * 256;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int b = m >> 1, q = 32 * (m & 1) + lane;
+        if (b < nb) cp_async16_rm(stage4 + 64 * b + (q ^ (2 * (b & 3))), in + 256 * b + 4 * q);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  issue(blockIdx.x * kCWarps + warp);
+  for (int t = blockIdx.x * kCWarps + warp; t < ntiles; t += stride) {
+    const int ty = t / tiles_x, tx = t - ty * tiles_x;
+    const int nb = min(8, (w - tx * kTileW) >> 4);
+    const bool va = p < nb, vb = p + 4 < nb;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    // the lane's columns 2j, 2j+1 of blocks p, p + 4 as (Y(u, 2j), Y(u, 2j+1)) pairs
+    int2 ya[16], yb[16];
+    unsigned big = 0u;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int wd = (16 * u + 2 * j) ^ s8;
+      ya[u] = *reinterpret_cast<const int2*>(stage + 256 * p + wd);
+      yb[u] = *reinterpret_cast<const int2*>(stage + 256 * (p + 4) + wd);
+      if (va) big |= ((unsigned)ya[u].x + (1u << 18)) | ((unsigned)ya[u].y + (1u << 18));
+      if (vb) big |= ((unsigned)yb[u].x + (1u << 18)) | ((unsigned)yb[u].y + (1u << 18));
+    }
+    const bool wide = __any_sync(0xffffffffu, big >= (1u << 19));
+    uint8_t* const drow = dst + (long long)(ty * kTileH + 2 * j) * pitch + (long long)(tx * kTileW + 16 * p) * kElem;
+    __syncwarp();  // every lane has its pairs: the stage may be refilled
+    if (!wide) {
+      issue(t + stride);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        int da[16], db[16], ua[16], ub[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int f = w_of(u) * wc[i];
+          da[u] = (i ? ya[u].y : ya[u].x) * f;
+          db[u] = (i ? yb[u].y : yb[u].x) * f;
+        }
+        inv16(da, ua);
+        inv16(db, ub);
+        float4* const ln = line + 138 * p + 17 * j + 8 * i;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          ln[q] = make_float4(__int_as_float(ua[2 * q]), __int_as_float(ub[2 * q]), __int_as_float(ua[2 * q + 1]),
+                              __int_as_float(ub[2 * q + 1]));
+      }
+      __syncwarp();
+#pragma unroll
+      for (int tr = 0; tr < 2; ++tr) {
+        const int rr = tr ^ jb1;
+        const float2* const fin = reinterpret_cast<const float2*>(line + 138 * p + j) + rr;
+        int ra[16], rb[16], za[16], zb[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float2 x = fin[2 * (8 * c + (c >> 1))];
+          ra[c] = __float_as_int(x.x);
+          rb[c] = __float_as_int(x.y);
+        }
+        inv16(ra, za);
+        inv16(rb, zb);
+        int qa[16], qb[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) round_pair<kDtype>(za[n], zb[n], qa[n], qb[n]);
+        store_row<kDtype>(drow + rr * pitch, va, vb, qa, qb);
+      }
+    } else {
+      // split route: high halves through the line buffer, low halves through
+      // the lane's own stage words (its two columns of blocks p, p + 4)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int c = 2 * j + i;
+        int xa[16], xb[16], ua[16], ub[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int f = w_of(u) * wc[i];
+          xa[u] = ((i ? ya[u].y : ya[u].x) >> 16) * f;
+          xb[u] = ((i ? yb[u].y : yb[u].x) >> 16) * f;
+        }
+        inv16(xa, ua);
+        inv16(xb, ub);
+        float4* const ln = line + 138 * p + 17 * j + 8 * i;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          ln[q] = make_float4(__int_as_float(ua[2 * q]), __int_as_float(ub[2 * q]), __int_as_float(ua[2 * q + 1]),
+                              __int_as_float(ub[2 * q + 1]));
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int f = w_of(u) * wc[i];
+          xa[u] = ((i ? ya[u].y : ya[u].x) & 0xffff) * f;
+          xb[u] = ((i ? yb[u].y : yb[u].x) & 0xffff) * f;
+        }
+        inv16(xa, ua);
+        inv16(xb, ub);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const int wd = (16 * m + c) ^ s8;
+          stage[256 * p + wd] = ua[m];
+          stage[256 * (p + 4) + wd] = ub[m];
+        }
+      }
+      __syncwarp();
+#pragma unroll 1
+      for (int rr = 0; rr < 2; ++rr) {
+        const int m = 2 * j + rr;
+        const float2* const fin = reinterpret_cast<const float2*>(line + 138 * p + j) + rr;
+        int ra[16], rb[16], zha[16], zhb[16], zla[16], zlb[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float2 x = fin[2 * (8 * c + (c >> 1))];
+          ra[c] = __float_as_int(x.x);
+          rb[c] = __float_as_int(x.y);
+        }
+        inv16(ra, zha);
+        inv16(rb, zhb);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int wd = (16 * m + c) ^ s8;
+          ra[c] = stage[256 * p + wd];
+          rb[c] = stage[256 * (p + 4) + wd];
+        }
+        inv16(ra, zla);
+        inv16(rb, zlb);
+        int qa[16], qb[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) {
+          qa[n] = round_clamp<kDtype, 2304u>((long long)zha[n] * 65536 + zla[n]);
+          qb[n] = round_clamp<kDtype, 2304u>((long long)zhb[n] * 65536 + zlb[n]);
+        }
+        store_row<kDtype>(drow + rr * pitch, va, vb, qa, qb);
+      }
+      __syncwarp();  // the stage's low halves are read: refill it
+      issue(t + stride);
+    }
+    __syncwarp();  // line buffer reads done before the next tile's writes
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // 1-D transforms over contiguous 16-sample vectors, one vector per lane,
 // 32 vectors per warp step; the 64-byte coefficient vectors pass through a
@@ -669,12 +842,12 @@ cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void*
   if (dtype == 0)
     return zigzag ? launch_persistent<coef_inverse_kernel<0, true>>(threads, smem, num_sms, kCWarps, ntiles, stream,
                                                                     d_coef, w, h, d, pitch)
-                  : launch_persistent<coef_inverse_kernel<0, false>>(threads, smem, num_sms, kCWarps, ntiles, stream,
-                                                                     d_coef, w, h, d, pitch);
+                  : launch_persistent<coef_inverse_rm_kernel<0>>(threads, smem, num_sms, kCWarps, ntiles, stream,
+                                                                 d_coef, w, h, d, pitch);
   return zigzag ? launch_persistent<coef_inverse_kernel<1, true>>(threads, smem, num_sms, kCWarps, ntiles, stream,
                                                                   d_coef, w, h, d, pitch)
-                : launch_persistent<coef_inverse_kernel<1, false>>(threads, smem, num_sms, kCWarps, ntiles, stream,
-                                                                   d_coef, w, h, d, pitch);
+                : launch_persistent<coef_inverse_rm_kernel<1>>(threads, smem, num_sms, kCWarps, ntiles, stream,
+                                                               d_coef, w, h, d, pitch);
 }
 
 cudaError_t launch_forward_1d(int dtype, const void* d_src, long long count, int32_t* d_coef, int num_sms,
