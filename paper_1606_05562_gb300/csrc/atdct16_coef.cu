@@ -299,6 +299,150 @@ coef_forward_kernel(const uint8_t* __restrict__ src, long long pitch, int w, int
   }
 }
 
+// Row-major forward whose coefficients leave through the copy engine: the
+// column pass writes each block's 256 int32 as (Y(u, 2j), Y(u, 2j+1)) pairs
+// into a padded stage (block stride 264 words: the pairs of the four blocks
+// of a lane quad fall on distinct banks), and one lane hands every valid block
+// to a 1 KB bulk shared-to-global copy, so the warp neither reads the stage
+// back nor issues the global stores.  The stage is rewritten only after the
+// previous tile's copies have read it.
+constexpr int kCBlockWords = 264;
+constexpr int kCRmWarpSmemBytes = 16 * kCLineUnits + 4 * 8 * kCBlockWords;
+
+__device__ __forceinline__ void bulk_store_1k(int32_t* gdst, const int* ssrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(ssrc);
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], 1024;" ::"l"(gdst), "r"(s) : "memory");
+}
+
+template <int kDtype>
+__global__ void __launch_bounds__(32 * kCWarps, 3)
+coef_forward_rm_kernel(const uint8_t* __restrict__ src, long long pitch, int w, int h, int32_t* __restrict__ coef) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = lane & 3, j = lane >> 2;
+  float4* const line = reinterpret_cast<float4*>(csm + warp * kCRmWarpSmemBytes);
+  int* const stage = reinterpret_cast<int*>(line + kCLineUnits);
+  constexpr int kElem = kDtype == 0 ? 1 : 2;
+  const int tiles_x = (w + kTileW - 1) / kTileW;
+  const int ntiles = tiles_x * (h >> 4);
+  const int bpr = w >> 4;
+  constexpr int kLoads = kDtype == 0 ? 4 : 8;
+  const int stride = gridDim.x * kCWarps;
+  auto load = [&](int t, uint4 (&r)[kLoads]) {
+#pragma unroll
+    for (int i = 0; i < kLoads; ++i) r[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (t >= ntiles) return;
+    const int ty = t / tiles_x, tx = t - ty * tiles_x;
+    const int nb = min(8, (w - tx * kTileW) >> 4);
+    const uint8_t* s = src + (long long)(ty * kTileH + 2 * j) * pitch + (long long)(tx * kTileW + 16 * p) * kElem;
+    if (kDtype == 0) {
+      if (p < nb) {
+        r[0] = ldg_stream(s);
+        r[1] = ldg_stream(s + pitch);
+      }
+      if (p + 4 < nb) {
+        r[2] = ldg_stream(s + 64);
+        r[3] = ldg_stream(s + 64 + pitch);
+      }
+    } else {
+      if (p < nb) {
+        r[0] = ldg_stream(s);
+        r[1] = ldg_stream(s + 16);
+        r[2] = ldg_stream(s + pitch);
+        r[3] = ldg_stream(s + pitch + 16);
+      }
+      if (p + 4 < nb) {
+        r[4] = ldg_stream(s + 128);
+        r[5] = ldg_stream(s + 144);
+        r[6] = ldg_stream(s + pitch + 128);
+        r[7] = ldg_stream(s + pitch + 144);
+      }
+    }
+  };
+  uint4 cur[kLoads], nxt[kLoads];
+  load(blockIdx.x * kCWarps + warp, cur);
+  for (int t = blockIdx.x * kCWarps + warp; t < ntiles; t += stride) {
+    const int ty = t / tiles_x, tx = t - ty * tiles_x;
+    const int nb = min(8, (w - tx * kTileW) >> 4);
+    load(t + stride, nxt);
+    // ---- row pass, both rows of a column as one 16-byte line-buffer unit
+    float2 rv[2][16];
+    if (kDtype == 0) {
+#pragma unroll
+      for (int tr = 0; tr < 2; ++tr) {
+        float2 xv[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n)
+          xv[n] = make_float2(u8_x256(word_at(cur[tr], n >> 2), n & 3), u8_x256(word_at(cur[2 + tr], n >> 2), n & 3));
+        fwd16(xv, rv[tr]);
+        rv[tr][0] = bsub(rv[tr][0], make_float2(134217728.0f, 134217728.0f));
+      }
+    } else {
+#pragma unroll
+      for (int tr = 0; tr < 2; ++tr) {
+        float2 xv[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) {
+          const unsigned wa = word_at(cur[2 * tr + (n >> 3)], (n & 7) >> 1);
+          const unsigned wb = word_at(cur[4 + 2 * tr + (n >> 3)], (n & 7) >> 1);
+          const float2 m = (n & 1) ? make_float2(i16_hi_f(wa), i16_hi_f(wb)) : make_float2(i16_lo_f(wa), i16_lo_f(wb));
+          xv[n] = __fadd2_rn(m, make_float2(-8421376.0f, -8421376.0f));
+        }
+        fwd16(xv, rv[tr]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      line[138 * p + 8 * k + (k >> 1) + j] = make_float4(rv[0][k].x, rv[0][k].y, rv[1][k].x, rv[1][k].y);
+#pragma unroll
+    for (int i = 0; i < kLoads; ++i) cur[i] = nxt[i];
+    __syncwarp();
+    // ---- column pass on columns 2j, 2j+1 (both kept for the pair writes)
+    int yv[2][2][16];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float4* const ln = line + 138 * p + 17 * j + 8 * i;
+      float2 cv[16], y[16];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 v = ln[q];
+        cv[2 * q] = make_float2(v.x, v.y);
+        cv[2 * q + 1] = make_float2(v.z, v.w);
+      }
+      fwd16(cv, y);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        if (kDtype == 0) {
+          const float2 m = __ffma2_rn(y[u], make_float2(0.00390625f, 0.00390625f), make_float2(12582912.0f, 12582912.0f));
+          yv[i][0][u] = (int)(__float_as_uint(m.x) - 0x4B400000u);
+          yv[i][1][u] = (int)(__float_as_uint(m.y) - 0x4B400000u);
+        } else {
+          yv[i][0][u] = __float2int_rn(y[u].x);
+          yv[i][1][u] = __float2int_rn(y[u].y);
+        }
+      }
+    }
+    // the previous tile's bulk copies must have read the stage
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      *reinterpret_cast<int2*>(stage + kCBlockWords * p + 16 * u + 2 * j) = make_int2(yv[0][0][u], yv[1][0][u]);
+      *reinterpret_cast<int2*>(stage + kCBlockWords * (p + 4) + 16 * u + 2 * j) = make_int2(yv[0][1][u], yv[1][1][u]);
+    }
+    // generic-proxy writes made visible to the copy engine, then one lane copies
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) {
+      int32_t* const out = coef + ((long long)ty * bpr + tx * 8) * 256;
+      for (int b = 0; b < nb; ++b) bulk_store_1k(out + 256 * b, stage + kCBlockWords * b);
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+    __syncwarp();  // line buffer reads done before the next tile's writes
+  }
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // 2-D exact inverse: Z = T^T (W Y W) T, X_hat = Z / 2304 (Sec. 4 with
 // S^2 = W / 48 folded in), round half to even, clamp.
@@ -820,16 +964,17 @@ cudaError_t launch_forward(int dtype, const void* d_src, long long pitch, int w,
   if (ntiles <= 0) return cudaSuccess;
   if (ntiles >= (1LL << 31) - 4096) return cudaErrorInvalidValue;  // tile indices are 32-bit in the kernel
   const int smem = kCWarps * kCWarpSmemBytes, threads = 32 * kCWarps;
+  const int smem_rm = kCWarps * kCRmWarpSmemBytes;
   const uint8_t* s = static_cast<const uint8_t*>(d_src);
   if (dtype == 0)
     return zigzag ? launch_persistent<coef_forward_kernel<0, true>>(threads, smem, num_sms, kCWarps, ntiles, stream, s,
                                                                     pitch, w, h, d_coef)
-                  : launch_persistent<coef_forward_kernel<0, false>>(threads, smem, num_sms, kCWarps, ntiles, stream,
-                                                                     s, pitch, w, h, d_coef);
+                  : launch_persistent<coef_forward_rm_kernel<0>>(threads, smem_rm, num_sms, kCWarps, ntiles, stream,
+                                                                 s, pitch, w, h, d_coef);
   return zigzag ? launch_persistent<coef_forward_kernel<1, true>>(threads, smem, num_sms, kCWarps, ntiles, stream, s,
                                                                   pitch, w, h, d_coef)
-                : launch_persistent<coef_forward_kernel<1, false>>(threads, smem, num_sms, kCWarps, ntiles, stream, s,
-                                                                   pitch, w, h, d_coef);
+                : launch_persistent<coef_forward_rm_kernel<1>>(threads, smem_rm, num_sms, kCWarps, ntiles, stream, s,
+                                                               pitch, w, h, d_coef);
 }
 
 cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void* d_dst, long long pitch,
