@@ -19,16 +19,15 @@
 // block-major coefficient array, so a tile's coefficients are one 8 KB
 // range).  Lane (p, j) = (lane & 3, lane >> 2) owns rows (and later
 // columns) 2j, 2j+1 of blocks p and p + 4.  Every global access moves whole
-// 32-byte sectors: image rows as 16-byte segments, coefficients as 512-byte
-// runs per warp instruction; the transposition and the reordering go
-// through shared memory:
+// 32-byte sectors: image rows as 16-byte segments, coefficient blocks as
+// 1 KB bulk copies (forward) or 512-byte cp.async runs per warp instruction
+// (inverse); the transposition and the reordering go through shared memory:
 //   line buffer  unit(p, c, q) = 138 p + 8 c + (c >> 1) + q (16-byte units):
 //                rows 2q, 2q+1 of column c of blocks p, p + 4;
-//   block stage  8 blocks x 256 int32, word (16 u + v) of block b stored at
-//                (16 u + v) ^ bswz(b), bswz(b) = (b & 1) | ((b & 2) << 3),
-//                which spreads the four blocks of a lane quad over all 32
-//                banks for the per-column accesses and keeps 16-byte
-//                chunks whole (XOR 16 moves a chunk, XOR 1 swaps within it).
+//   block stage  the tile's 8 blocks of 256 int32 in their global order
+//                (row-major or scan order), block b at word 264 b; the
+//                row-major inverse instead keeps block b at word 256 b with
+//                16-byte chunk q at q ^ 2 (b & 3).
 #include <algorithm>
 #include <atomic>
 #include <cstdint>
@@ -44,8 +43,8 @@ namespace {
 
 constexpr int kCWarps = 4;
 constexpr int kCLineUnits = 549;
-constexpr int kCStageUnits = 512;
-constexpr int kCWarpSmemBytes = 16 * (kCLineUnits + kCStageUnits);
+constexpr int kCStageUnits = 512;                                    // 8 x 256 int32, in 16-byte units
+constexpr int kCWarpSmemBytes = 16 * (kCLineUnits + kCStageUnits);  // row-major inverse
 
 // W_u = 48 S_u^2 = 48 / nnz_u for rows u = 0..15 of T: nnz_u in {16, 12, 8},
 // i.e. W_u in {3, 4, 6}, coded 0, 1, 2 in two bits per row.
@@ -53,15 +52,6 @@ __host__ __device__ constexpr int w_of(int u) {
   return 3 + ((0x56945290u >> (2 * u)) & 3u) + (((0x56945290u >> (2 * u)) & 3u) >> 1);
 }
 static_assert(w_of(0) == 3 && w_of(2) == 4 && w_of(3) == 6 && w_of(15) == 4, "W = 48 S^2");
-
-__device__ __forceinline__ int bswz(int b) { return (b & 1) | ((b & 2) << 3); }
-
-// Four consecutive scan positions k .. k+3, one byte each.
-__device__ unsigned zz_pack4(int k) {
-  return (unsigned)zigzag_word(k) | ((unsigned)zigzag_word(k + 1) << 8) | ((unsigned)zigzag_word(k + 2) << 16) |
-         ((unsigned)zigzag_word(k + 3) << 24);
-}
-__device__ __forceinline__ int zz_byte(unsigned packed, int e) { return (packed >> (8 * e)) & 0xff; }
 
 __device__ __forceinline__ unsigned word_at(const uint4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
@@ -149,179 +139,50 @@ cudaError_t launch_persistent(int threads, int smem, int num_sms, long long item
 // is a multiple of 256 below 2^28 and the offsets cancel in all rows but the
 // DC, which subtracts 16 * 2^23; the column nodes are 256 Y, |256 Y| < 2^24.
 // I16: the inputs themselves; every node is an integer of magnitude <= 2^23.
-// ---------------------------------------------------------------------------
-template <int kDtype, bool kZigzag>
-__global__ void __launch_bounds__(32 * kCWarps, 3)
-coef_forward_kernel(const uint8_t* __restrict__ src, long long pitch, int w, int h, int32_t* __restrict__ coef) {
-  extern __shared__ __align__(16) unsigned char csm[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int p = lane & 3, j = lane >> 2;
-  float4* const line = reinterpret_cast<float4*>(csm + warp * kCWarpSmemBytes);
-  int* const stage = reinterpret_cast<int*>(line + kCLineUnits);
-  const int swz = bswz(p);
-  unsigned zz[2] = {0u, 0u};
-  if (kZigzag) {
-    zz[0] = zz_pack4(4 * lane);
-    zz[1] = zz_pack4(128 + 4 * lane);
-  }
-  constexpr int kElem = kDtype == 0 ? 1 : 2;
-  const int tiles_x = (w + kTileW - 1) / kTileW;
-  const int ntiles = tiles_x * (h >> 4);  // the launcher checks it fits
-  const int bpr = w >> 4;
-  // The input rows of the warp's next tile are loaded while the current one
-  // is transformed (register double buffer: U8 4, I16 8 16-byte words).
-  constexpr int kLoads = kDtype == 0 ? 4 : 8;
-  const int stride = gridDim.x * kCWarps;
-  auto load = [&](int t, uint4 (&r)[kLoads]) {
-#pragma unroll
-    for (int i = 0; i < kLoads; ++i) r[i] = make_uint4(0u, 0u, 0u, 0u);
-    if (t >= ntiles) return;
-    const int ty = t / tiles_x, tx = t - ty * tiles_x;
-    const int nb = min(8, (w - tx * kTileW) >> 4);
-    const uint8_t* s = src + (long long)(ty * kTileH + 2 * j) * pitch + (long long)(tx * kTileW + 16 * p) * kElem;
-    if (kDtype == 0) {
-      if (p < nb) {
-        r[0] = ldg_stream(s);
-        r[1] = ldg_stream(s + pitch);
-      }
-      if (p + 4 < nb) {
-        r[2] = ldg_stream(s + 64);
-        r[3] = ldg_stream(s + 64 + pitch);
-      }
-    } else {
-      if (p < nb) {
-        r[0] = ldg_stream(s);
-        r[1] = ldg_stream(s + 16);
-        r[2] = ldg_stream(s + pitch);
-        r[3] = ldg_stream(s + pitch + 16);
-      }
-      if (p + 4 < nb) {
-        r[4] = ldg_stream(s + 128);
-        r[5] = ldg_stream(s + 144);
-        r[6] = ldg_stream(s + pitch + 128);
-        r[7] = ldg_stream(s + pitch + 144);
-      }
-    }
-  };
-  uint4 cur[kLoads], nxt[kLoads];
-  load(blockIdx.x * kCWarps + warp, cur);
-  for (int t = blockIdx.x * kCWarps + warp; t < ntiles; t += stride) {
-    const int ty = t / tiles_x, tx = t - ty * tiles_x;
-    const int nb = min(8, (w - tx * kTileW) >> 4);
-    load(t + stride, nxt);
-    // ---- row pass on rows 2j, 2j+1; both rows of column k go to the line
-    // buffer as one 16-byte unit (138 p + 8 k + (k >> 1) + j), conflict-free
-    float2 rv[2][16];
-    if (kDtype == 0) {
-#pragma unroll
-      for (int tr = 0; tr < 2; ++tr) {
-        float2 xv[16];
-#pragma unroll
-        for (int n = 0; n < 16; ++n)
-          xv[n] = make_float2(u8_x256(word_at(cur[tr], n >> 2), n & 3), u8_x256(word_at(cur[2 + tr], n >> 2), n & 3));
-        fwd16(xv, rv[tr]);
-        rv[tr][0] = bsub(rv[tr][0], make_float2(134217728.0f, 134217728.0f));  // 16 * 2^23 of the offsets
-      }
-    } else {
-#pragma unroll
-      for (int tr = 0; tr < 2; ++tr) {
-        float2 xv[16];
-#pragma unroll
-        for (int n = 0; n < 16; ++n) {
-          const unsigned wa = word_at(cur[2 * tr + (n >> 3)], (n & 7) >> 1);
-          const unsigned wb = word_at(cur[4 + 2 * tr + (n >> 3)], (n & 7) >> 1);
-          const float2 m = (n & 1) ? make_float2(i16_hi_f(wa), i16_hi_f(wb)) : make_float2(i16_lo_f(wa), i16_lo_f(wb));
-          xv[n] = __fadd2_rn(m, make_float2(-8421376.0f, -8421376.0f));  // exact sample value
-        }
-        fwd16(xv, rv[tr]);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 16; ++k)
-      line[138 * p + 8 * k + (k >> 1) + j] = make_float4(rv[0][k].x, rv[0][k].y, rv[1][k].x, rv[1][k].y);
-#pragma unroll
-    for (int i = 0; i < kLoads; ++i) cur[i] = nxt[i];
-    __syncwarp();
-    // ---- column pass on columns 2j, 2j+1 into the block stage
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int c = 2 * j + i;
-      const float4* const ln = line + 138 * p + 17 * j + 8 * i;
-      float2 cv[16], y[16];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 v = ln[q];
-        cv[2 * q] = make_float2(v.x, v.y);
-        cv[2 * q + 1] = make_float2(v.z, v.w);
-      }
-      fwd16(cv, y);
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        int ya, yb;
-        if (kDtype == 0) {
-          // Y = y / 256 exactly; 1.5 * 2^23 + Y puts Y in the low mantissa bits
-          const float2 m = __ffma2_rn(y[u], make_float2(0.00390625f, 0.00390625f), make_float2(12582912.0f, 12582912.0f));
-          ya = (int)(__float_as_uint(m.x) - 0x4B400000u);
-          yb = (int)(__float_as_uint(m.y) - 0x4B400000u);
-        } else {
-          ya = __float2int_rn(y[u].x);
-          yb = __float2int_rn(y[u].y);
-        }
-        const int wd = (16 * u + c) ^ swz;
-        stage[256 * p + wd] = ya;
-        stage[256 * (p + 4) + wd] = yb;
-      }
-    }
-    __syncwarp();
-    // ---- the tile's blocks as 512-byte runs, row-major or zig-zag
-    int32_t* const out = coef + ((long long)ty * bpr + tx * 8) * 256;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      if (b >= nb) break;
-      const int* const sb = stage + 256 * b;
-      const int bs = bswz(b);
-#pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        uint4 v;
-        if (!kZigzag) {
-          v = reinterpret_cast<const uint4*>(sb)[(32 * hh + lane) ^ (bs >> 2)];
-          if (b & 1) v = make_uint4(v.y, v.x, v.w, v.z);
-        } else {
-          v.x = (unsigned)sb[zz_byte(zz[hh], 0) ^ bs];
-          v.y = (unsigned)sb[zz_byte(zz[hh], 1) ^ bs];
-          v.z = (unsigned)sb[zz_byte(zz[hh], 2) ^ bs];
-          v.w = (unsigned)sb[zz_byte(zz[hh], 3) ^ bs];
-        }
-        stg_stream(out + 256 * b + 4 * (32 * hh + lane), v);
-      }
-    }
-    __syncwarp();
-  }
-}
-
-// Row-major forward whose coefficients leave through the copy engine: the
-// column pass writes each block's 256 int32 as (Y(u, 2j), Y(u, 2j+1)) pairs
-// into a padded stage (block stride 264 words: the pairs of the four blocks
-// of a lane quad fall on distinct banks), and one lane hands every valid block
-// to a 1 KB bulk shared-to-global copy, so the warp neither reads the stage
-// back nor issues the global stores.  The stage is rewritten only after the
-// previous tile's copies have read it.
+//
+// The input rows of the warp's next tile are loaded while the current one is
+// transformed (register double buffer), and the coefficients leave through
+// the copy engine: the column pass
+// writes each block's 256 int32 in their final order into a padded stage
+// (block stride 264 words), and one lane hands every valid block to a 1 KB
+// bulk shared-to-global copy, so the warp neither reads the stage back nor
+// issues the global stores.  Row-major blocks take (Y(u, 2j), Y(u, 2j+1))
+// pairs (the four blocks of a lane quad fall on distinct banks); zig-zag
+// blocks take single words at the scan positions of the lane's columns, kept
+// as bytes in eight registers (at most two lanes share a bank per store with
+// this stride).  The stage is rewritten only after the previous tile's copies
+// have read it.
 constexpr int kCBlockWords = 264;
-constexpr int kCRmWarpSmemBytes = 16 * kCLineUnits + 4 * 8 * kCBlockWords;
+constexpr int kCPaddedWarpSmemBytes = 16 * kCLineUnits + 4 * 8 * kCBlockWords;
 
 __device__ __forceinline__ void bulk_store_1k(int32_t* gdst, const int* ssrc) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(ssrc);
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], 1024;" ::"l"(gdst), "r"(s) : "memory");
 }
 
-template <int kDtype>
+// Scan positions of (u, 2j + i), u = 0..15, i = 0, 1: byte u & 3 of word 4 i + (u >> 2).
+__device__ __forceinline__ void column_ranks(int j, unsigned (&zr)[8]) {
+#pragma unroll
+  for (int e = 0; e < 8; ++e) zr[e] = 0u;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int u = 0; u < 16; ++u) zr[4 * i + (u >> 2)] |= (unsigned)zigzag_rank(16 * u + 2 * j + i) << (8 * (u & 3));
+}
+__device__ __forceinline__ int rank_of(const unsigned (&zr)[8], int i, int u) {
+  return (int)((zr[4 * i + (u >> 2)] >> (8 * (u & 3))) & 0xffu);
+}
+
+template <int kDtype, bool kZigzag>
 __global__ void __launch_bounds__(32 * kCWarps, 3)
-coef_forward_rm_kernel(const uint8_t* __restrict__ src, long long pitch, int w, int h, int32_t* __restrict__ coef) {
+coef_forward_kernel(const uint8_t* __restrict__ src, long long pitch, int w, int h, int32_t* __restrict__ coef) {
   extern __shared__ __align__(16) unsigned char csm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int p = lane & 3, j = lane >> 2;
-  float4* const line = reinterpret_cast<float4*>(csm + warp * kCRmWarpSmemBytes);
+  float4* const line = reinterpret_cast<float4*>(csm + warp * kCPaddedWarpSmemBytes);
   int* const stage = reinterpret_cast<int*>(line + kCLineUnits);
+  unsigned zr[8];
+  if (kZigzag) column_ranks(j, zr);
   constexpr int kElem = kDtype == 0 ? 1 : 2;
   const int tiles_x = (w + kTileW - 1) / kTileW;
   const int ntiles = tiles_x * (h >> 4);
@@ -425,10 +286,21 @@ coef_forward_rm_kernel(const uint8_t* __restrict__ src, long long pitch, int w, 
     // the previous tile's bulk copies must have read the stage
     if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     __syncwarp();
+    if (!kZigzag) {
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      *reinterpret_cast<int2*>(stage + kCBlockWords * p + 16 * u + 2 * j) = make_int2(yv[0][0][u], yv[1][0][u]);
-      *reinterpret_cast<int2*>(stage + kCBlockWords * (p + 4) + 16 * u + 2 * j) = make_int2(yv[0][1][u], yv[1][1][u]);
+      for (int u = 0; u < 16; ++u) {
+        *reinterpret_cast<int2*>(stage + kCBlockWords * p + 16 * u + 2 * j) = make_int2(yv[0][0][u], yv[1][0][u]);
+        *reinterpret_cast<int2*>(stage + kCBlockWords * (p + 4) + 16 * u + 2 * j) = make_int2(yv[0][1][u], yv[1][1][u]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          int* const sw = stage + kCBlockWords * p + rank_of(zr, i, u);
+          sw[0] = yv[i][0][u];
+          sw[4 * kCBlockWords] = yv[i][1][u];
+        }
     }
     // generic-proxy writes made visible to the copy engine, then one lane copies
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -451,8 +323,8 @@ coef_forward_rm_kernel(const uint8_t* __restrict__ src, long long pitch, int w, 
 // |Z| <= (sum_u W_u)^2 2^18 = 68^2 2^18 < 2^31.  Any other tile (checked per warp)
 // splits Y = 2^16 Y_h + Y_l (|Y_h| <= 2^15, 0 <= Y_l < 2^16), transforms both
 // halves exactly in int32 and forms Z = 2^16 Z_h + Z_l in 64 bits.  The
-// low-half column results go to the block stage, into the words their lane
-// has just read (each lane reads and writes only its own 64 words there).
+// high-half column results go through the line buffer, the low-half ones
+// through the block stage, whose coefficients are all in registers by then.
 // ---------------------------------------------------------------------------
 template <int kDtype>
 __device__ __forceinline__ void store_row(uint8_t* d, bool va, bool vb, const int (&qa)[16], const int (&qb)[16]) {
@@ -505,184 +377,34 @@ __device__ __forceinline__ void round_pair(int za, int zb, int& qa, int& qb) {
   }
 }
 
-template <int kDtype, bool kZigzag>
-__global__ void __launch_bounds__(32 * kCWarps, 3)
-coef_inverse_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __restrict__ dst, long long pitch) {
-  extern __shared__ __align__(16) unsigned char csm[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int p = lane & 3, j = lane >> 2, jb1 = (j >> 1) & 1;
-  float4* const line = reinterpret_cast<float4*>(csm + warp * kCWarpSmemBytes);
-  int* const stage = reinterpret_cast<int*>(line + kCLineUnits);
-  const int swz = bswz(p);
-  unsigned zz[2] = {0u, 0u};
-  if (kZigzag) {
-    zz[0] = zz_pack4(4 * lane);
-    zz[1] = zz_pack4(128 + 4 * lane);
-  }
-  const int wc[2] = {w_of(2 * j), w_of(2 * j + 1)};
-  constexpr int kElem = kDtype == 0 ? 1 : 2;
-  const int tiles_x = (w + kTileW - 1) / kTileW;
-  const int ntiles = tiles_x * (h >> 4);
-  const int bpr = w >> 4;
-  for (int t = blockIdx.x * kCWarps + warp; t < ntiles; t += gridDim.x * kCWarps) {
-    const int ty = t / tiles_x, tx = t - ty * tiles_x;
-    const int nb = min(8, (w - tx * kTileW) >> 4);
-    const bool va = p < nb, vb = p + 4 < nb;
-    // ---- the tile's coefficients (8 KB) into the block stage
-    const int32_t* const in = coef + ((long long)ty * bpr + tx * 8) * 256;
-    uint4 v[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m)
-      v[m] = (m >> 1) < nb ? ldg_stream(in + 256 * (m >> 1) + 4 * (32 * (m & 1) + lane)) : make_uint4(0u, 0u, 0u, 0u);
-    // range test: Y + 2^18 < 2^19 (as unsigned) for every Y of the tile
-    unsigned big = 0u;
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int b = m >> 1, hh = m & 1, bs = bswz(b);
-      big |= (v[m].x + (1u << 18)) | (v[m].y + (1u << 18)) | (v[m].z + (1u << 18)) | (v[m].w + (1u << 18));
-      int* const sb = stage + 256 * b;
-      if (!kZigzag) {
-        const uint4 x = (b & 1) ? make_uint4(v[m].y, v[m].x, v[m].w, v[m].z) : v[m];
-        reinterpret_cast<uint4*>(sb)[(32 * hh + lane) ^ (bs >> 2)] = x;
-      } else {
-        sb[zz_byte(zz[hh], 0) ^ bs] = (int)v[m].x;
-        sb[zz_byte(zz[hh], 1) ^ bs] = (int)v[m].y;
-        sb[zz_byte(zz[hh], 2) ^ bs] = (int)v[m].z;
-        sb[zz_byte(zz[hh], 3) ^ bs] = (int)v[m].w;
-      }
-    }
-    const bool wide = __any_sync(0xffffffffu, big >= (1u << 19));
-    __syncwarp();
-    uint8_t* const drow = dst + (long long)(ty * kTileH + 2 * j) * pitch + (long long)(tx * kTileW + 16 * p) * kElem;
-    if (!wide) {
-      // ---- column pass (int32): U(:, c) = T^T (W_u W_c Y(:, c))
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int c = 2 * j + i;
-        int da[16], db[16], ua[16], ub[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int wd = (16 * u + c) ^ swz, f = w_of(u) * wc[i];
-          da[u] = stage[256 * p + wd] * f;
-          db[u] = stage[256 * (p + 4) + wd] * f;
-        }
-        inv16(da, ua);
-        inv16(db, ub);
-        float4* const ln = line + 138 * p + 17 * j + 8 * i;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          ln[q] = make_float4(__int_as_float(ua[2 * q]), __int_as_float(ub[2 * q]), __int_as_float(ua[2 * q + 1]),
-                              __int_as_float(ub[2 * q + 1]));
-      }
-      __syncwarp();
-      // ---- row pass (int32) on rows 2j + rr, round, store
-#pragma unroll
-      for (int tr = 0; tr < 2; ++tr) {
-        const int rr = tr ^ jb1;
-        const float2* const fin = reinterpret_cast<const float2*>(line + 138 * p + j) + rr;
-        int ra[16], rb[16], za[16], zb[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const float2 x = fin[2 * (8 * c + (c >> 1))];
-          ra[c] = __float_as_int(x.x);
-          rb[c] = __float_as_int(x.y);
-        }
-        inv16(ra, za);
-        inv16(rb, zb);
-        int qa[16], qb[16];
-#pragma unroll
-        for (int n = 0; n < 16; ++n) round_pair<kDtype>(za[n], zb[n], qa[n], qb[n]);
-        store_row<kDtype>(drow + rr * pitch, va, vb, qa, qb);
-      }
-    } else {
-      // ---- split path: high halves through the line buffer, low halves
-      // through the lane's own words of the block stage
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int c = 2 * j + i;
-        int ha[16], hb[16], la[16], lb[16], ua[16], ub[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int wd = (16 * u + c) ^ swz, f = w_of(u) * wc[i];
-          const int ya = stage[256 * p + wd], yb = stage[256 * (p + 4) + wd];
-          ha[u] = (ya >> 16) * f;
-          hb[u] = (yb >> 16) * f;
-          la[u] = (ya & 0xffff) * f;
-          lb[u] = (yb & 0xffff) * f;
-        }
-        inv16(ha, ua);
-        inv16(hb, ub);
-        float4* const ln = line + 138 * p + 17 * j + 8 * i;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          ln[q] = make_float4(__int_as_float(ua[2 * q]), __int_as_float(ub[2 * q]), __int_as_float(ua[2 * q + 1]),
-                              __int_as_float(ub[2 * q + 1]));
-        inv16(la, ua);
-        inv16(lb, ub);
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-          const int wd = (16 * m + c) ^ swz;
-          stage[256 * p + wd] = ua[m];
-          stage[256 * (p + 4) + wd] = ub[m];
-        }
-      }
-      __syncwarp();
-#pragma unroll 1
-      for (int rr = 0; rr < 2; ++rr) {
-        const int m = 2 * j + rr;
-        const float2* const fin = reinterpret_cast<const float2*>(line + 138 * p + j) + rr;
-        int ra[16], rb[16], zha[16], zhb[16], zla[16], zlb[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const float2 x = fin[2 * (8 * c + (c >> 1))];
-          ra[c] = __float_as_int(x.x);
-          rb[c] = __float_as_int(x.y);
-        }
-        inv16(ra, zha);
-        inv16(rb, zhb);
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int wd = (16 * m + c) ^ swz;
-          ra[c] = stage[256 * p + wd];
-          rb[c] = stage[256 * (p + 4) + wd];
-        }
-        inv16(ra, zla);
-        inv16(rb, zlb);
-        int qa[16], qb[16];
-#pragma unroll
-        for (int n = 0; n < 16; ++n) {
-          qa[n] = round_clamp<kDtype, 2304u>((long long)zha[n] * 65536 + zla[n]);
-          qb[n] = round_clamp<kDtype, 2304u>((long long)zhb[n] * 65536 + zlb[n]);
-        }
-        store_row<kDtype>(drow + rr * pitch, va, vb, qa, qb);
-      }
-    }
-    __syncwarp();
-  }
-}
-
-// Row-major exact inverse with the next tile's coefficients copied in while
-// the current one is inverted.  The block stage holds the tile's 8 blocks with
+// Exact inverse with the next tile's coefficients copied in while the current
+// one is inverted.  Row-major: the block stage holds the tile's 8 blocks with
 // 16-byte chunk q of block b at q ^ 2 (b & 3) (word XOR 8 (b & 3)), so that
 // cp.async can fill it directly and each lane reads its two columns as 8-byte
-// pairs without bank conflicts.  After a tile's pairs are in registers the
-// stage is free and the next copy starts; a tile that needs the split route
-// keeps the stage for its low halves and starts the copy when it is done.
-__device__ __forceinline__ void cp_async16_rm(void* smem_dst, const void* gsrc) {
+// pairs without bank conflicts.  Zig-zag: the blocks sit in scan order at a
+// padded stride of 264 words and each lane gathers its columns' words by their
+// scan positions.  After a tile's coefficients are in registers the stage is
+// free and the next copy starts; a tile that needs the split route keeps the
+// stage for its low halves (same word permutation in both layouts) and starts
+// the copy when it is done.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
 }
 
-template <int kDtype>
+template <int kDtype, bool kZigzag>
 __global__ void __launch_bounds__(32 * kCWarps, 3)
-coef_inverse_rm_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __restrict__ dst, long long pitch) {
+coef_inverse_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __restrict__ dst, long long pitch) {
   extern __shared__ __align__(16) unsigned char csm[];
+  constexpr int kBW = kZigzag ? kCBlockWords : 256;  // block stride in the stage, words
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int p = lane & 3, j = lane >> 2, jb1 = (j >> 1) & 1;
-  float4* const line = reinterpret_cast<float4*>(csm + warp * kCWarpSmemBytes);
+  float4* const line = reinterpret_cast<float4*>(csm + warp * (kZigzag ? kCPaddedWarpSmemBytes : kCWarpSmemBytes));
   int* const stage = reinterpret_cast<int*>(line + kCLineUnits);
   uint4* const stage4 = reinterpret_cast<uint4*>(stage);
   const int s8 = 8 * p;  // word XOR of blocks p and p + 4
+  unsigned zr[8];
+  if (kZigzag) column_ranks(j, zr);
   const int wc[2] = {w_of(2 * j), w_of(2 * j + 1)};
   constexpr int kElem = kDtype == 0 ? 1 : 2;
   const int tiles_x = (w + kTileW - 1) / kTileW;
@@ -697,7 +419,7 @@ coef_inverse_rm_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* 
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int b = m >> 1, q = 32 * (m & 1) + lane;
-        if (b < nb) cp_async16_rm(stage4 + 64 * b + (q ^ (2 * (b & 3))), in + 256 * b + 4 * q);
+        if (b < nb) cp_async16(stage4 + (kBW / 4) * b + (kZigzag ? q : q ^ (2 * (b & 3))), in + 256 * b + 4 * q);
       }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -714,9 +436,16 @@ coef_inverse_rm_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* 
     unsigned big = 0u;
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
-      const int wd = (16 * u + 2 * j) ^ s8;
-      ya[u] = *reinterpret_cast<const int2*>(stage + 256 * p + wd);
-      yb[u] = *reinterpret_cast<const int2*>(stage + 256 * (p + 4) + wd);
+      if (!kZigzag) {
+        const int wd = (16 * u + 2 * j) ^ s8;
+        ya[u] = *reinterpret_cast<const int2*>(stage + 256 * p + wd);
+        yb[u] = *reinterpret_cast<const int2*>(stage + 256 * (p + 4) + wd);
+      } else {
+        const int* const s0 = stage + kBW * p + rank_of(zr, 0, u);
+        const int* const s1 = stage + kBW * p + rank_of(zr, 1, u);
+        ya[u] = make_int2(s0[0], s1[0]);
+        yb[u] = make_int2(s0[4 * kBW], s1[4 * kBW]);
+      }
       if (va) big |= ((unsigned)ya[u].x + (1u << 18)) | ((unsigned)ya[u].y + (1u << 18));
       if (vb) big |= ((unsigned)yb[u].x + (1u << 18)) | ((unsigned)yb[u].y + (1u << 18));
     }
@@ -792,8 +521,8 @@ coef_inverse_rm_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* 
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
           const int wd = (16 * m + c) ^ s8;
-          stage[256 * p + wd] = ua[m];
-          stage[256 * (p + 4) + wd] = ub[m];
+          stage[kBW * p + wd] = ua[m];
+          stage[kBW * (p + 4) + wd] = ub[m];
         }
       }
       __syncwarp();
@@ -813,8 +542,8 @@ coef_inverse_rm_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* 
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int wd = (16 * m + c) ^ s8;
-          ra[c] = stage[256 * p + wd];
-          rb[c] = stage[256 * (p + 4) + wd];
+          ra[c] = stage[kBW * p + wd];
+          rb[c] = stage[kBW * (p + 4) + wd];
         }
         inv16(ra, zla);
         inv16(rb, zlb);
@@ -963,18 +692,19 @@ cudaError_t launch_forward(int dtype, const void* d_src, long long pitch, int w,
   const long long ntiles = (long long)((w + kTileW - 1) / kTileW) * (h >> 4);
   if (ntiles <= 0) return cudaSuccess;
   if (ntiles >= (1LL << 31) - 4096) return cudaErrorInvalidValue;  // tile indices are 32-bit in the kernel
-  const int smem = kCWarps * kCWarpSmemBytes, threads = 32 * kCWarps;
-  const int smem_rm = kCWarps * kCRmWarpSmemBytes;
+  const int smem = kCWarps * kCPaddedWarpSmemBytes, threads = 32 * kCWarps;
   const uint8_t* s = static_cast<const uint8_t*>(d_src);
+  if (dtype == 0 && zigzag)
+    return launch_persistent<coef_forward_kernel<0, true>>(threads, smem, num_sms, kCWarps, ntiles, stream, s, pitch, w,
+                                                           h, d_coef);
   if (dtype == 0)
-    return zigzag ? launch_persistent<coef_forward_kernel<0, true>>(threads, smem, num_sms, kCWarps, ntiles, stream, s,
-                                                                    pitch, w, h, d_coef)
-                  : launch_persistent<coef_forward_rm_kernel<0>>(threads, smem_rm, num_sms, kCWarps, ntiles, stream,
-                                                                 s, pitch, w, h, d_coef);
-  return zigzag ? launch_persistent<coef_forward_kernel<1, true>>(threads, smem, num_sms, kCWarps, ntiles, stream, s,
-                                                                  pitch, w, h, d_coef)
-                : launch_persistent<coef_forward_rm_kernel<1>>(threads, smem_rm, num_sms, kCWarps, ntiles, stream, s,
-                                                               pitch, w, h, d_coef);
+    return launch_persistent<coef_forward_kernel<0, false>>(threads, smem, num_sms, kCWarps, ntiles, stream, s, pitch,
+                                                            w, h, d_coef);
+  if (zigzag)
+    return launch_persistent<coef_forward_kernel<1, true>>(threads, smem, num_sms, kCWarps, ntiles, stream, s, pitch, w,
+                                                           h, d_coef);
+  return launch_persistent<coef_forward_kernel<1, false>>(threads, smem, num_sms, kCWarps, ntiles, stream, s, pitch, w,
+                                                          h, d_coef);
 }
 
 cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void* d_dst, long long pitch,
@@ -982,17 +712,20 @@ cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void*
   const long long ntiles = (long long)((w + kTileW - 1) / kTileW) * (h >> 4);
   if (ntiles <= 0) return cudaSuccess;
   if (ntiles >= (1LL << 31) - 4096) return cudaErrorInvalidValue;
-  const int smem = kCWarps * kCWarpSmemBytes, threads = 32 * kCWarps;
+  const int threads = 32 * kCWarps;
+  const int smem = kCWarps * (zigzag ? kCPaddedWarpSmemBytes : kCWarpSmemBytes);
   uint8_t* d = static_cast<uint8_t*>(d_dst);
+  if (dtype == 0 && zigzag)
+    return launch_persistent<coef_inverse_kernel<0, true>>(threads, smem, num_sms, kCWarps, ntiles, stream, d_coef, w,
+                                                           h, d, pitch);
   if (dtype == 0)
-    return zigzag ? launch_persistent<coef_inverse_kernel<0, true>>(threads, smem, num_sms, kCWarps, ntiles, stream,
-                                                                    d_coef, w, h, d, pitch)
-                  : launch_persistent<coef_inverse_rm_kernel<0>>(threads, smem, num_sms, kCWarps, ntiles, stream,
-                                                                 d_coef, w, h, d, pitch);
-  return zigzag ? launch_persistent<coef_inverse_kernel<1, true>>(threads, smem, num_sms, kCWarps, ntiles, stream,
-                                                                  d_coef, w, h, d, pitch)
-                : launch_persistent<coef_inverse_rm_kernel<1>>(threads, smem, num_sms, kCWarps, ntiles, stream,
-                                                               d_coef, w, h, d, pitch);
+    return launch_persistent<coef_inverse_kernel<0, false>>(threads, smem, num_sms, kCWarps, ntiles, stream, d_coef, w,
+                                                            h, d, pitch);
+  if (zigzag)
+    return launch_persistent<coef_inverse_kernel<1, true>>(threads, smem, num_sms, kCWarps, ntiles, stream, d_coef, w,
+                                                           h, d, pitch);
+  return launch_persistent<coef_inverse_kernel<1, false>>(threads, smem, num_sms, kCWarps, ntiles, stream, d_coef, w, h,
+                                                          d, pitch);
 }
 
 cudaError_t launch_forward_1d(int dtype, const void* d_src, long long count, int32_t* d_coef, int num_sms,

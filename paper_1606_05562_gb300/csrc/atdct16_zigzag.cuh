@@ -27,4 +27,15 @@ ATDCT16_ZZ_HD int zigzag_word(int k) {
   return (s & 1) ? 16 * b + a : 16 * a + b;
 }
 
+// Scan position of the coefficient (u, v) = (word >> 4, word & 15): the
+// inverse of zigzag_word.  Diagonal s = u + v starts after s (s + 1) / 2
+// positions (s <= 15) or 256 - (31 - s)(32 - s) / 2 (s >= 16); along it the
+// offset counts down from min(s, 15) in u (even s) or in v (odd s).
+ATDCT16_ZZ_HD int zigzag_rank(int word) {
+  const int u = word >> 4, v = word & 15, s = u + v;
+  const int base = s <= 15 ? s * (s + 1) / 2 : 256 - (31 - s) * (32 - s) / 2;
+  const int hi = s < 16 ? s : 15;
+  return base + hi - ((s & 1) ? v : u);
+}
+
 }  // namespace atdct16
