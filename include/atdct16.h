@@ -339,13 +339,17 @@ atdct16_status atdct16_server_destroy(atdct16_server_t server);
  * checks rejected a descriptor).  Synchronises the plan's last stream. */
 atdct16_status atdct16_last_device_status(atdct16_plan_t plan);
 
-/* Kernel timing hook (tracing support; not part of the paper).  While
- * enabled, every fused zonal / quantisation kernel launch of the plan is
- * bracketed by CUDA events on the launch stream.  atdct16_plan_profile
- * synchronises on those events and returns the number of timed launches and
- * their summed device time in milliseconds, then clears the record.  At most
- * 4096 launches are recorded between two queries; later ones are not timed. */
-atdct16_status atdct16_plan_set_profiling(atdct16_plan_t plan, int32_t enable);
+/* Kernel timing hook (tracing support; not part of the paper).  With
+ * every = n > 0, the first fused zonal / quantisation kernel launch of the
+ * plan after this call and then every n-th one is bracketed by CUDA events on
+ * the launch stream (n = 1: every launch; sampling leaves the other calls
+ * free of the extra stream operations, which would otherwise separate the
+ * fused kernel from the finalize that overlaps its end); every = 0 turns the
+ * hook off; every < 0 is EINVAL.  atdct16_plan_profile synchronises on those
+ * events and returns the number of timed launches and their summed device
+ * time in milliseconds, then clears the record.  At most 4096 launches are
+ * recorded between two queries; later ones are not timed. */
+atdct16_status atdct16_plan_set_profiling(atdct16_plan_t plan, int32_t every);
 atdct16_status atdct16_plan_profile(atdct16_plan_t plan, int64_t* launches, double* kernel_ms);
 
 /* Runs the library's 1-D butterflies on the host, for tests:

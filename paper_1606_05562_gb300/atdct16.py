@@ -256,8 +256,9 @@ class Plan:
         arr = _as_array(images)
         _check(lib().atdct16_ssim_batch(self._h, arr, len(images), _ptr(out), _stream(stream)), "ssim_batch")
 
-    def set_profiling(self, on=True):
-        _check(lib().atdct16_plan_set_profiling(self._h, 1 if on else 0), "set_profiling")
+    def set_profiling(self, on=True, every=1):
+        """Bracket the first fused launch and then every `every`-th one with CUDA events."""
+        _check(lib().atdct16_plan_set_profiling(self._h, int(every) if on else 0), "set_profiling")
 
     def profile(self):
         """(timed kernel launches, summed kernel milliseconds) since the last call."""

@@ -49,6 +49,8 @@ struct atdct16_plan_st {
   std::map<unsigned long long, Tuned> tuned;
   // kernel timing hook
   bool profiling = false;
+  int prof_every = 1;        // time one launch in prof_every
+  long long prof_calls = 0;  // launches seen since profiling was enabled
   std::vector<cudaEvent_t> prof_events;  // pairs (start, stop)
   int prof_used = 0;                     // pairs recorded since the last query
 };
@@ -81,6 +83,7 @@ constexpr int kProfPairs = 4096;
 // Start / stop events around one kernel launch when profiling is on.
 int prof_begin(atdct16_plan_t plan, cudaStream_t stream) {
   if (!plan->profiling || plan->prof_used >= kProfPairs) return -1;
+  if (plan->prof_calls++ % plan->prof_every != 0) return -1;
   const int k = plan->prof_used++;
   if (cudaEventRecord(plan->prof_events[2 * k], stream) != cudaSuccess) return -1;
   return k;
@@ -449,14 +452,16 @@ atdct16_status atdct16_psnr(atdct16_dtype dtype, const void* d_a, int64_t pitch_
   return from_cuda(launch_psnr_pair(dtype, d_a, pitch_a, d_b, pitch_b, w, h, d_out, stream));
 }
 
-atdct16_status atdct16_plan_set_profiling(atdct16_plan_t plan, int32_t enable) {
-  if (!plan) return ATDCT16_EINVAL;
-  if (enable && plan->prof_events.empty()) {
+atdct16_status atdct16_plan_set_profiling(atdct16_plan_t plan, int32_t every) {
+  if (!plan || every < 0) return ATDCT16_EINVAL;
+  if (every && plan->prof_events.empty()) {
     plan->prof_events.resize(2 * kProfPairs, nullptr);
     for (auto& ev : plan->prof_events)
       if (cudaEventCreate(&ev) != cudaSuccess) return ATDCT16_ECUDA;
   }
-  plan->profiling = enable != 0;
+  plan->profiling = every != 0;
+  plan->prof_every = every > 0 ? every : 1;
+  plan->prof_calls = 0;
   plan->prof_used = 0;
   return ATDCT16_OK;
 }

@@ -331,6 +331,25 @@ def test_invalid_arguments_rejected(torch, plan):
     assert plan.last_device_status() == atdct16.OK
 
 
+def test_profiling_hook_samples_every_nth_launch(torch, plan):
+    img = dev_image(torch, synth.ar1_image(64, 256, 0.9, 2))
+    out = empty_like_img(torch, 64, 256, torch.uint8)
+    psnr = torch.empty(1, dtype=torch.float64, device="cuda")
+    d = [atdct16.image(img, out, 36)]
+    for every, calls, want in ((1, 5, 5), (3, 7, 3), (8, 8, 1)):
+        plan.set_profiling(True, every=every)
+        for _ in range(calls):
+            plan.compress_zonal(d, psnr)
+        n, ms = plan.profile()
+        assert n == want and ms > 0.0
+    plan.set_profiling(False)
+    plan.compress_zonal(d, psnr)
+    assert plan.profile() == (0, 0.0)
+    with pytest.raises(atdct16.Atdct16Error) as e:
+        plan.set_profiling(True, every=-1)
+    assert e.value.status == atdct16.EINVAL
+
+
 def test_in_tree_library_loaded(torch):
     import os
     path = atdct16.library_path()
