@@ -299,7 +299,7 @@ def quant_phase(torch, atdct16, synth, dev, n_frames, steps, warmup, peak_gbs, c
         for _ in range(max(warmup, 3)):
             plan.compress_quant(descs, psnr, levels=lv, sse=sse)
         torch.cuda.synchronize()
-        plan.set_profiling(True)
+        plan.set_profiling(True, every=4)  # sampled, as in the main phase
         plan.profile()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
