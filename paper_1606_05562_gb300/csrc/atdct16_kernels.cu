@@ -167,16 +167,6 @@ struct ZonalTile {
   int r;
 };
 
-// 16-byte read-only streaming load that does not allocate in L1: the input
-// is read exactly once, so a fill of the L1 data array would be wasted work.
-__device__ __forceinline__ uint4 ld_stream_na(const uint8_t* ptr) {
-  uint4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(ptr));
-  return v;
-}
-
 // Programmatic dependent launch: a kernel lets the next kernel of its stream
 // (launched with the programmatic-serialisation attribute) be scheduled
 // early; that kernel waits for this grid's completion and memory flush.  The
@@ -512,7 +502,6 @@ constexpr int kMStageUnits = 2 * 128;
 constexpr int kZonalMmaWarpSmemBytes = 16 * (kMUnits + kMStageUnits);
 
 __host__ __device__ constexpr int mma_region(int p) { return p == 0 ? 0 : (p == 1 ? 145 : (p == 2 ? 292 : 437)); }
-__host__ __device__ constexpr int mma_unit(int p, int c, int q) { return mma_region(p) + 8 * c + (c & 14) + q; }
 __device__ __forceinline__ int stage_slot(int b, int r) {
   const int pb = b & 3;
   return 16 * b + (r ^ ((pb & 1) | ((pb & 2) << 1)));
