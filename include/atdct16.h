@@ -50,7 +50,7 @@ typedef enum {
   ATDCT16_ENOMEM = 2,       /* workspace or device memory exhausted */
   ATDCT16_ECUDA = 3,        /* a CUDA runtime call failed */
   ATDCT16_ETIMEOUT = 4,     /* a bounded device-side wait expired */
-  ATDCT16_EUNSUPPORTED = 5, /* valid request this build does not support */
+  ATDCT16_EUNSUPPORTED = 5, /* a valid request this library does not support */
   ATDCT16_EDEVICE = 6       /* a kernel's own bounds checks rejected work */
 } atdct16_status;
 
