@@ -339,7 +339,8 @@ atdct16_status atdct16_inverse(atdct16_plan_t plan, atdct16_dtype dtype, const i
   if (w <= 0 || h <= 0 || (w & 15) || (h & 15) || pitch < (int64_t)w * elem || (pitch & 15)) return ATDCT16_EINVAL;
   if (!aligned16(d_dst) || !aligned16(d_coef)) return ATDCT16_EINVAL;
   plan->last_stream = stream;
-  return from_cuda(launch_inverse(dtype, d_coef, w, h, d_dst, pitch, plan->zigzag, plan->num_sms, stream));
+  return from_cuda(
+      launch_inverse(dtype, d_coef, w, h, d_dst, pitch, plan->zigzag, plan->d_status, plan->num_sms, stream));
 }
 
 atdct16_status atdct16_forward_1d(atdct16_plan_t plan, atdct16_dtype dtype, const void* d_src, int64_t count,
@@ -487,7 +488,7 @@ atdct16_status atdct16_last_device_status(atdct16_plan_t plan) {
   if (plan->last_stream && cudaStreamSynchronize(plan->last_stream) != cudaSuccess) return ATDCT16_ECUDA;
   int v = 0;
   if (cudaMemcpy(&v, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return ATDCT16_ECUDA;
-  return v == kDevOk ? ATDCT16_OK : ATDCT16_EDEVICE;
+  return v == kDevOk ? ATDCT16_OK : (v == kDevTimeout ? ATDCT16_ETIMEOUT : ATDCT16_EDEVICE);
 }
 
 }  // extern "C"

@@ -20,14 +20,13 @@
 // range).  Lane (p, j) = (lane & 3, lane >> 2) owns rows (and later
 // columns) 2j, 2j+1 of blocks p and p + 4.  Every global access moves whole
 // 32-byte sectors: image rows as 16-byte segments, coefficient blocks as
-// 1 KB bulk copies (forward) or 512-byte cp.async runs per warp instruction
-// (inverse); the transposition and the reordering go through shared memory:
+// 1 KB bulk copies between global and shared memory (the copy engine, in
+// both directions); the transposition and the reordering go through shared
+// memory:
 //   line buffer  unit(p, c, q) = 138 p + 8 c + (c >> 1) + q (16-byte units):
 //                rows 2q, 2q+1 of column c of blocks p, p + 4;
 //   block stage  the tile's 8 blocks of 256 int32 in their global order
-//                (row-major or scan order), block b at word 264 b; the
-//                row-major inverse instead keeps block b at word 256 b with
-//                16-byte chunk q at q ^ 2 (b & 3).
+//                (row-major or scan order), block b at word 264 b.
 #include <algorithm>
 #include <atomic>
 #include <cstdint>
@@ -43,8 +42,6 @@ namespace {
 
 constexpr int kCWarps = 4;
 constexpr int kCLineUnits = 549;
-constexpr int kCStageUnits = 512;                                    // 8 x 256 int32, in 16-byte units
-constexpr int kCWarpSmemBytes = 16 * (kCLineUnits + kCStageUnits);  // row-major inverse
 
 // W_u = 48 S_u^2 = 48 / nnz_u for rows u = 0..15 of T: nnz_u in {16, 12, 8},
 // i.e. W_u in {3, 4, 6}, coded 0, 1, 2 in two bits per row.
@@ -378,68 +375,114 @@ __device__ __forceinline__ void round_pair(int za, int zb, int& qa, int& qb) {
 }
 
 // Exact inverse with the next tile's coefficients copied in while the current
-// one is inverted.  Row-major: the block stage holds the tile's 8 blocks with
-// 16-byte chunk q of block b at q ^ 2 (b & 3) (word XOR 8 (b & 3)), so that
-// cp.async can fill it directly and each lane reads its two columns as 8-byte
-// pairs without bank conflicts.  Zig-zag: the blocks sit in scan order at a
-// padded stride of 264 words and each lane gathers its columns' words by their
-// scan positions.  After a tile's coefficients are in registers the stage is
-// free and the next copy starts; a tile that needs the split route keeps the
-// stage for its low halves (same word permutation in both layouts) and starts
-// the copy when it is done.
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+// one is inverted.  The tile's 8 blocks arrive as 1 KB bulk copies (the copy
+// engine, completion counted in bytes on a per-warp mbarrier) into the padded
+// stage, block b at word 264 b in its global order.  Row-major: each lane
+// reads its two columns as (Y(u, 2j), Y(u, 2j+1)) pairs, conflict-free with
+// this stride; zig-zag: each lane gathers its columns' words by their scan
+// positions.  After a tile's coefficients are in registers the stage is free
+// and the next copy starts; a tile that needs the split route keeps the stage
+// for its low halves and starts the copy when it is done.  A copy that has
+// not landed within about a second (a bounded wait) sets the plan's status to
+// a timeout and ends the warp.
+constexpr int kCInvWarpSmemBytes = kCPaddedWarpSmemBytes + 16;  // + the warp's mbarrier
+constexpr long long kCWaitCycles = 2000000000LL;                // ~1 s at 2 GHz
+
+__device__ __forceinline__ unsigned smem_u32(const void* ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// one arrival that also announces the bytes the bulk copies will deliver
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// true once the phase with the given parity has completed
+__device__ __forceinline__ bool mbar_done(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ void bulk_load_1k(int* sdst, const int32_t* gsrc, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 1024, [%2];" ::"r"(
+                   smem_u32(sdst)),
+               "l"(gsrc), "r"(smem_u32(bar))
+               : "memory");
+}
+// bounded wait of the whole warp for the phase; false (on every lane) if any lane gave up
+__device__ __forceinline__ bool mbar_wait_warp(unsigned long long* bar, unsigned parity) {
+  const long long t0 = clock64();
+  bool ok = true;
+  while (!mbar_done(bar, parity)) {
+    if (clock64() - t0 > kCWaitCycles) {
+      ok = false;
+      break;
+    }
+  }
+  return __all_sync(0xffffffffu, ok);
 }
 
 template <int kDtype, bool kZigzag>
 __global__ void __launch_bounds__(32 * kCWarps, 3)
-coef_inverse_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __restrict__ dst, long long pitch) {
+coef_inverse_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __restrict__ dst, long long pitch,
+                    int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char csm[];
-  constexpr int kBW = kZigzag ? kCBlockWords : 256;  // block stride in the stage, words
+  constexpr int kBW = kCBlockWords;  // block stride in the stage, words
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int p = lane & 3, j = lane >> 2, jb1 = (j >> 1) & 1;
-  float4* const line = reinterpret_cast<float4*>(csm + warp * (kZigzag ? kCPaddedWarpSmemBytes : kCWarpSmemBytes));
+  float4* const line = reinterpret_cast<float4*>(csm + warp * kCInvWarpSmemBytes);
   int* const stage = reinterpret_cast<int*>(line + kCLineUnits);
-  uint4* const stage4 = reinterpret_cast<uint4*>(stage);
-  const int s8 = 8 * p;  // word XOR of blocks p and p + 4
+  unsigned long long* const bar = reinterpret_cast<unsigned long long*>(stage + 8 * kBW);
+  const int s8 = 8 * p;  // word XOR of the split route's low halves in blocks p and p + 4
   unsigned zr[8];
   if (kZigzag) column_ranks(j, zr);
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  unsigned phase = 0;
   const int wc[2] = {w_of(2 * j), w_of(2 * j + 1)};
   constexpr int kElem = kDtype == 0 ? 1 : 2;
   const int tiles_x = (w + kTileW - 1) / kTileW;
   const int ntiles = tiles_x * (h >> 4);
   const int bpr = w >> 4;
   const int stride = gridDim.x * kCWarps;
+  // The warp's stage reads and writes (generic proxy) are ordered before the
+  // copy engine's writes by the warp barrier before each call and the proxy
+  // fence here.
   auto issue = [&](int t) {
-    if (t < ntiles) {
+    if (t < ntiles && lane == 0) {
       const int ty = t / tiles_x, tx = t - ty * tiles_x;
       const int nb = min(8, (w - tx * kTileW) >> 4);
       const int32_t* const in = coef + ((long long)ty * bpr + tx * 8) * 256;
-#pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        const int b = m >> 1, q = 32 * (m & 1) + lane;
-        if (b < nb) cp_async16(stage4 + (kBW / 4) * b + (kZigzag ? q : q ^ (2 * (b & 3))), in + 256 * b + 4 * q);
-      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive_expect_tx(bar, 1024u * (unsigned)nb);
+      for (int b = 0; b < nb; ++b) bulk_load_1k(stage + kBW * b, in + 256 * b, bar);
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
   };
   issue(blockIdx.x * kCWarps + warp);
   for (int t = blockIdx.x * kCWarps + warp; t < ntiles; t += stride) {
     const int ty = t / tiles_x, tx = t - ty * tiles_x;
     const int nb = min(8, (w - tx * kTileW) >> 4);
     const bool va = p < nb, vb = p + 4 < nb;
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncwarp();
+    if (!mbar_wait_warp(bar, phase)) {
+      if (lane == 0) atomicCAS(status, kDevOk, kDevTimeout);
+      mbar_wait_warp(bar, phase);  // let a late copy land before the warp leaves
+      return;
+    }
+    phase ^= 1u;
     // the lane's columns 2j, 2j+1 of blocks p, p + 4 as (Y(u, 2j), Y(u, 2j+1)) pairs
     int2 ya[16], yb[16];
     unsigned big = 0u;
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       if (!kZigzag) {
-        const int wd = (16 * u + 2 * j) ^ s8;
-        ya[u] = *reinterpret_cast<const int2*>(stage + 256 * p + wd);
-        yb[u] = *reinterpret_cast<const int2*>(stage + 256 * (p + 4) + wd);
+        ya[u] = *reinterpret_cast<const int2*>(stage + kBW * p + 16 * u + 2 * j);
+        yb[u] = *reinterpret_cast<const int2*>(stage + kBW * (p + 4) + 16 * u + 2 * j);
       } else {
         const int* const s0 = stage + kBW * p + rank_of(zr, 0, u);
         const int* const s1 = stage + kBW * p + rank_of(zr, 1, u);
@@ -560,7 +603,6 @@ coef_inverse_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __r
     }
     __syncwarp();  // line buffer reads done before the next tile's writes
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -708,24 +750,24 @@ cudaError_t launch_forward(int dtype, const void* d_src, long long pitch, int w,
 }
 
 cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void* d_dst, long long pitch,
-                           bool zigzag, int num_sms, cudaStream_t stream) {
+                           bool zigzag, int* d_status, int num_sms, cudaStream_t stream) {
   const long long ntiles = (long long)((w + kTileW - 1) / kTileW) * (h >> 4);
   if (ntiles <= 0) return cudaSuccess;
   if (ntiles >= (1LL << 31) - 4096) return cudaErrorInvalidValue;
   const int threads = 32 * kCWarps;
-  const int smem = kCWarps * (zigzag ? kCPaddedWarpSmemBytes : kCWarpSmemBytes);
+  const int smem = kCWarps * kCInvWarpSmemBytes;
   uint8_t* d = static_cast<uint8_t*>(d_dst);
   if (dtype == 0 && zigzag)
     return launch_persistent<coef_inverse_kernel<0, true>>(threads, smem, num_sms, kCWarps, ntiles, stream, d_coef, w,
-                                                           h, d, pitch);
+                                                           h, d, pitch, d_status);
   if (dtype == 0)
     return launch_persistent<coef_inverse_kernel<0, false>>(threads, smem, num_sms, kCWarps, ntiles, stream, d_coef, w,
-                                                            h, d, pitch);
+                                                            h, d, pitch, d_status);
   if (zigzag)
     return launch_persistent<coef_inverse_kernel<1, true>>(threads, smem, num_sms, kCWarps, ntiles, stream, d_coef, w,
-                                                           h, d, pitch);
+                                                           h, d, pitch, d_status);
   return launch_persistent<coef_inverse_kernel<1, false>>(threads, smem, num_sms, kCWarps, ntiles, stream, d_coef, w, h,
-                                                          d, pitch);
+                                                          d, pitch, d_status);
 }
 
 cudaError_t launch_forward_1d(int dtype, const void* d_src, long long count, int32_t* d_coef, int num_sms,
