@@ -95,11 +95,17 @@ const char* atdct16_status_string(atdct16_status s);
  *                  coefficient (u, v) at scan position k: anti-diagonals
  *                  s = u + v in increasing order, even s with u decreasing,
  *                  odd s with v decreasing), the order an entropy coder reads
- *                  them in; without it they are row-major in (u, v).  Other
- *                  bits: ATDCT16_EINVAL.
+ *                  them in; without it they are row-major in (u, v).
+ *                  ATDCT16_PLAN_TEST_STALL_COPIES (failure-path test hook):
+ *                  atdct16_inverse announces 16 bytes more than its bulk
+ *                  copies deliver, so its bounded waits expire (about 2 s per
+ *                  call) and atdct16_last_device_status reports
+ *                  ATDCT16_ETIMEOUT; the context stays usable.  Other bits:
+ *                  ATDCT16_EINVAL.
  * Allocates the plan's workspace (device tables, descriptor ring, partials)
  * with cudaMalloc and pinned host staging with cudaHostAlloc. */
 #define ATDCT16_PLAN_ZIGZAG 1u
+#define ATDCT16_PLAN_TEST_STALL_COPIES 0x80000000u
 atdct16_status atdct16_plan_create(atdct16_plan_t* plan, atdct16_dtype dtype, int32_t max_images,
                                    size_t workspace_budget_bytes, uint32_t flags);
 

@@ -16,6 +16,7 @@ from . import build as _build
 
 U8, I16 = 0, 1
 PLAN_ZIGZAG = 1  # ATDCT16_PLAN_ZIGZAG
+PLAN_TEST_STALL_COPIES = 0x80000000  # ATDCT16_PLAN_TEST_STALL_COPIES (failure-path test hook)
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EDEVICE = range(7)
 
 

@@ -18,6 +18,7 @@ struct atdct16_plan_st {
   int device = 0;
   atdct16_dtype dtype = ATDCT16_U8;
   bool zigzag = false;                  // ATDCT16_PLAN_ZIGZAG: block coefficients / levels in zig-zag order
+  bool stall_copies = false;            // ATDCT16_PLAN_TEST_STALL_COPIES (failure-path test hook)
   int max_images = 0;
   long long max_tiles = 0;
   int num_sms = 0;
@@ -245,13 +246,14 @@ atdct16_status atdct16_plan_destroy(atdct16_plan_t plan) {
 
 atdct16_status atdct16_plan_create(atdct16_plan_t* out, atdct16_dtype dtype, int32_t max_images,
                                    size_t workspace_budget_bytes, uint32_t flags) {
-  if (!out || max_images < 1 || (flags & ~ATDCT16_PLAN_ZIGZAG) != 0 || (dtype != ATDCT16_U8 && dtype != ATDCT16_I16))
+  if (!out || max_images < 1 || (flags & ~(ATDCT16_PLAN_ZIGZAG | ATDCT16_PLAN_TEST_STALL_COPIES)) != 0 || (dtype != ATDCT16_U8 && dtype != ATDCT16_I16))
     return ATDCT16_EINVAL;
   *out = nullptr;
   atdct16_plan_st* plan = new (std::nothrow) atdct16_plan_st();
   if (!plan) return ATDCT16_ENOMEM;
   plan->dtype = dtype;
   plan->zigzag = (flags & ATDCT16_PLAN_ZIGZAG) != 0;
+  plan->stall_copies = (flags & ATDCT16_PLAN_TEST_STALL_COPIES) != 0;
   plan->max_images = max_images;
   if (cudaGetDevice(&plan->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device) != cudaSuccess) {
@@ -340,7 +342,8 @@ atdct16_status atdct16_inverse(atdct16_plan_t plan, atdct16_dtype dtype, const i
   if (!aligned16(d_dst) || !aligned16(d_coef)) return ATDCT16_EINVAL;
   plan->last_stream = stream;
   return from_cuda(
-      launch_inverse(dtype, d_coef, w, h, d_dst, pitch, plan->zigzag, plan->d_status, plan->num_sms, stream));
+      launch_inverse(dtype, d_coef, w, h, d_dst, pitch, plan->zigzag, plan->d_status, plan->stall_copies ? 16u : 0u,
+                     plan->num_sms, stream));
 }
 
 atdct16_status atdct16_forward_1d(atdct16_plan_t plan, atdct16_dtype dtype, const void* d_src, int64_t count,

@@ -428,7 +428,7 @@ __device__ __forceinline__ bool mbar_wait_warp(unsigned long long* bar, unsigned
 template <int kDtype, bool kZigzag>
 __global__ void __launch_bounds__(32 * kCWarps, 3)
 coef_inverse_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __restrict__ dst, long long pitch,
-                    int* __restrict__ status) {
+                    int* __restrict__ status, unsigned extra_tx) {
   extern __shared__ __align__(16) unsigned char csm[];
   constexpr int kBW = kCBlockWords;  // block stride in the stage, words
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -460,7 +460,7 @@ coef_inverse_kernel(const int32_t* __restrict__ coef, int w, int h, uint8_t* __r
       const int nb = min(8, (w - tx * kTileW) >> 4);
       const int32_t* const in = coef + ((long long)ty * bpr + tx * 8) * 256;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive_expect_tx(bar, 1024u * (unsigned)nb);
+      mbar_arrive_expect_tx(bar, 1024u * (unsigned)nb + extra_tx);  // extra_tx = 0 except in the stall test
       for (int b = 0; b < nb; ++b) bulk_load_1k(stage + kBW * b, in + 256 * b, bar);
     }
   };
@@ -750,7 +750,7 @@ cudaError_t launch_forward(int dtype, const void* d_src, long long pitch, int w,
 }
 
 cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void* d_dst, long long pitch,
-                           bool zigzag, int* d_status, int num_sms, cudaStream_t stream) {
+                           bool zigzag, int* d_status, unsigned extra_tx, int num_sms, cudaStream_t stream) {
   const long long ntiles = (long long)((w + kTileW - 1) / kTileW) * (h >> 4);
   if (ntiles <= 0) return cudaSuccess;
   if (ntiles >= (1LL << 31) - 4096) return cudaErrorInvalidValue;
@@ -759,15 +759,15 @@ cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void*
   uint8_t* d = static_cast<uint8_t*>(d_dst);
   if (dtype == 0 && zigzag)
     return launch_persistent<coef_inverse_kernel<0, true>>(threads, smem, num_sms, kCWarps, ntiles, stream, d_coef, w,
-                                                           h, d, pitch, d_status);
+                                                           h, d, pitch, d_status, extra_tx);
   if (dtype == 0)
     return launch_persistent<coef_inverse_kernel<0, false>>(threads, smem, num_sms, kCWarps, ntiles, stream, d_coef, w,
-                                                            h, d, pitch, d_status);
+                                                            h, d, pitch, d_status, extra_tx);
   if (zigzag)
     return launch_persistent<coef_inverse_kernel<1, true>>(threads, smem, num_sms, kCWarps, ntiles, stream, d_coef, w,
-                                                           h, d, pitch, d_status);
+                                                           h, d, pitch, d_status, extra_tx);
   return launch_persistent<coef_inverse_kernel<1, false>>(threads, smem, num_sms, kCWarps, ntiles, stream, d_coef, w, h,
-                                                          d, pitch, d_status);
+                                                          d, pitch, d_status, extra_tx);
 }
 
 cudaError_t launch_forward_1d(int dtype, const void* d_src, long long count, int32_t* d_coef, int num_sms,

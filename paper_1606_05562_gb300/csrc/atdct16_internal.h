@@ -79,7 +79,7 @@ cudaError_t launch_ssim(const ImageJob* d_jobs, int njobs, long long ntiles, flo
 cudaError_t launch_forward(int dtype, const void* d_src, long long pitch, int w, int h, int32_t* d_coef,
                            bool zigzag, int num_sms, cudaStream_t stream);
 cudaError_t launch_inverse(int dtype, const int32_t* d_coef, int w, int h, void* d_dst, long long pitch,
-                           bool zigzag, int* d_status, int num_sms, cudaStream_t stream);
+                           bool zigzag, int* d_status, unsigned extra_tx, int num_sms, cudaStream_t stream);
 cudaError_t launch_forward_1d(int dtype, const void* d_src, long long count, int32_t* d_coef, int num_sms,
                               cudaStream_t stream);
 cudaError_t launch_inverse_1d(int dtype, const int32_t* d_coef, long long count, void* d_dst, int num_sms,

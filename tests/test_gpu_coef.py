@@ -264,3 +264,29 @@ def test_quant_levels_in_plan_order(torch, qp):
             assert np.abs(diff).max() <= 1
         assert qplan.last_device_status() == atdct16.OK
         qplan.close()
+
+
+# ------------------------------------------------- bounded copy waits ---
+def test_inverse_copy_wait_times_out_cleanly(torch):
+    """With the stall test hook the inverse announces more bytes than its bulk
+    copies deliver: every warp's bounded wait expires, the plan's device
+    status reads ETIMEOUT, and the context keeps working."""
+    stall = atdct16.Plan(atdct16.U8, max_images=1, flags=atdct16.PLAN_TEST_STALL_COPIES)
+    x = synth.ar1_image(16, 256, 0.9, 11)
+    y = O.forward_int(x).reshape(-1)
+    coef = torch.from_numpy(y.astype(np.int32)).cuda()
+    out = out_img(torch, 16, 256, torch.uint8)
+    stall.inverse(coef, out, dtype=atdct16.U8)
+    assert stall.last_device_status() == atdct16.ETIMEOUT
+    stall.close()
+    ok = atdct16.Plan(atdct16.U8, max_images=1)
+    got = run_inverse(torch, ok, y, 16, 256, atdct16.U8)
+    assert np.array_equal(got, x)
+    assert ok.last_device_status() == atdct16.OK
+    ok.close()
+
+
+def test_unknown_plan_flags_rejected(torch):
+    with pytest.raises(atdct16.Atdct16Error) as e:
+        atdct16.Plan(atdct16.U8, max_images=1, flags=0x40000000)
+    assert e.value.status == atdct16.EINVAL
