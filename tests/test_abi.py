@@ -65,3 +65,28 @@ def test_host_butterfly_random_vectors(lib):
 def test_null_arguments_rejected_without_gpu(lib):
     assert lib.atdct16_host_butterfly(None, None, 0) == atdct16.EINVAL
     assert lib.atdct16_plan_destroy(None) == atdct16.EINVAL
+
+
+def test_kernel_zigzag_tables_match_the_oracle_scan(tmp_path):
+    """The device-side scan tables (zigzag_word / zigzag_rank, compiled here
+    for the host) against the oracle's own walk of the Sec. 4 scan."""
+    src = tmp_path / "zz.cpp"
+    src.write_text(
+        '#include "atdct16_zigzag.cuh"\n#include <cstdio>\n'
+        "int main() {\n"
+        '  for (int k = 0; k < 256; ++k) std::printf("%d %d\\n", atdct16::zigzag_word(k), atdct16::zigzag_rank(k));\n'
+        "  return 0;\n}\n")
+    exe = tmp_path / "zz"
+    import shutil
+    import subprocess
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    subprocess.run([cxx, "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_1606_05562_gb300", "csrc"),
+                    str(src), "-o", str(exe)], check=True)
+    rows = [tuple(map(int, ln.split())) for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                                 check=True).stdout.split("\n") if ln]
+    order = O.zigzag_order()
+    rank = O.zigzag_rank()
+    assert [w for w, _ in rows] == [16 * u + v for u, v in order]
+    assert [r for _, r in rows] == [int(rank[w >> 4, w & 15]) for w in range(256)]
