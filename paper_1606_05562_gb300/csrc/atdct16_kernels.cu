@@ -862,10 +862,6 @@ __device__ __forceinline__ float i16_hi_m(unsigned w) {
   return __uint_as_float(__byte_perm(w, 0x4B00u, 0x5432u) ^ 0x8000u);
 }
 
-__device__ __forceinline__ float2 f2abs(float2 v) {
-  return make_float2(__uint_as_float(__float_as_uint(v.x) & 0x7fffffffu),
-                     __uint_as_float(__float_as_uint(v.y) & 0x7fffffffu));
-}
 // a + b rounded toward -inf, both halves
 __device__ __forceinline__ float2 f2add_rm(float2 a, float2 b) {
   unsigned long long d;
@@ -1089,8 +1085,8 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         const float k = kq[i][quant_uclass(u)], g = gq[i][quant_uclass(u)];
-        const float2 a = f2abs(y[u]);
-        const float2 t = __fmul2_rn(a, make_float2(k, k));
+        // |Y| k as two scalar multiplies: the absolute value folds into them
+        const float2 t = make_float2(__fmul_rn(fabsf(y[u].x), k), __fmul_rn(fabsf(y[u].y), k));
         const float2 b = __fadd2_rn(t, make_float2(0.5f, 0.5f));
         const float2 f = f2add_rm(b, make_float2(8388608.0f, 8388608.0f));  // floor(b) + 2^23
         const float2 L = __fadd2_rn(f, make_float2(-8388608.0f, -8388608.0f));
