@@ -893,11 +893,12 @@ struct QuantTile {
 
 // Levels leave through the input staging slot of the current tile (free
 // once its rows are in registers): the column pass writes the tile's 8 x 256
-// int16 levels there, row-major in (u, v) with halfword (16 u + v) of block b
-// at (16 u + v) ^ (16 (b & 3)) (conflict-free for the per-column writes),
-// and the warp stores each block as one 512-byte run, gathered in zig-zag
-// order (Sec. 4 scan) when kZigzag.  The copy of the tile after next into
-// that slot starts after the levels have left.
+// int16 levels there in their output order, halfword k of block b at
+// k ^ (16 (b & 3)), with k = 16 u + v row-major (conflict-free per-column
+// writes) or k = the scan position of (u, v) when kZigzag (Sec. 4 scan; at
+// most two lanes per bank), and the warp stores each block as one 512-byte
+// run of 16-byte chunks.  The copy of the tile after next into that slot
+// starts after the levels have left.
 template <bool kLevels, bool kZigzag>
 __global__ void __launch_bounds__(128, 3)
 quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
@@ -1010,11 +1011,13 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
   int wq = -1;
   float kq[2][3], gq[2][3], qstep = 1.f;
   int st = 0;
-  // zig-zag scan positions 8 lane .. 8 lane + 7, one byte each
-  unsigned zzl[2] = {0u, 0u};
+  // scan positions of (u, 2j + i), one byte each: byte u & 3 of word 4 i + (u >> 2)
+  unsigned zzl[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
   if (kLevels && kZigzag) {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) zzl[e >> 2] |= (unsigned)zigzag_word(8 * lane + e) << (8 * (e & 3));
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int u = 0; u < 16; ++u) zzl[4 * i + (u >> 2)] |= (unsigned)zigzag_rank(16 * u + 2 * j + i) << (8 * (u & 3));
   }
   while (true) {
     cp_async_wait<1>();
@@ -1096,7 +1099,7 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
         sacc = __ffma2_rn(e, e, sacc);
         if (kLevels) {
           const int la = (int)(__float_as_uint(f.x) - 0x4B000000u), lb = (int)(__float_as_uint(f.y) - 0x4B000000u);
-          const int hw = (16 * u + c) ^ (16 * p);
+          const int hw = (kZigzag ? (int)((zzl[4 * i + (u >> 2)] >> (8 * (u & 3))) & 0xffu) : (16 * u + c)) ^ (16 * p);
           lvs[256 * p + hw] = (int16_t)(y[u].x < 0.f ? -la : la);
           lvs[256 * (p + 4) + hw] = (int16_t)(y[u].y < 0.f ? -lb : lb);
         }
@@ -1114,17 +1117,7 @@ quant_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
         if (b >= cur.nb) break;
-        uint4 v;
-        if (!kZigzag) {
-          v = reinterpret_cast<const uint4*>(lvs + 256 * b)[lane ^ (2 * (b & 3))];
-        } else {
-          const int16_t* const lb = lvs + 256 * b;
-          unsigned hw[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e)
-            hw[e] = (unsigned short)lb[((zzl[e >> 2] >> (8 * (e & 3))) & 0xffu) ^ (16 * (b & 3))];
-          v = make_uint4(hw[0] | (hw[1] << 16), hw[2] | (hw[3] << 16), hw[4] | (hw[5] << 16), hw[6] | (hw[7] << 16));
-        }
+        const uint4 v = reinterpret_cast<const uint4*>(lvs + 256 * b)[lane ^ (2 * (b & 3))];
         __stcs(reinterpret_cast<uint4*>(gl + 256 * b + 8 * lane), v);
       }
       __syncwarp();
