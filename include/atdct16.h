@@ -133,7 +133,10 @@ atdct16_status atdct16_forward(atdct16_plan_t plan, atdct16_dtype dtype, const v
  * Any int32 coefficients are accepted and give the exact result: tiles whose
  * coefficients all satisfy |Y| < 2^18 run in 32-bit integers (|Z| < 2^31),
  * others in two 32-bit halves combined in 64 bits.  d_coef, d_dst and pitch
- * 16-byte aligned, w, h multiples of 16 (EINVAL otherwise). */
+ * 16-byte aligned, w, h multiples of 16 (EINVAL otherwise).  Each tile's
+ * coefficients arrive by bulk copies whose completion every warp awaits for
+ * at most about a second; an expired wait leaves that part of d_dst
+ * unwritten and makes atdct16_last_device_status report ATDCT16_ETIMEOUT. */
 atdct16_status atdct16_inverse(atdct16_plan_t plan, atdct16_dtype dtype, const int32_t* d_coef,
                                int32_t w, int32_t h, void* d_dst, int64_t pitch,
                                cudaStream_t stream);
