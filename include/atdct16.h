@@ -344,8 +344,10 @@ atdct16_status atdct16_server_stats(atdct16_server_t server, uint64_t* completed
 /* Stops the scheduler after the work in flight, frees everything. */
 atdct16_status atdct16_server_destroy(atdct16_server_t server);
 
-/* Sticky device-side status of the plan (ATDCT16_OK unless a kernel's own
- * checks rejected a descriptor).  Synchronises the plan's last stream. */
+/* Sticky device-side status of the plan: ATDCT16_OK, ATDCT16_EDEVICE when a
+ * kernel's own checks rejected a descriptor, or ATDCT16_ETIMEOUT when a
+ * bounded device-side wait expired (first event wins).  Synchronises the
+ * plan's last stream. */
 atdct16_status atdct16_last_device_status(atdct16_plan_t plan);
 
 /* Kernel timing hook (tracing support; not part of the paper).  With
