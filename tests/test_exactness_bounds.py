@@ -1,0 +1,168 @@
+"""Exactness of the fused zonal kernel's arithmetic for every u8 input, pinned
+by running the kernels' own butterfly source (atdct16_butterfly.cuh) on the
+host over linear forms: every node is a form in the 256 pixels of a block,
+and its exact range over [0, 255]^256 is read off its coefficients.
+
+- forward row and column passes on int16 fields (bias 32768), with the DC
+  row output centred by -2048 as in the kernel: every node must stay in
+  [-32768, 32767], or the packed 32-bit adds would carry between fields;
+- inverse column and row passes on FP32, fed with keep(u, v) W_u W_v Y for
+  every zig-zag prefix r = 1..256: every node must stay below 2^24 in
+  magnitude, so that FP32 holds each one exactly.
+No GPU needed."""
+
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+HARNESS = r"""
+#include <algorithm>
+#include <array>
+#include <cstdio>
+
+namespace atdct16 {
+// a linear form sum_i c[i] x_i + k over the 256 pixels x_i of one block
+struct Form {
+  std::array<long long, 256> c{};
+  long long k = 0;
+};
+static long long g_lo = 0, g_hi = 0;  // extremes of the nodes made since the last reset
+inline void note(const Form& f) {
+  long long lo = f.k, hi = f.k;
+  for (int i = 0; i < 256; ++i) (f.c[i] > 0 ? hi : lo) += 255 * f.c[i];
+  g_lo = std::min(g_lo, lo);
+  g_hi = std::max(g_hi, hi);
+}
+inline Form badd(const Form& a, const Form& b) {
+  Form o;
+  for (int i = 0; i < 256; ++i) o.c[i] = a.c[i] + b.c[i];
+  o.k = a.k + b.k;
+  note(o);
+  return o;
+}
+inline Form bsub(const Form& a, const Form& b) {
+  Form o;
+  for (int i = 0; i < 256; ++i) o.c[i] = a.c[i] - b.c[i];
+  o.k = a.k - b.k;
+  note(o);
+  return o;
+}
+inline Form scaled(const Form& a, long long s) {
+  Form o;
+  for (int i = 0; i < 256; ++i) o.c[i] = s * a.c[i];
+  o.k = s * a.k;
+  return o;
+}
+}  // namespace atdct16
+
+#include "atdct16_butterfly.cuh"
+#include "atdct16_zigzag.cuh"
+
+using atdct16::Form;
+
+static Form X[16][16], R[16][16], Y[16][16], D[16][16], U[16][16];
+
+int main() {
+  for (int m = 0; m < 16; ++m)
+    for (int n = 0; n < 16; ++n) X[m][n].c[16 * m + n] = 1;
+  // forward row pass, then the DC centring of the kernel's int16 column pass
+  atdct16::g_lo = atdct16::g_hi = 0;
+  for (int m = 0; m < 16; ++m) atdct16::fwd16(X[m], R[m]);
+  std::printf("row %lld %lld\n", atdct16::g_lo, atdct16::g_hi);
+  for (int m = 0; m < 16; ++m) R[m][0].k -= 2048;
+  atdct16::g_lo = atdct16::g_hi = 0;
+  for (int m = 0; m < 16; ++m) atdct16::note(R[m][0]);
+  for (int k = 0; k < 16; ++k) {
+    Form col[16], out[16];
+    for (int m = 0; m < 16; ++m) col[m] = R[m][k];
+    atdct16::fwd16(col, out);
+    for (int u = 0; u < 16; ++u) Y[u][k] = out[u];
+  }
+  std::printf("col %lld %lld\n", atdct16::g_lo, atdct16::g_hi);
+  Y[0][0].k += 16 * 2048;  // the centring taken back: Y = T X T^T exactly
+  // W_u = 48 / (number of non-zeros in row u of T), from the butterfly's response
+  int w[16];
+  {
+    long long e[16][16];
+    for (int i = 0; i < 16; ++i) {
+      long long x[16] = {}, y[16];
+      x[i] = 1;
+      atdct16::fwd16(x, y);
+      for (int u = 0; u < 16; ++u) e[u][i] = y[u];
+    }
+    for (int u = 0; u < 16; ++u) {
+      int nnz = 0;
+      for (int i = 0; i < 16; ++i) nnz += e[u][i] != 0;
+      w[u] = 48 / nnz;
+    }
+  }
+  long long in_max = 0, node_max = 0;
+  for (int r = 1; r <= 256; ++r) {
+    atdct16::g_lo = atdct16::g_hi = 0;
+    for (int u = 0; u < 16; ++u)
+      for (int v = 0; v < 16; ++v) {
+        D[u][v] = atdct16::zigzag_rank(16 * u + v) < r ? atdct16::scaled(Y[u][v], (long long)w[u] * w[v]) : Form{};
+        atdct16::note(D[u][v]);
+      }
+    in_max = std::max({in_max, -atdct16::g_lo, atdct16::g_hi});
+    for (int v = 0; v < 16; ++v) {
+      Form col[16], out[16];
+      for (int u = 0; u < 16; ++u) col[u] = D[u][v];
+      atdct16::inv16(col, out);
+      for (int m = 0; m < 16; ++m) U[m][v] = out[m];
+    }
+    for (int m = 0; m < 16; ++m) {
+      Form z[16];
+      atdct16::inv16(U[m], z);
+    }
+    node_max = std::max({node_max, -atdct16::g_lo, atdct16::g_hi});
+  }
+  std::printf("inv %lld %lld\n", in_max, node_max);
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def bounds(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("bounds")
+    src, exe = d / "bounds.cpp", d / "bounds"
+    src.write_text(HARNESS)
+    subprocess.run([cxx, "-std=c++17", "-O2", "-I", os.path.join(ROOT, "paper_1606_05562_gb300", "csrc"),
+                    str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    return {ln.split()[0]: tuple(int(t) for t in ln.split()[1:]) for ln in out.splitlines()}
+
+
+def test_forward_int16_fields_never_overflow(bounds):
+    lo, hi = bounds["row"]
+    assert -4080 <= lo and hi <= 4080  # 16 terms of magnitude <= 255
+    lo, hi = bounds["col"]
+    assert -32768 <= lo and hi <= 32767, (lo, hi)
+    assert (lo, hi) == (-32768, 32640)  # the range the kernel's layout is designed around
+
+
+def test_inverse_nodes_exact_in_fp32(bounds):
+    d_max, node_max = bounds["inv"]
+    assert d_max == 9 * 65280  # the weighted DC, W_0^2 = 9, of an all-255 block
+    assert node_max < 2 ** 24, node_max
+    assert node_max == 1941060
+
+
+def test_weighted_dc_of_a_constant_block(bounds):
+    """The largest weighted input is attained: an all-255 block has Y(0, 0) =
+    256 x 255 (oracle) and weight W_0^2 = 9, i.e. 2304 x 255, the numerator
+    of a reconstruction of 255 everywhere."""
+    y = O.forward_int(np.full((16, 16), 255, dtype=np.uint8))
+    assert int(np.asarray(y).reshape(16, 16)[0, 0]) == 65280
+    assert bounds["inv"][0] == 9 * int(np.asarray(y).reshape(16, 16)[0, 0]) == 2304 * 255
