@@ -34,9 +34,18 @@ struct Form {
   long long k = 0;
 };
 static long long g_lo = 0, g_hi = 0;  // extremes of the nodes made since the last reset
+static long long g_box_lo = 0, g_box_hi = 255;  // every variable ranges over [g_box_lo, g_box_hi]
 inline void note(const Form& f) {
   long long lo = f.k, hi = f.k;
-  for (int i = 0; i < 256; ++i) (f.c[i] > 0 ? hi : lo) += 255 * f.c[i];
+  for (int i = 0; i < 256; ++i) {
+    if (f.c[i] > 0) {
+      hi += g_box_hi * f.c[i];
+      lo += g_box_lo * f.c[i];
+    } else {
+      hi += g_box_lo * f.c[i];
+      lo += g_box_hi * f.c[i];
+    }
+  }
   g_lo = std::min(g_lo, lo);
   g_hi = std::max(g_hi, hi);
 }
@@ -125,6 +134,30 @@ int main() {
     node_max = std::max({node_max, -atdct16::g_lo, atdct16::g_hi});
   }
   std::printf("inv %lld %lld\n", in_max, node_max);
+  // the standalone exact inverse on int32 coefficients, all kept: 32-bit route for
+  // -2^18 <= Y < 2^18, split route on the halves Y_h in [-2^15, 2^15), Y_l in [0, 2^16)
+  const long long boxes[3][2] = {{-(1LL << 18), (1LL << 18) - 1}, {-(1LL << 15), (1LL << 15) - 1}, {0, (1LL << 16) - 1}};
+  for (int b = 0; b < 3; ++b) {
+    atdct16::g_box_lo = boxes[b][0];
+    atdct16::g_box_hi = boxes[b][1];
+    atdct16::g_lo = atdct16::g_hi = 0;
+    for (int u = 0; u < 16; ++u)
+      for (int v = 0; v < 16; ++v) {
+        D[u][v] = Form{};
+        D[u][v].c[16 * u + v] = (long long)w[u] * w[v];
+      }
+    for (int v = 0; v < 16; ++v) {
+      Form col[16], out[16];
+      for (int u = 0; u < 16; ++u) col[u] = D[u][v];
+      atdct16::inv16(col, out);
+      for (int m = 0; m < 16; ++m) U[m][v] = out[m];
+    }
+    for (int m = 0; m < 16; ++m) {
+      Form z[16];
+      atdct16::inv16(U[m], z);
+    }
+    std::printf("int32_%d %lld %lld\n", b, atdct16::g_lo, atdct16::g_hi);
+  }
   return 0;
 }
 """
@@ -166,3 +199,15 @@ def test_weighted_dc_of_a_constant_block(bounds):
     y = O.forward_int(np.full((16, 16), 255, dtype=np.uint8))
     assert int(np.asarray(y).reshape(16, 16)[0, 0]) == 65280
     assert bounds["inv"][0] == 9 * int(np.asarray(y).reshape(16, 16)[0, 0]) == 2304 * 255
+
+
+def test_exact_inverse_int32_routes_never_overflow(bounds):
+    """The standalone inverse of any int32 coefficients: tiles with every
+    -2^18 <= Y < 2^18 run in 32-bit integers, the others transform the halves
+    Y = 2^16 Y_h + Y_l in 32 bits; no node of either route leaves int32."""
+    for key in ("int32_0", "int32_1", "int32_2"):
+        lo, hi = bounds[key]
+        assert -(2 ** 31) <= lo and hi < 2 ** 31, (key, lo, hi)
+    # the exact extreme is 2304 x 2^18 (2304 = 48^2), half the analytic
+    # (sum_u W_u)^2 2^18 = 68^2 2^18 bound
+    assert max(-bounds["int32_0"][0], bounds["int32_0"][1]) == 2304 * 2 ** 18
