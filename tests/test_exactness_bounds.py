@@ -211,3 +211,25 @@ def test_exact_inverse_int32_routes_never_overflow(bounds):
     # the exact extreme is 2304 x 2^18 (2304 = 48^2), half the analytic
     # (sum_u W_u)^2 2^18 = 68^2 2^18 bound
     assert max(-bounds["int32_0"][0], bounds["int32_0"][1]) == 2304 * 2 ** 18
+
+
+def test_u8_rounding_is_exact_for_every_numerator():
+    """The kernels' u8 rounding of X_hat = Z / 2304, restated step by step in
+    IEEE single precision (numpy keeps subnormals): t = fl(Z fl(1/2304)),
+    then fl(t 2^-149) lands on the subnormal grid, whose bit pattern read as
+    int32 is the signed rounded value, saturated to 0..255 as cvt.pack.sat
+    does.  Against round-half-to-even of the exact quotient for every
+    integer |Z| <= 2^24 (every numerator a u8 block can produce lies within
+    +-1941060; larger ones convert to float exactly up to 2^24 and saturate
+    beyond)."""
+    c = np.float32(1.0) / np.float32(2304.0)
+    tiny = np.float32(2.0 ** -149)
+    assert tiny.view(np.int32) == 1
+    step = 1 << 22
+    for lo in range(-(1 << 24), (1 << 24) + 1, step):
+        z = np.arange(lo, min(lo + step, (1 << 24) + 1), dtype=np.int64)
+        t = z.astype(np.float32) * c
+        got = np.clip((t * tiny).view(np.int32), 0, 255)
+        q, rem = np.divmod(z, 2304)
+        want = q + (rem > 1152) + ((rem == 1152) & (q % 2 == 1))
+        assert np.array_equal(got, np.clip(want, 0, 255)), int(z[np.argmax(got != np.clip(want, 0, 255))])
