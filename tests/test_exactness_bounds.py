@@ -134,6 +134,33 @@ int main() {
     node_max = std::max({node_max, -atdct16::g_lo, atdct16::g_hi});
   }
   std::printf("inv %lld %lld\n", in_max, node_max);
+  // the FP32 forward of the standalone u8 path: inputs carried as 2^23 + 256 x,
+  // the DC row output takes back 16 x 2^23, the column pass sees 256 x (row outputs)
+  {
+    static Form Xs[16][16], Rs[16][16];
+    for (int m = 0; m < 16; ++m)
+      for (int n = 0; n < 16; ++n) {
+        Xs[m][n] = Form{};
+        Xs[m][n].c[16 * m + n] = 256;
+        Xs[m][n].k = 1LL << 23;
+      }
+    atdct16::g_lo = atdct16::g_hi = 0;
+    for (int m = 0; m < 16; ++m) atdct16::fwd16(Xs[m], Rs[m]);
+    long long row_lo = atdct16::g_lo, row_hi = atdct16::g_hi;
+    bool offsets_cancel = true;
+    for (int m = 0; m < 16; ++m) {
+      Rs[m][0].k -= 16LL << 23;
+      for (int k = 0; k < 16; ++k) offsets_cancel = offsets_cancel && Rs[m][k].k == 0;
+    }
+    atdct16::g_lo = atdct16::g_hi = 0;
+    for (int k = 0; k < 16; ++k) {
+      Form col[16], out[16];
+      for (int m = 0; m < 16; ++m) col[m] = Rs[m][k];
+      atdct16::fwd16(col, out);
+    }
+    std::printf("fwd_u8_f32 %lld %lld %lld %lld %d\n", row_lo, row_hi, atdct16::g_lo, atdct16::g_hi,
+                offsets_cancel ? 1 : 0);
+  }
   // the standalone exact inverse on int32 coefficients, all kept: 32-bit route for
   // -2^18 <= Y < 2^18, split route on the halves Y_h in [-2^15, 2^15), Y_l in [0, 2^16)
   const long long boxes[3][2] = {{-(1LL << 18), (1LL << 18) - 1}, {-(1LL << 15), (1LL << 15) - 1}, {0, (1LL << 16) - 1}};
@@ -233,3 +260,15 @@ def test_u8_rounding_is_exact_for_every_numerator():
         q, rem = np.divmod(z, 2304)
         want = q + (rem > 1152) + ((rem == 1152) & (q % 2 == 1))
         assert np.array_equal(got, np.clip(want, 0, 255)), int(z[np.argmax(got != np.clip(want, 0, 255))])
+
+
+def test_standalone_u8_forward_exact_in_fp32(bounds):
+    """The standalone forward carries u8 inputs as 2^23 + 256 x: every row
+    node is a multiple of 256 below 2^28 (so exact in FP32), the offsets
+    cancel in every row output but the DC, and every column node, 256 x an
+    integer, stays below 2^24."""
+    row_lo, row_hi, col_lo, col_hi, cancel = bounds["fwd_u8_f32"]
+    assert -(2 ** 28) < row_lo and row_hi < 2 ** 28
+    assert cancel == 1
+    assert -(2 ** 24) < col_lo and col_hi < 2 ** 24
+    assert col_hi == 256 * 65280
