@@ -161,6 +161,20 @@ int main() {
     std::printf("fwd_u8_f32 %lld %lld %lld %lld %d\n", row_lo, row_hi, atdct16::g_lo, atdct16::g_hi,
                 offsets_cancel ? 1 : 0);
   }
+  // the fused kernel's FP32-column variant: integer row outputs v (13-bit fields)
+  // enter the column pass as the floats 2^23 + 2^20 + 256 v
+  {
+    atdct16::g_lo = atdct16::g_hi = 0;
+    for (int k = 0; k < 16; ++k) {
+      Form col[16], out[16];
+      for (int m = 0; m < 16; ++m) {
+        col[m] = atdct16::scaled(R[m][k], 256);
+        col[m].k += (1LL << 23) + (1LL << 20) + 256 * 2048 * (k == 0);  // R[m][0] was centred
+      }
+      atdct16::fwd16(col, out);
+    }
+    std::printf("fwd_f32col %lld %lld\n", atdct16::g_lo, atdct16::g_hi);
+  }
   // the standalone exact inverse on int32 coefficients, all kept: 32-bit route for
   // -2^18 <= Y < 2^18, split route on the halves Y_h in [-2^15, 2^15), Y_l in [0, 2^16)
   const long long boxes[3][2] = {{-(1LL << 18), (1LL << 18) - 1}, {-(1LL << 15), (1LL << 15) - 1}, {0, (1LL << 16) - 1}};
@@ -272,3 +286,11 @@ def test_standalone_u8_forward_exact_in_fp32(bounds):
     assert cancel == 1
     assert -(2 ** 24) < col_lo and col_hi < 2 ** 24
     assert col_hi == 256 * 65280
+
+
+def test_fused_fp32_column_variant_exact(bounds):
+    """The fused kernel's FP32-column variant feeds 2^23 + 2^20 + 256 v into an
+    f32x2 column pass: every node is a multiple of 256 (integer forms times
+    256 plus multiples of 2^20) below 2^28 in magnitude, hence exact."""
+    lo, hi = bounds["fwd_f32col"]
+    assert -(2 ** 28) < lo and hi < 2 ** 28, (lo, hi)
