@@ -56,10 +56,20 @@ def test_host_butterfly_matches_t_on_unit_vectors(lib):
 def test_host_butterfly_random_vectors(lib):
     # the FPGA co-simulation of Sec. 5.2 used 10,000 random 16-point vectors
     rng = np.random.default_rng(1191)
-    for _ in range(2000):
+    for _ in range(10000):
         x = rng.integers(-255, 256, size=16)
         assert atdct16.host_butterfly(x) == list(O.T @ x)
         assert atdct16.host_butterfly(x, inverse=True) == list(O.T.T @ x)
+
+
+def test_host_butterfly_every_pm255_vector(lib):
+    # all 2^16 vectors with entries +-255: the extremes of every output row
+    signs = ((np.arange(1 << 16)[:, None] >> np.arange(16)) & 1) * 2 - 1
+    x = 255 * signs
+    want_f, want_i = x @ O.T.T, x @ O.T
+    for k in range(1 << 16):
+        assert atdct16.host_butterfly(x[k]) == list(want_f[k])
+        assert atdct16.host_butterfly(x[k], inverse=True) == list(want_i[k])
 
 
 def test_null_arguments_rejected_without_gpu(lib):
