@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/atdct16.h"
+#include "atdct16_arena.h"
 #include "atdct16_internal.h"
 
 namespace {
@@ -25,54 +26,6 @@ double now_s() {
   using namespace std::chrono;
   return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
-
-// First-fit allocator over one device arena, 256-byte granules, coalescing.
-class Arena {
- public:
-  void init(size_t size) {
-    size_ = size;
-    free_.clear();
-    free_[0] = size;
-    used_ = 0;
-  }
-  bool alloc(size_t bytes, size_t* off) {
-    bytes = (bytes + 255) & ~size_t(255);
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= bytes) {
-        *off = it->first;
-        const size_t rest = it->second - bytes, start = it->first + bytes;
-        free_.erase(it);
-        if (rest) free_[start] = rest;
-        used_ += bytes;
-        return true;
-      }
-    }
-    return false;
-  }
-  void release(size_t off, size_t bytes) {
-    bytes = (bytes + 255) & ~size_t(255);
-    used_ -= bytes;
-    auto it = free_.emplace(off, bytes).first;
-    auto next = std::next(it);
-    if (next != free_.end() && it->first + it->second == next->first) {
-      it->second += next->second;
-      free_.erase(next);
-    }
-    if (it != free_.begin()) {
-      auto prev = std::prev(it);
-      if (prev->first + prev->second == it->first) {
-        prev->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
-  size_t size() const { return size_; }
-  size_t used() const { return used_; }
-
- private:
-  size_t size_ = 0, used_ = 0;
-  std::map<size_t, size_t> free_;
-};
 
 struct Req {
   uint64_t id;
@@ -100,7 +53,7 @@ struct atdct16_server_st {
   atdct16_server_config cfg{};
   int device = 0;
   unsigned char* arena_base = nullptr;
-  Arena arena;
+  atdct16::Arena arena;
   cudaStream_t h2d = nullptr, d2h = nullptr;
   std::vector<Slot> slots;
   std::mutex mu;
