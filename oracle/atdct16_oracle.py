@@ -447,13 +447,30 @@ def compress_zonal_fp64(img: np.ndarray, r: int, transform: str = "approx") -> d
 # Quantisation with S absorbed (Sec. 2 last paragraph; Sec. 5.3).
 # --------------------------------------------------------------------------
 def qstep(qp: float) -> float:
+    """Quantisation step ``2^(QP/6)``: 1 at QP = 0 and doubling every six
+    points, the step law of the HEVC quantiser that Sec. 5.3 sweeps."""
     return 2.0 ** (qp / 6.0)
 
 
-def quant_levels(coef: np.ndarray, qp: float, precision: str = "fp64") -> np.ndarray:
-    """``level = sign(B) floor(|B| / Qstep + 1/2)`` with ``B = s_u s_v Y``.
+def _quant_quotient_fp64(y: np.ndarray, qp: float) -> np.ndarray:
+    """``|B| / Qstep = |Y| / sqrt(nnz_u nnz_v 2^(QP/3))`` in FP64.
 
-    ``precision="fp64"``: the definition in FP64.
+    ``s_u s_v = 1 / sqrt(nnz_u nnz_v)`` (``nnz = diag(T T^T)``, Sec. 2), so the
+    quotient is one division by the square root of ``nnz_u nnz_v 2^(QP/3)``.
+    Whenever the quotient is rational that radicand is an exact FP64 number
+    whose square root is exact, and a correctly rounded division then lands
+    exactly on every half-integer quotient: the ties of the rounding rule are
+    decided exactly (when the quotient is irrational there are no ties)."""
+    nnz = np.diag(t_t_transpose()).astype(np.float64)
+    den = np.sqrt(nnz[:, None] * nnz[None, :] * 2.0 ** (qp / 3.0))
+    return np.abs(y).astype(np.float64) / den
+
+
+def quant_levels(coef: np.ndarray, qp: float, precision: str = "fp64") -> np.ndarray:
+    """``level = sign(B) floor(|B| / Qstep + 1/2)`` with ``B = s_u s_v Y``
+    (rounding half away from zero).
+
+    ``precision="fp64"``: the definition in FP64, ties decided exactly.
     ``precision="fp32"``: the same decision taken in single precision, as a
     GPU takes it: one rounded FP32 product of the exact integer ``Y`` and the
     FP32 constant ``fp32(s_u s_v / Qstep)``, then ``floor(|p| + 0.5)`` with the
@@ -462,8 +479,8 @@ def quant_levels(coef: np.ndarray, qp: float, precision: str = "fp64") -> np.nda
     s = s_diag()
     y = np.asarray(coef, dtype=np.int64)
     if precision == "fp64":
-        b = y.astype(np.float64) * (s[:, None] * s[None, :]) / qstep(qp)
-        return (np.sign(b) * np.floor(np.abs(b) + 0.5)).astype(np.int64)
+        q = _quant_quotient_fp64(y, qp)
+        return (np.sign(y) * np.floor(q + 0.5)).astype(np.int64)
     if precision == "fp32":
         k = (s[:, None] * s[None, :] / qstep(qp)).astype(np.float32)
         p = y.astype(np.float32) * k

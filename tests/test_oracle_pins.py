@@ -346,12 +346,15 @@ def test_quantiser_fp32_decision_close_to_fp64():
 
 
 def test_quantiser_closed_forms():
-    # QP = 0 -> Qstep = 1: level = round_half_away(B)
+    # QP = 0 -> Qstep = 1: level = round_half_away(Y / sqrt(nnz_u nnz_v)),
+    # decided in exact arithmetic
     y = np.arange(-512, 512).reshape(4, 16, 16)[None]
-    s = O.s_diag()
-    b = y * (s[:, None] * s[None, :])
-    expect = np.sign(b) * np.floor(np.abs(b) + 0.5)
-    assert np.array_equal(O.quant_levels(y, 0, "fp64"), expect)
+    nnz = _nnz_printed()
+    got = O.quant_levels(y, 0, "fp64")
+    for b in range(4):
+        for u in range(16):
+            for v in range(16):
+                assert got[0, b, u, v] == _level_exact(int(y[0, b, u, v]), nnz[u], nnz[v], 0)
     # very fine step reconstructs the residual to within the step
     x = np.random.default_rng(2).integers(-255, 256, size=(32, 32)).astype(np.int16)
     res = O.compress_quant(x, -60)
@@ -360,6 +363,97 @@ def test_quantiser_closed_forms():
     # huge step zeroes everything
     res = O.compress_quant(x, 120)
     assert np.all(res["levels"] == 0) and np.all(res["recon"] == 0)
+
+
+def _nnz_printed():
+    """Non-zeros per row of the printed T (Sec. 2): ``s_u^2 = 1 / nnz_u``."""
+    return [int(np.count_nonzero(row)) for row in O.T]
+
+
+def _level_exact(y: int, nu: int, nv: int, qp: int) -> int:
+    """``sign(B) floor(|B| / Qstep + 1/2)`` for ``B = Y / sqrt(nu nv)`` and
+    ``Qstep = 2^(QP/6)``, decided without rounding error: when ``3 | QP`` the
+    squared quotient ``Y^2 / (nu nv 2^(QP/3))`` is a fraction and the level is
+    the largest L with ``(L - 1/2)^2 <= q^2``; otherwise the quotient is
+    irrational (no ties) and 60-digit decimal arithmetic decides it."""
+    import decimal
+    from fractions import Fraction
+
+    if y == 0:
+        return 0
+    a = abs(y)
+    if qp % 3 == 0:
+        q2 = Fraction(a * a, nu * nv) / (Fraction(2) ** (qp // 3))
+        lo = 0  # (lo - 1/2)^2 <= q2 holds for lo = 0
+        hi = int(math.isqrt(int(q2)) + 2)
+        while lo < hi:  # largest L with L - 1/2 <= q
+            mid = (lo + hi + 1) // 2
+            if (Fraction(2 * mid - 1, 2)) ** 2 <= q2:
+                lo = mid
+            else:
+                hi = mid - 1
+        lev = lo
+    else:
+        with decimal.localcontext() as ctx:
+            ctx.prec = 60
+            q = decimal.Decimal(a) / ((decimal.Decimal(nu * nv)).sqrt() * decimal.Decimal(2) ** (decimal.Decimal(qp) / 6))
+            lev = int((q + decimal.Decimal("0.5")).to_integral_value(rounding=decimal.ROUND_FLOOR))
+    return lev if y > 0 else -lev
+
+
+# Exact half-integer quotients |B| / Qstep (rounded half away from zero):
+# (u, v, Y, QP, level).  nnz = 16 at u in {0, 1, 5, 8}, 12 at {2, 6, 7, 9, 10,
+# 13, 14, 15}, 8 at {3, 4, 11, 12}.
+_QUANT_TIES = [
+    (0, 0, 8, 0, 1), (0, 0, -8, 0, -1), (1, 5, 24, 0, 2), (8, 0, 40, 0, 3), (5, 8, -40, 0, -3),
+    (3, 4, 4, 0, 1), (11, 12, 20, 0, 3), (12, 3, -20, 0, -3),           # Y / 8
+    (2, 6, 12, 6, 1), (9, 13, 60, 6, 3), (14, 15, -36, 6, -2),          # Y / 24
+    (0, 3, 40, 3, 3), (4, 8, -24, 3, -2),                               # Y / 16 (nnz 16 x 8, QP 3)
+    (1, 1, 640, 24, 3), (6, 7, 336, 18, 4), (13, 9, -36, 6, -2),          # Y / 256, Y / 96, Y / 24
+]
+
+
+def test_qstep_law():
+    # Sec. 5.3 sweeps the HEVC quantisation point; its step is 1 at QP 0 and
+    # doubles every six points, i.e. Qstep^6 = 2^QP
+    assert O.qstep(0) == 1.0
+    for k in range(-4, 11):
+        assert O.qstep(6 * k) == 2.0 ** k
+    for qp in range(-30, 64):
+        assert O.qstep(qp) > 0
+        assert O.qstep(qp) ** 6 == pytest.approx(2.0 ** qp, rel=1e-13)
+        assert O.qstep(qp + 6) == pytest.approx(2 * O.qstep(qp), rel=1e-15)
+    assert [round(O.qstep(q), 2) for q in (22, 27, 32, 37)] == [12.7, 22.63, 40.32, 71.84]
+
+
+def test_quant_levels_ties_round_half_away_from_zero():
+    nnz = _nnz_printed()
+    for u, v, y, qp, want in _QUANT_TIES:
+        assert _level_exact(y, nnz[u], nnz[v], qp) == want, (u, v, y, qp)
+        c = np.zeros((16, 16), dtype=np.int64)
+        c[u, v] = y
+        got = O.quant_levels(c[None, None], qp, "fp64")[0, 0]
+        assert got[u, v] == want, (u, v, y, qp, got[u, v])
+        assert np.count_nonzero(got) == (1 if want else 0)
+
+
+@pytest.mark.parametrize("qp", [0, 1, 3, 6, 9, 13, 22, 27, 32, 37, 51])
+def test_quant_levels_match_exact_arithmetic(qp):
+    nnz = _nnz_printed()
+    rng = np.random.default_rng(100 + qp)
+    y = rng.integers(-65280, 65281, size=(1, 3, 16, 16))
+    y[0, 1] = rng.integers(-300, 301, size=(16, 16))
+    q = O.qstep(qp)
+    # exact ties of this QP at the classes where the quotient is rational
+    for u in range(16):
+        for v in range(16):
+            if nnz[u] == nnz[v] and qp % 6 == 0:
+                y[0, 2, u, v] = int(nnz[u] * q) * (2 * ((u + v) % 5) + 1) // 2 * (1 if (u ^ v) & 1 else -1)
+    got = O.quant_levels(y, qp, "fp64")
+    for b in range(3):
+        for u in range(16):
+            for v in range(16):
+                assert got[0, b, u, v] == _level_exact(int(y[0, b, u, v]), nnz[u], nnz[v], qp), (b, u, v)
 
 
 # ------------------------------------------------------------------ PSNR ---
@@ -414,6 +508,64 @@ def test_pins_catch_planted_mistakes():
     t7 = t.copy(); t7[9, 4] = 1; mutants.append((t7, w, p2, zig))            # dropped zero
     for i, m in enumerate(mutants):
         assert not _pins_pass(*m), f"mutant {i} passed the pins"
+
+
+def _quant_pins_pass(qstep_fn, levels_fn):
+    """The quantiser pins above, as one predicate over a (possibly mutated)
+    step law and level function."""
+    if qstep_fn(0) != 1.0:
+        return False
+    if any(abs(qstep_fn(q) ** 6 / 2.0 ** q - 1) > 1e-12 for q in range(-12, 52)):
+        return False
+    nnz = _nnz_printed()
+    for u, v, y, qp, want in _QUANT_TIES:
+        c = np.zeros((16, 16), dtype=np.int64)
+        c[u, v] = y
+        if levels_fn(c[None, None], qp)[0, 0, u, v] != want:
+            return False
+    y = np.random.default_rng(7).integers(-2000, 2001, size=(1, 1, 16, 16))
+    got = levels_fn(y, 27)
+    return all(got[0, 0, u, v] == _level_exact(int(y[0, 0, u, v]), nnz[u], nnz[v], 27)
+               for u in range(16) for v in range(16))
+
+
+def test_quant_pins_catch_planted_mistakes():
+    from oracle.atdct16_oracle import _quant_quotient_fp64 as _quotient
+
+    assert _quant_pins_pass(O.qstep, lambda y, qp: O.quant_levels(y, qp, "fp64"))
+
+    def with_rounding(rnd):
+        def levels(y, qp):
+            q = _quotient(y, qp)
+            return (np.sign(y) * rnd(q)).astype(np.int64)
+        return levels
+
+    def with_step(step):
+        def levels(y, qp):
+            s = O.s_diag()
+            b = y * (s[:, None] * s[None, :]) / step(qp)
+            return (np.sign(b) * np.floor(np.abs(b) + 0.5)).astype(np.int64)
+        return levels
+
+    def with_scale(scale):
+        def levels(y, qp):
+            b = y * scale(O.s_diag()) / O.qstep(qp)
+            return (np.sign(b) * np.floor(np.abs(b) + 0.5)).astype(np.int64)
+        return levels
+
+    exact = lambda y, qp: O.quant_levels(y, qp, "fp64")
+    mutants = [
+        (lambda qp: 2.0 ** (qp / 5.0), with_step(lambda qp: 2.0 ** (qp / 5.0))),                  # wrong slope
+        (lambda qp: 2.0 ** ((qp - 4) / 6.0), with_step(lambda qp: 2.0 ** ((qp - 4) / 6.0))),      # HEVC offset
+        (O.qstep, with_rounding(np.rint)),                                                       # half to even
+        (O.qstep, with_rounding(np.floor)),                                                      # truncation
+        (O.qstep, with_rounding(lambda q: np.ceil(q - 0.5))),                                    # half toward zero
+        (O.qstep, lambda y, qp: exact(np.abs(y), qp)),                                           # sign dropped
+        (O.qstep, with_scale(lambda s: s[:, None] * s[:, None])),                               # s_u^2 for s_u s_v
+        (O.qstep, with_scale(lambda s: np.ones((16, 16)) / 16.0)),                               # S left out
+    ]
+    for i, (st, lv) in enumerate(mutants):
+        assert not _quant_pins_pass(st, lv), f"quantiser mutant {i} passed the pins"
 
 
 # --------------------------------------------------------------------------
