@@ -211,7 +211,8 @@ atdct16_status atdct16_compress_quant(atdct16_plan_t plan, const atdct16_image* 
  *   meaning of d_psnr / d_sse are those of atdct16_compress_zonal.
  * The first call on each device sets that device up (looks up the scratch
  * area's device address and fills its weight table on `stream`); make that
- * first call before any stream capture.  All calls share the scratch area and
+ * first call before any stream capture (while `stream` is being captured it
+ * returns ATDCT16_EUNSUPPORTED and enqueues nothing).  All calls share the scratch area and
  * it keeps the last call's contents: calls that may overlap on the GPU
  * (other streams, other host threads) race on it and must be serialised by
  * the caller. */
@@ -219,6 +220,14 @@ atdct16_status atdct16_compress_quant(atdct16_plan_t plan, const atdct16_image* 
 #define ATDCT16_NOALLOC_MAX_TILES 131072
 atdct16_status atdct16_compress_zonal_noalloc(const atdct16_image* h_images, int32_t n, double* d_psnr,
                                               double* d_sse, cudaStream_t stream);
+/* Device-side status of the last atdct16_compress_zonal_noalloc call on the
+ * current device (the paper has no counterpart: the plan-free callers above
+ * have no plan whose status they could read).  Synchronises `stream`, which
+ * should be the stream of that call, then reads the status word of the
+ * shared scratch area: ATDCT16_OK, or ATDCT16_EDEVICE when the kernel's own
+ * checks rejected a descriptor.  Each call clears the word, so it reports the
+ * last call only.  ATDCT16_EINVAL if no call has set this device up yet. */
+atdct16_status atdct16_noalloc_last_device_status(cudaStream_t stream);
 
 /* Exact-DCT baseline of atdct16_compress_zonal: the same Sec. 4 procedure
  * with the orthonormal 16-point DCT-II (Sec. 3.2, the transform the paper

@@ -85,6 +85,7 @@ _SIGS = {
     "atdct16_last_device_status": (C.c_int, [C.c_void_p]),
     "atdct16_host_butterfly": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32]),
     "atdct16_compress_zonal_noalloc": (C.c_int, [C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "atdct16_noalloc_last_device_status": (C.c_int, [C.c_void_p]),
     "atdct16_batch_create": (C.c_int, [C.c_void_p, C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p, C.c_uint32,
                                        C.c_void_p, C.POINTER(C.c_void_p)]),
     "atdct16_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -370,6 +371,12 @@ def compress_zonal_noalloc(images, psnr, sse=None, stream=None):
     arr = _as_array(images)
     _check(lib().atdct16_compress_zonal_noalloc(arr, len(images), _ptr(psnr), _ptr(sse), _stream(stream)),
            "compress_zonal_noalloc")
+
+
+def noalloc_last_device_status(stream=None) -> int:
+    """Device-side status of the last no-allocation call on the current
+    device (synchronises ``stream``)."""
+    return int(lib().atdct16_noalloc_last_device_status(_stream(stream)))
 
 
 def psnr(a, b, out, dtype=U8, stream=None):

@@ -66,19 +66,6 @@ void zigzag_rank16(int rank[16][16]) {
   }
 }
 
-// Number of non-zero entries in each row of T, read off the factorisation:
-// row i of T = row p(i) of M4 M3 M2 P1 M1, evaluated here by running the
-// library's own butterfly on unit vectors.
-void row_nonzeros(int nnz[16]) {
-  for (int i = 0; i < 16; ++i) nnz[i] = 0;
-  for (int j = 0; j < 16; ++j) {
-    int x[16] = {0}, y[16];
-    x[j] = 1;
-    fwd16(x, y);
-    for (int i = 0; i < 16; ++i) nnz[i] += (y[i] != 0);
-  }
-}
-
 constexpr int kProfPairs = 4096;
 
 // Start / stop events around one kernel launch when profiling is on.

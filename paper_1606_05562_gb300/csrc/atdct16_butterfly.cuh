@@ -144,4 +144,17 @@ ATDCT16_HD void inv16(const V (&y)[16], V (&x)[16]) {
   }
 }
 
+// Number of non-zero entries in each row of T (the diagonal of T T^T, Sec. 2),
+// read off the factorisation by running the butterfly on unit vectors
+// (host code; the scaling S^2 = 1 / nnz and W = 48 / nnz follow from it).
+inline void row_nonzeros(int nnz[16]) {
+  for (int i = 0; i < 16; ++i) nnz[i] = 0;
+  for (int j = 0; j < 16; ++j) {
+    int x[16] = {0}, y[16];
+    x[j] = 1;
+    fwd16(x, y);
+    for (int i = 0; i < 16; ++i) nnz[i] += (y[i] != 0);
+  }
+}
+
 }  // namespace atdct16

@@ -22,6 +22,7 @@
 #include "../../include/atdct16.h"
 #include "atdct16_butterfly.cuh"
 #include "atdct16_internal.h"
+#include "atdct16_zigzag.cuh"
 
 namespace atdct16 {
 namespace {
@@ -89,23 +90,14 @@ atdct16_status setup_device(int dev, cudaStream_t stream, DeviceSetup** out) {
       if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ATDCT16_ECUDA;
       int sms = 0;
       if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return ATDCT16_ECUDA;
+      // Stream capture would record the table fill instead of running it, and
+      // the synchronisation below would then fail: refuse before enqueuing.
+      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return ATDCT16_ECUDA;
+      if (cap != cudaStreamCaptureStatusNone) return ATDCT16_EUNSUPPORTED;
       TableSeed seed;
-      int idx = 0;
-      for (int sd = 0; sd <= 30; ++sd) {  // zig-zag, JPEG convention extended to 16x16
-        const int lo = sd > 15 ? sd - 15 : 0, hi = sd < 15 ? sd : 15;
-        if (sd % 2 == 0) {
-          for (int u = hi; u >= lo; --u) seed.rank[u * 16 + (sd - u)] = (unsigned char)idx++;
-        } else {
-          for (int v = hi; v >= lo; --v) seed.rank[(sd - v) * 16 + v] = (unsigned char)idx++;
-        }
-      }
-      for (int i = 0; i < 16; ++i) seed.nnz[i] = 0;
-      for (int j = 0; j < 16; ++j) {
-        int x[16] = {0}, y[16];
-        x[j] = 1;
-        fwd16(x, y);
-        for (int i = 0; i < 16; ++i) seed.nnz[i] += (y[i] != 0);
-      }
+      for (int w = 0; w < 256; ++w) seed.rank[w] = (unsigned char)zigzag_rank(w);  // Sec. 4 scan
+      row_nonzeros(seed.nnz);
       noalloc_fill_weights<<<64, 256, 0, stream>>>(seed, static_cast<unsigned char*>(p));
       // later calls may come on other streams: the table must be complete
       if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(stream) != cudaSuccess) return ATDCT16_ECUDA;
@@ -122,6 +114,18 @@ atdct16_status setup_device(int dev, cudaStream_t stream, DeviceSetup** out) {
 }  // namespace atdct16
 
 using namespace atdct16;
+
+extern "C" atdct16_status atdct16_noalloc_last_device_status(cudaStream_t stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ATDCT16_ECUDA;
+  if (dev < 0 || dev >= kMaxDevices || !g_setup[dev].ready.load(std::memory_order_acquire)) return ATDCT16_EINVAL;
+  int v = 0;
+  if (cudaMemcpyFromSymbolAsync(&v, g_noalloc_scratch, sizeof(int), kOffStatus, cudaMemcpyDeviceToHost, stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return ATDCT16_ECUDA;
+  return v == kDevOk ? ATDCT16_OK : (v == kDevTimeout ? ATDCT16_ETIMEOUT : ATDCT16_EDEVICE);
+}
 
 extern "C" atdct16_status atdct16_compress_zonal_noalloc(const atdct16_image* h_images, int32_t n, double* d_psnr,
                                                          double* d_sse, cudaStream_t stream) {

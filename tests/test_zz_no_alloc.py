@@ -1,17 +1,20 @@
-"""The zonal entry point that allocates nothing, against the plan-based one.
+"""The zonal entry point that allocates nothing, against the plan-based one
+and against the CPU oracle.
 
 Callers that cannot allocate device memory while they compress (fixed memory
 budgets, latency-critical paths, applications whose own allocator owns the
 device) use atdct16_compress_zonal_noalloc.  Its results must equal those of
-atdct16_compress_zonal, with the same tolerances as the other parity tests,
-on two calls in a row (the second call reuses the shared scratch area).  This
-file is collected last on purpose."""
+atdct16_compress_zonal and of the oracle's exact reconstruction, with the same
+tolerances as the other parity tests, on two calls in a row (the second call
+reuses the shared scratch area), and its plan-free status read must report
+success after each good call.  This file is collected last on purpose."""
 
 import math
 
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1606_05562_gb300 import atdct16, build, synth
 
 pytestmark = pytest.mark.gpu
@@ -63,6 +66,15 @@ def test_noalloc_matches_plan_path_twice(torch):
             else:
                 assert pg == pytest.approx(pr, rel=PSNR_RTOL, abs=1e-5)
         np.testing.assert_allclose(got[2], ref[2], rtol=PSNR_RTOL)
+        assert atdct16.noalloc_last_device_status() == atdct16.OK
+        # the oracle's exact route (Sec. 4 procedure), image by image
+        for im, r, out, pg in zip(imgs, rs, got[0], got[1]):
+            want = O.compress_zonal_exact(im, r)
+            assert np.array_equal(out, want["recon_u8"])
+            if math.isinf(want["psnr"]):
+                assert math.isinf(pg)
+            else:
+                assert pg == pytest.approx(want["psnr"], rel=PSNR_RTOL, abs=1e-5)
     plan.close()
 
 
