@@ -78,28 +78,39 @@ def single_image_256(seed: int = 1) -> np.ndarray:
     return ar1_image(256, 256, 0.95, seed)
 
 
-def image_batch_512(n: int = 64, side: int = 512, first_seed: int = 100) -> np.ndarray:
-    """``n`` uint8 images; the first half AR(1) rho=0.95, the second half
-    AR(1) rho=0.80 plus N(0, 8^2) noise.  Shape (n, side, side)."""
-    out = np.empty((n, side, side), dtype=np.uint8)
-    for i in range(n):
-        if i < n // 2:
-            out[i] = ar1_image(side, side, 0.95, first_seed + i)
-        else:
-            out[i] = ar1_image(side, side, 0.80, first_seed + i, noise_sigma=8.0)
+def batch_image(i: int, n: int = 64, side: int = 512, first_seed: int = 100) -> np.ndarray:
+    """Image ``i`` of the ``n``-image batch: the first half AR(1) rho=0.95,
+    the second half AR(1) rho=0.80 plus N(0, 8^2) noise; seed first_seed + i."""
+    if i < n // 2:
+        return ar1_image(side, side, 0.95, first_seed + i)
+    return ar1_image(side, side, 0.80, first_seed + i, noise_sigma=8.0)
+
+
+def image_batch_512(n: int = 64, side: int = 512, first_seed: int = 100, indices=None) -> np.ndarray:
+    """The images ``indices`` (default: all) of the ``n``-image batch of
+    :func:`batch_image`.  Shape (len(indices), side, side)."""
+    idx = list(range(n)) if indices is None else list(indices)
+    out = np.empty((len(idx), side, side), dtype=np.uint8)
+    for k, i in enumerate(idx):
+        out[k] = batch_image(i, n, side, first_seed)
     return out
 
 
-def residual_frames(n_frames: int, luma=(1088, 1920), seed: int = 3):
-    """4:2:0 int16 residual frames: list of (Y, Cb, Cr) planes."""
+N_VIDEO_FRAMES = 240
+
+
+def residual_frame(index: int, luma=(1088, 1920), seed: int = 3):
+    """Frame ``index`` of the 4:2:0 int16 residual sequence: (Y, Cb, Cr)."""
     ly, lx = luma
-    frames = []
-    for f in range(n_frames):
-        s = seed * 1000003 + 3 * f
-        frames.append((laplacian_residual(ly, lx, s),
-                       laplacian_residual(ly // 2, lx // 2, s + 1),
-                       laplacian_residual(ly // 2, lx // 2, s + 2)))
-    return frames
+    s = seed * 1000003 + 3 * index
+    return (laplacian_residual(ly, lx, s),
+            laplacian_residual(ly // 2, lx // 2, s + 1),
+            laplacian_residual(ly // 2, lx // 2, s + 2))
+
+
+def residual_frames(n_frames: int, luma=(1088, 1920), seed: int = 3, first: int = 0):
+    """Frames ``first .. first + n_frames - 1`` of the residual sequence."""
+    return [residual_frame(f, luma, seed) for f in range(first, first + n_frames)]
 
 
 def mixed_sizes(n: int, lo: int, hi: int, seed: int) -> list:

@@ -292,6 +292,33 @@ def test_quant_bench_configuration_sampled(torch, zigzag):
     plan.close()
 
 
+@pytest.mark.parametrize("qp", synth.QUANT_QP_SWEEP)
+def test_quant_fp32_against_fp64_definition(torch, qplan, qp):
+    # The FP32 quantiser (S absorbed, Sec. 2 last paragraph) against the FP64
+    # definition at the operating points of Sec. 5.3, on one 4:2:0 frame
+    # (3.1 M coefficients): level flips well under 1e-6 of the coefficients,
+    # each by one step; PSNR within 1e-5; int16 planes within rounding of the
+    # FP64 reconstruction away from blocks whose levels flipped.
+    planes = list(synth.residual_frame(7))
+    outs, psnr, lev = run_quant(torch, qplan, planes, [qp] * 3)
+    n = flips = 0
+    off = 0
+    for plane, out, p in zip(planes, outs, psnr):
+        ref = O.compress_quant(plane, qp, precision="fp64")
+        want = ref["levels"]
+        got = lev[off:off + plane.size].reshape(want.shape)
+        off += plane.size
+        d = got != want
+        flips += int(d.sum())
+        n += plane.size
+        assert np.all(np.abs(got - want) <= 1)
+        assert abs(p - ref["psnr"]) <= PSNR_RTOL * abs(ref["psnr"])
+        flipped = O.from_blocks(np.broadcast_to(d.any(axis=(2, 3))[:, :, None, None], d.shape))
+        err = np.abs(out.astype(np.float64) - ref["recon"])
+        assert np.all(err[~flipped] <= 0.5 + 1e-3)
+    assert flips / n < 1e-6, (flips, n)
+
+
 # --------------------------------------------------------------- PSNR ---
 def test_psnr_pair(torch):
     a = synth.ar1_image(64, 80, 0.9, 1)
