@@ -300,7 +300,7 @@ def transform_matrix(torch, atdct16, dev):
     plan.forward_1d(eye, coef, dtype=atdct16.I16)
     torch.cuda.synchronize()
     plan.close()
-    return coef.view(16, 16).t().to(torch.float64).contiguous()  # column k = T e_k
+    return coef.view(16, 16).t().to(torch.float64).contiguous()  # T[u, k]: column k = T e_k
 
 
 def quant_phase(torch, atdct16, synth, dev, n_frames, chunk, steps, warmup, peak_gbs, cpu_oracle=False):
@@ -325,7 +325,7 @@ def quant_phase(torch, atdct16, synth, dev, n_frames, chunk, steps, warmup, peak
     rplan = atdct16.Plan(atdct16.I16, max_images=per_chunk * nq, workspace_bytes=1 << 30)
     zplan = atdct16.Plan(atdct16.I16, max_images=per_chunk * nq, workspace_bytes=1 << 30, zigzag=True)
     tmat = transform_matrix(torch, atdct16, dev)
-    nnz = (tmat.t() != 0).sum(dim=1).to(torch.float64)  # non-zeros per row of T
+    nnz = (tmat != 0).sum(dim=1).to(torch.float64)  # non-zeros per row of T
     sq = 1.0 / torch.sqrt(nnz[:, None] * nnz[None, :])   # s_u s_v
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     tot_ms = tot_kms = 0.0
@@ -399,7 +399,7 @@ def quant_phase(torch, atdct16, synth, dev, n_frames, chunk, steps, warmup, peak
             r["coefficients"] += int(y.shape[0]) * 256
             r["level_flips_vs_fp64"] += int((d != 0).sum())
             r["max_level_diff"] = max(r["max_level_diff"], int(d.max()))
-            rec = torch.einsum("um,buv,vn->bmn", tmat.t(), l64 * sq * qs, tmat.t())  # T^T (S B' S) T
+            rec = torch.einsum("um,buv,vn->bmn", tmat, l64 * sq * qs, tmat)  # T^T (S B' S) T
             err2 = (y * sq - l64 * qs) ** 2  # Parseval: (B - B')^2
             boff = 0
             for i, p in enumerate(planes):
