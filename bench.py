@@ -144,12 +144,13 @@ def measured_peak_hbm():
 
 
 def kernel_source_sha256():
-    """Hash of the zonal kernel's source: the headers it includes and the part
-    of atdct16_kernels.cu before the quantisation kernel (its helpers and the
-    kernel itself)."""
+    """Hash of the zonal kernels' source: the headers they include, the
+    small-extent kernels with the class split, and the part of
+    atdct16_kernels.cu before the quantisation kernel (the general kernel)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1606_05562_gb300", "csrc")
-    for f in ("atdct16_butterfly.cuh", "atdct16_ops.cuh", "atdct16_internal.h"):
+    for f in ("atdct16_butterfly.cuh", "atdct16_ops.cuh", "atdct16_internal.h", "atdct16_device.cuh",
+              "atdct16_zonal_box.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     with open(os.path.join(csrc, "atdct16_kernels.cu"), "rb") as fh:

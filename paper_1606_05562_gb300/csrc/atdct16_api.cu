@@ -100,7 +100,8 @@ atdct16_status check_image(const atdct16_image& im, int elem, bool need_dst) {
 // overlaps the previous call's kernels) and `stream` waits for it.  While
 // `stream` is being captured into a graph the upload goes on `stream` itself.
 atdct16_status stage_jobs(atdct16_plan_t plan, const atdct16_image* h_images, int32_t n, int elem,
-                          cudaStream_t stream, long long* ntiles_out, bool with_level_base, bool ssim_tiles = false) {
+                          cudaStream_t stream, long long* ntiles_out, bool with_level_base, bool ssim_tiles = false,
+                          ZonalSplit* zonal_split = nullptr) {
   const int b = plan->buf ^ 1;
   if (plan->uploaded_pending[b]) {
     if (cudaEventSynchronize(plan->uploaded[b]) != cudaSuccess) return ATDCT16_ECUDA;
@@ -130,9 +131,11 @@ atdct16_status stage_jobs(atdct16_plan_t plan, const atdct16_image* h_images, in
     blocks += (long long)(im.width / 16) * (im.height / 16);
   }
   if (tiles > plan->max_tiles) return ATDCT16_ENOMEM;
+  // zonal calls: the class-ordered copy for the kernels follows the table
+  if (zonal_split) zonal_order(hj, n, hj + n, zonal_split);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return ATDCT16_ECUDA;
-  const size_t bytes = sizeof(ImageJob) * n;
+  const size_t bytes = sizeof(ImageJob) * n * (zonal_split ? 2 : 1);
   cudaError_t e = cudaSuccess;
   if (cap == cudaStreamCaptureStatusNone) {
     if (plan->consumed_pending[b]) e = cudaStreamWaitEvent(plan->copy_stream, plan->consumed[b], 0);
@@ -248,7 +251,7 @@ atdct16_status atdct16_plan_create(atdct16_plan_t* out, atdct16_dtype dtype, int
     return ATDCT16_ECUDA;
   }
   const size_t budget = workspace_budget_bytes ? workspace_budget_bytes : (size_t)256 << 20;
-  const size_t fixed = sizeof(ImageJob) * max_images +
+  const size_t fixed = 4 * sizeof(ImageJob) * max_images +
                        sizeof(float2) * kZonalTableEntries + sizeof(float4) * kQuantTableEntries + 256;
   if (budget <= fixed + 1024 * sizeof(float)) {
     delete plan;
@@ -281,20 +284,22 @@ atdct16_status atdct16_plan_create(atdct16_plan_t* out, atdct16_dtype dtype, int
   }
 
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMalloc(&plan->d_jobs_buf[0], 2 * sizeof(ImageJob) * max_images);
+  // two descriptor buffers of 2 max_images each: a zonal call stores its
+  // table followed by the class-ordered copy the kernels read
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_jobs_buf[0], 4 * sizeof(ImageJob) * max_images);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_wtab, sizeof(float2) * kZonalTableEntries);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_qtab, sizeof(float4) * kQuantTableEntries);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_tile_sse, sizeof(float) * plan->max_tiles);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_status, sizeof(int));
-  if (e == cudaSuccess) e = cudaHostAlloc(&plan->h_jobs_buf[0], 2 * sizeof(ImageJob) * max_images, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc(&plan->h_jobs_buf[0], 4 * sizeof(ImageJob) * max_images, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking);
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
     e = cudaEventCreateWithFlags(&plan->uploaded[b], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->consumed[b], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) {
-    plan->d_jobs_buf[1] = plan->d_jobs_buf[0] + max_images;
-    plan->h_jobs_buf[1] = plan->h_jobs_buf[0] + max_images;
+    plan->d_jobs_buf[1] = plan->d_jobs_buf[0] + 2 * max_images;
+    plan->h_jobs_buf[1] = plan->h_jobs_buf[0] + 2 * max_images;
     plan->d_jobs = plan->d_jobs_buf[0];
     plan->h_jobs = plan->h_jobs_buf[0];
   }
@@ -360,11 +365,12 @@ atdct16_status atdct16_compress_zonal(atdct16_plan_t plan, const atdct16_image* 
     if (h_images[i].r_or_qp < 0 || h_images[i].r_or_qp > 256) return ATDCT16_EINVAL;
   }
   long long ntiles = 0;
-  atdct16_status s = stage_jobs(plan, h_images, n, 1, stream, &ntiles, false);
+  ZonalSplit split;
+  atdct16_status s = stage_jobs(plan, h_images, n, 1, stream, &ntiles, false, false, &split);
   if (s != ATDCT16_OK) return s;
-  const int grid = (int)std::min<long long>(plan->zonal_grid, (ntiles + kZonalWarps - 1) / kZonalWarps);
   const int pk = prof_begin(plan, stream);
-  cudaError_t e = launch_zonal(plan->d_jobs, n, ntiles, plan->d_wtab, plan->d_tile_sse, plan->d_status, grid, stream);
+  cudaError_t e = launch_zonal_ordered(plan->d_jobs + n, split, default_zonal_config(), plan->zonal_grid,
+                                       plan->d_wtab, plan->d_tile_sse, plan->d_status, plan->num_sms, stream);
   prof_end(plan, pk, stream);
   if (e == cudaSuccess)
     e = launch_psnr_finalize(plan->d_jobs, n, ntiles, plan->d_tile_sse, 255.0, d_psnr, d_sse, stream);

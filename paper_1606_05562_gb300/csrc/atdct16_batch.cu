@@ -18,7 +18,8 @@ struct atdct16_batch_st {
   int device = 0;
   int n = 0;
   long long ntiles = 0;
-  ImageJob* d_jobs = nullptr;
+  ImageJob* d_jobs = nullptr;  // the table (n jobs), then its class-ordered copy (n jobs)
+  ZonalSplit split{};
   float* d_tile_sse = nullptr;
   int* d_status = nullptr;
   double* d_psnr = nullptr;
@@ -133,8 +134,8 @@ void file_store(unsigned long long key, const ZonalConfig& cfg, int ctas, float 
 }
 
 cudaError_t launch_batch_once(atdct16_batch_st* b, const ZonalConfig& cfg, int grid, cudaStream_t stream) {
-  cudaError_t e = launch_zonal_config(cfg, b->d_jobs, b->n, b->ntiles, plan_zonal_table(b->plan), b->d_tile_sse,
-                                      b->d_status, grid, stream);
+  cudaError_t e = launch_zonal_ordered(b->d_jobs + b->n, b->split, cfg, grid, plan_zonal_table(b->plan),
+                                       b->d_tile_sse, b->d_status, plan_num_sms(b->plan), stream);
   if (e == cudaSuccess)
     e = launch_psnr_finalize(b->d_jobs, b->n, b->ntiles, b->d_tile_sse, 255.0, b->d_psnr, b->d_sse, stream);
   return e;
@@ -225,7 +226,7 @@ atdct16_status atdct16_batch_create(atdct16_plan_t plan, const atdct16_image* h_
   if (cudaGetDevice(&dev) != cudaSuccess) return ATDCT16_ECUDA;
   if (dev != plan_device(plan)) return ATDCT16_EINVAL;
 
-  std::vector<ImageJob> jobs(n);
+  std::vector<ImageJob> jobs(2 * (size_t)n);
   long long tiles = 0;
   for (int i = 0; i < n; ++i) {
     const atdct16_image& im = h_images[i];
@@ -252,10 +253,11 @@ atdct16_status atdct16_batch_create(atdct16_plan_t plan, const atdct16_image* h_
   b->d_psnr = d_psnr;
   b->d_sse = d_sse;
   b->last_stream = stream;
-  cudaError_t e = cudaMalloc(&b->d_jobs, sizeof(ImageJob) * n);
+  zonal_order(jobs.data(), n, jobs.data() + n, &b->split);
+  cudaError_t e = cudaMalloc(&b->d_jobs, 2 * sizeof(ImageJob) * n);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_tile_sse, sizeof(float) * std::max<long long>(1, tiles));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_jobs, jobs.data(), sizeof(ImageJob) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_jobs, jobs.data(), 2 * sizeof(ImageJob) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
   if (e != cudaSuccess) {
     free_batch(b);

@@ -41,8 +41,8 @@ constexpr int kDevBadJob = 1;
 constexpr int kDevTimeout = 2;  // a bounded wait on an asynchronous copy expired
 
 // Kernel launchers (atdct16_kernels.cu).  All asynchronous on `stream`.
-cudaError_t launch_zonal(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
-                         float* d_tile_sse, int* d_status, int grid, cudaStream_t stream);
+// The zonal launchers take a class-ordered table (see zonal_order below):
+// the partial of a job's tile k goes to d_tile_sse[level_base + k].
 // Launch shapes of the fused zonal kernel (chosen by the batch autotuner).
 constexpr int kZonalF32 = 0;   // integer row pass, FP32 column pass and inverse
 constexpr int kZonalSwar = 1;  // whole forward transform on the integer pipe (int16 SWAR)
@@ -55,9 +55,11 @@ struct ZonalConfig {
 bool zonal_config_supported(const ZonalConfig& c);
 ZonalConfig default_zonal_config();
 int zonal_config_max_ctas_per_sm(const ZonalConfig& c);
+// dependent: a programmatic dependent launch after the previous zonal kernel
+// of the same call; early: let the next kernel be scheduled from the start.
 cudaError_t launch_zonal_config(const ZonalConfig& cfg, const ImageJob* d_jobs, int njobs, long long ntiles,
                                 const float2* d_wtab, float* d_tile_sse, int* d_status, int grid,
-                                cudaStream_t stream);
+                                cudaStream_t stream, bool dependent = false, bool early = false);
 // d_levels (optional, 16-byte aligned): int16 levels per block, row-major
 // in (u, v) or, with zigzag, in zig-zag order.
 cudaError_t launch_quant(const ImageJob* d_jobs, int njobs, long long ntiles, const float4* d_qtab,
@@ -87,6 +89,30 @@ cudaError_t launch_inverse_1d(int dtype, const int32_t* d_coef, long long count,
 cudaError_t launch_psnr_pair(int dtype, const void* d_a, long long pitch_a, const void* d_b,
                              long long pitch_b, int w, int h, double* d_out, cudaStream_t stream);
 int zonal_ctas_per_sm();
+
+// Classes of zonal jobs (atdct16_zonal_box.cu).  A job whose kept zig-zag
+// prefix lies in the K x K low-frequency corner (r <= K (K + 1) / 2, r >= 1)
+// runs the box kernel of the smallest such K in kZonalBoxK; r = 0 and
+// r > 36 run the general kernel.
+constexpr int kZonalBoxClasses = 4;
+constexpr int kZonalBoxK[kZonalBoxClasses] = {1, 3, 6, 8};
+constexpr int kZonalGeneral = kZonalBoxClasses;
+constexpr int kZonalClasses = kZonalBoxClasses + 1;
+struct ZonalSplit {
+  int first[kZonalClasses + 1];     // class c: jobs [first[c], first[c + 1]) of the class-ordered table
+  long long ntiles[kZonalClasses];  // tiles of class c
+};
+int zonal_class_of(int r);
+// Class-ordered copy of a zonal job table of n jobs: grouped by class (table
+// order kept inside a class), each class's tiles numbered from 0 in
+// tile_begin, and level_base = the job's tile_begin in `jobs` (where the
+// kernels write its per-tile partials, which the PSNR finalize reads).
+void zonal_order(const ImageJob* jobs, int n, ImageJob* ordered, ZonalSplit* split);
+// One launch per non-empty class on `stream`; `general` and `general_grid`
+// shape the general kernel's launch.
+cudaError_t launch_zonal_ordered(const ImageJob* d_ordered, const ZonalSplit& split, const ZonalConfig& general,
+                                 int general_grid, const float2* d_wtab, float* d_tile_sse, int* d_status,
+                                 int num_sms, cudaStream_t stream);
 
 }  // namespace atdct16
 

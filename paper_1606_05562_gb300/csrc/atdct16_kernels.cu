@@ -24,6 +24,7 @@
 #include <math_constants.h>
 
 #include "atdct16_butterfly.cuh"
+#include "atdct16_device.cuh"
 #include "atdct16_internal.h"
 #include "atdct16_zigzag.cuh"
 
@@ -32,95 +33,6 @@
 #include <type_traits>
 
 namespace atdct16 {
-
-// --------------------------------------------------------------------------
-// Value types for the generic butterflies.
-// --------------------------------------------------------------------------
-__device__ __forceinline__ float2 f2mul(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
-
-__device__ __forceinline__ unsigned word_of(const uint4& v, int i) {
-  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
-}
-
-// SwarRow word (fields f_lo, f_hi, each value + 4096 < 2^13) -> the exact
-// floats 2^23 + 256 f = 2^23 + 2^20 + 256 value, one byte permute each.
-__device__ __forceinline__ float2 swar_row_f2(unsigned w) {
-  return make_float2(__uint_as_float(__byte_perm(w, 0x00004B00u, 0x5104u)),
-                     __uint_as_float(__byte_perm(w, 0x00004B00u, 0x5324u)));
-}
-
-// Swar16 word (fields f_lo, f_hi < 2^16) -> the exact floats 2^23 + f, one
-// byte permute each.
-__device__ __forceinline__ float2 swar16_f2(unsigned w) {
-  return make_float2(__uint_as_float(__byte_perm(w, 0x00004B00u, 0x5410u)),
-                     __uint_as_float(__byte_perm(w, 0x00004B00u, 0x5432u)));
-}
-
-// d = (c << 16) | (sat_u8(a) << 8) | sat_u8(b)   (PTX cvt.pack semantics)
-__device__ __forceinline__ unsigned pack_u8(unsigned a, unsigned b, unsigned c) {
-  unsigned d;
-  asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-  return d;
-}
-// d = (sat_s16(a) << 16) | sat_s16(b)
-__device__ __forceinline__ unsigned pack_s16(int a, int b) {
-  unsigned d;
-  asm("cvt.pack.sat.s16.s32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-  return d;
-}
-
-// Round half to even of x, clamped to 0..255, as the raw bits of a denormal:
-// fl(x * 2^-149) lands on the denormal grid, whose spacing is 2^-149, so its
-// bit pattern is rne(|x|) with the sign in bit 31.  As a signed 32-bit integer
-// that saturates to 0 for negative x and to 255 above 255 in cvt.pack.sat.
-__device__ __forceinline__ float2 rne_denormal(float2 x) {
-  return __fmul2_rn(x, make_float2(__uint_as_float(1u), __uint_as_float(1u)));
-}
-
-// fp32(1/2304): with it, fl(Z * c) equals Z / 2304 exactly whenever Z / 2304 is
-// a half-integer (Z is then a multiple of 9 and 9 * fp32(1/9) = 1 + 2^-27), and
-// is within 6e-5 of Z / 2304 otherwise, far inside the 1/2304 gap to any .5.
-__constant__ float kInv2304 = 1.0f / 2304.0f;
-
-// The job holding tile t: the last job with tile_begin <= t (tile_begin is
-// increasing and jobs[0].tile_begin = 0), by binary search.
-__device__ __forceinline__ void find_job(const ImageJob* __restrict__ jobs, int njobs, long long t, int& job) {
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(&jobs[mid].tile_begin) <= t) lo = mid; else hi = mid - 1;
-  }
-  job = lo;
-}
-
-// The same job as a 32-way search by the whole warp:
-// each round the lanes probe 32 evenly spaced jobs of the remaining range in
-// parallel, so 512 jobs take two rounds of loads instead of nine dependent
-// ones.  Every lane of the warp must call it; all get the same job.
-__device__ __forceinline__ void warp_find_job(const ImageJob* __restrict__ jobs, int njobs,
-                                              long long t, int& job) {
-  const int lane = threadIdx.x & 31;
-  int lo = 0, hi = njobs;  // the job is in [lo, hi), jobs[lo].tile_begin <= t
-  while (hi - lo > 1) {
-    const int step = (hi - lo + 31) >> 5;
-    const int idx = lo + lane * step;
-    const bool le = idx < hi && __ldg(&jobs[idx].tile_begin) <= t;
-    const unsigned m = __ballot_sync(0xffffffffu, le);  // bit 0 is always set
-    lo += (31 - __clz(m)) * step;
-    hi = min(hi, lo + step);
-  }
-  job = lo;
-}
-
-__device__ __forceinline__ void set_status(int* status, int code) {
-  atomicCAS(status, kDevOk, code);
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // --------------------------------------------------------------------------
 // Fused zonal compression: forward, keep the first r zig-zag coefficients,
@@ -158,43 +70,11 @@ constexpr int kZWUnits = 143;
 constexpr int kZStageUnits = 2 * 4 * 32;  // two tiles of input rows, 4 x 16 bytes per lane
 constexpr int kZonalWarpSmemBytes = 16 * (kZT2Units + kZWUnits + kZStageUnits);
 
-struct ZonalTile {
-  const uint8_t* src;  // row 2j of block p of this lane
-  uint8_t* dst;
-  int src_pitch, dst_pitch;
-  int nb;              // valid 16-pixel blocks in the tile (1..8)
-  int t;               // tile index
-  int r;
-};
-
-// Programmatic dependent launch: a kernel lets the next kernel of its stream
-// (launched with the programmatic-serialisation attribute) be scheduled
-// early; that kernel waits for this grid's completion and memory flush.  The
-// fused kernels trigger as each CTA finishes its tiles, so the finalize's CTAs
-// take the places of departing ones (a trigger at kernel start measured 2 us
-// slower per call).
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait_primary() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-// Asynchronous 16-byte global -> shared copy (L2 only), its group commit and
-// the wait until at most N of this thread's groups are still in flight.
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
-}
-// The same with src_bytes (0 or 16) read and the rest of the 16 filled with zeros.
-__device__ __forceinline__ void cp_async16_zfill(void* smem_dst, const void* gsrc, int src_bytes) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gsrc), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 template <int kWarps, bool kColSwar>
 __global__ void __launch_bounds__(32 * kWarps, 12 / kWarps)
 zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
-             const float2* __restrict__ wtab, float* __restrict__ tile_sse, int* __restrict__ status) {
+             const float2* __restrict__ wtab, float* __restrict__ tile_sse, int* __restrict__ status,
+             int pdl_early) {
   extern __shared__ __align__(16) unsigned char zsmem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int p = lane & 3, j = lane >> 2, jb1 = (j >> 1) & 1;
@@ -213,9 +93,13 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
   const int per_warp = (ntiles + nwarps - 1) / nwarps;
   const int t_first = (blockIdx.x * kWarps + warp) * per_warp;
   const int t_stop = min(ntiles, t_first + per_warp);
-  if (t_first >= t_stop) return;
+  if (pdl_early) pdl_launch_dependents();  // the next class's kernel may be scheduled
+  if (t_first >= t_stop) {
+    pdl_chain_exit();
+    return;
+  }
 
-  int c_t = 0, c_end = 0, tiles_x = 1, tx = 0, nb_last = 8, r_job = 0, src_pitch = 0, dst_pitch = 0;
+  int c_t = 0, c_end = 0, tiles_x = 1, tx = 0, nb_last = 8, r_job = 0, src_pitch = 0, dst_pitch = 0, t_shift = 0;
   const uint8_t* src_band = nullptr;  // this lane's row 2j of block p in tile column 0 of the band
   uint8_t* dst_band = nullptr;
   auto enter = [&](int t) -> bool {   // place the cursor on tile t
@@ -230,6 +114,7 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     const int lt = (int)(t - tb);
     const int ty = lt / tiles_x;
     tx = lt - ty * tiles_x;
+    t_shift = (int)(__ldg(&J->level_base) - (long long)(t - lt));  // partials: level_base + (t - tile_begin)
     src_pitch = (int)__ldg(&J->src_pitch);
     dst_pitch = (int)__ldg(&J->dst_pitch);
     const long long row = (long long)ty * kTileH + 2 * j;
@@ -248,7 +133,7 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     z.src_pitch = src_pitch;
     z.dst_pitch = dst_pitch;
     z.nb = tx == tiles_x - 1 ? nb_last : 8;
-    z.t = c_t;
+    z.t = c_t + t_shift;
     z.r = r_job;
   };
   auto advance = [&]() -> bool {      // false: the job table does not cover the next tile
@@ -279,6 +164,7 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
 
   if (!enter(t_first)) {
     if (lane == 0) set_status(status, kDevBadJob);
+    pdl_chain_exit();
     return;
   }
   int wr = -1;  // r whose weights are in wsm
@@ -462,7 +348,7 @@ zonal_f32_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
   }
   cp_async_wait<0>();
   if (!ok && lane == 0) set_status(status, kDevBadJob);
-  pdl_launch_dependents();  // the PSNR finalize may now take this CTA's place
+  pdl_chain_exit();  // the next kernel (or the PSNR finalize) may now take this CTA's place
 }
 
 // --------------------------------------------------------------------------
@@ -534,7 +420,8 @@ __device__ __forceinline__ unsigned f16x2_of_t(int lo, int hi) { return f16_of_t
 template <int kWarps>
 __global__ void __launch_bounds__(32 * kWarps, 12 / kWarps)
 zonal_mma_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
-                 const float2* __restrict__ wtab, float* __restrict__ tile_sse, int* __restrict__ status) {
+                 const float2* __restrict__ wtab, float* __restrict__ tile_sse, int* __restrict__ status,
+             int pdl_early) {
   extern __shared__ __align__(16) unsigned char msmem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, q = lane & 3;  // MMA fragment coordinates
@@ -582,9 +469,13 @@ zonal_mma_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
   const int per_warp = (ntiles + nwarps - 1) / nwarps;
   const int t_first = (blockIdx.x * kWarps + warp) * per_warp;
   const int t_stop = min(ntiles, t_first + per_warp);
-  if (t_first >= t_stop) return;
+  if (pdl_early) pdl_launch_dependents();  // the next class's kernel may be scheduled
+  if (t_first >= t_stop) {
+    pdl_chain_exit();
+    return;
+  }
 
-  int c_t = 0, c_end = 0, tiles_x = 1, tx = 0, nb_last = 8, r_job = 0, src_pitch = 0, dst_pitch = 0;
+  int c_t = 0, c_end = 0, tiles_x = 1, tx = 0, nb_last = 8, r_job = 0, src_pitch = 0, dst_pitch = 0, t_shift = 0;
   const uint8_t* src_band = nullptr;  // row 0 of the current band, tile column 0
   uint8_t* dst_band = nullptr;        // this lane's row 2j of block p in tile column 0 of the band
   auto enter = [&](int t) -> bool {
@@ -599,6 +490,7 @@ zonal_mma_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     const int lt = (int)(t - tb0);
     const int ty = lt / tiles_x;
     tx = lt - ty * tiles_x;
+    t_shift = (int)(__ldg(&J->level_base) - (long long)(t - lt));  // partials: level_base + (t - tile_begin)
     src_pitch = (int)__ldg(&J->src_pitch);
     dst_pitch = (int)__ldg(&J->dst_pitch);
     const long long row0 = (long long)ty * kTileH;
@@ -617,7 +509,7 @@ zonal_mma_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     z.src_pitch = src_pitch;
     z.dst_pitch = dst_pitch;
     z.nb = tx == tiles_x - 1 ? nb_last : 8;
-    z.t = c_t;
+    z.t = c_t + t_shift;
     z.r = r_job;
   };
   auto advance = [&]() -> bool {
@@ -646,6 +538,7 @@ zonal_mma_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
 
   if (!enter(t_first)) {
     if (lane == 0) set_status(status, kDevBadJob);
+    pdl_chain_exit();
     return;
   }
   bool ok = true;
@@ -829,7 +722,7 @@ zonal_mma_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
   }
   cp_async_wait<0>();
   if (!ok && lane == 0) set_status(status, kDevBadJob);
-  pdl_launch_dependents();  // the PSNR finalize may now take this CTA's place
+  pdl_chain_exit();  // the next kernel (or the PSNR finalize) may now take this CTA's place
 }
 
 // --------------------------------------------------------------------------
@@ -1734,6 +1627,7 @@ static cudaError_t launch_with_smem(K kernel, int grid, int threads, int smem, c
   return cudaGetLastError();
 }
 
+
 template <class K>
 static cudaError_t occupancy_with_smem(int* n, K kernel, int threads, int smem) {
   if (smem > 48 * 1024) {
@@ -1752,20 +1646,21 @@ bool zonal_config_supported(const ZonalConfig& c) { return config_index(c) >= 0;
 
 cudaError_t launch_zonal_config(const ZonalConfig& cfg, const ImageJob* d_jobs, int njobs, long long ntiles,
                                 const float2* d_wtab, float* d_tile_sse, int* d_status, int grid,
-                                cudaStream_t stream) {
+                                cudaStream_t stream, bool dependent, bool early) {
   if (ntiles <= 0) return cudaSuccess;
   if (ntiles >= (1LL << 30)) return cudaErrorInvalidValue;  // tile indices are 32-bit in the kernels
   const int threads = 32 * cfg.warps;
+  const int pe = early ? 1 : 0;
   switch (config_index(cfg)) {
     case 0:
-      return launch_with_smem(zonal_f32_kernel<4, true>, grid, threads, 4 * kZonalWarpSmemBytes, stream, d_jobs,
-                              njobs, ntiles, d_wtab, d_tile_sse, d_status);
+      return launch_chained(zonal_f32_kernel<4, true>, grid, threads, 4 * kZonalWarpSmemBytes, stream, dependent,
+                            d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, pe);
     case 1:
-      return launch_with_smem(zonal_f32_kernel<4, false>, grid, threads, 4 * kZonalWarpSmemBytes, stream, d_jobs,
-                              njobs, ntiles, d_wtab, d_tile_sse, d_status);
+      return launch_chained(zonal_f32_kernel<4, false>, grid, threads, 4 * kZonalWarpSmemBytes, stream, dependent,
+                            d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, pe);
     case 2:
-      return launch_with_smem(zonal_mma_kernel<4>, grid, threads, 4 * kZonalMmaWarpSmemBytes, stream, d_jobs,
-                              njobs, ntiles, d_wtab, d_tile_sse, d_status);
+      return launch_chained(zonal_mma_kernel<4>, grid, threads, 4 * kZonalMmaWarpSmemBytes, stream, dependent,
+                            d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, pe);
   }
   return cudaErrorInvalidValue;
 }
@@ -1783,12 +1678,6 @@ int zonal_config_max_ctas_per_sm(const ZonalConfig& cfg) {
 }
 
 ZonalConfig default_zonal_config() { return ZonalConfig{kZonalSwar, kZonalWarps, 1}; }
-
-cudaError_t launch_zonal(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
-                         float* d_tile_sse, int* d_status, int grid, cudaStream_t stream) {
-  return launch_zonal_config(default_zonal_config(), d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, grid,
-                             stream);
-}
 
 cudaError_t launch_quant(const ImageJob* d_jobs, int njobs, long long ntiles, const float4* d_qtab,
                          int16_t* d_levels, bool zigzag, float* d_tile_sse, int* d_status, int grid,

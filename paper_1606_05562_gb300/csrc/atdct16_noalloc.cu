@@ -9,8 +9,9 @@
 // caller's inputs and outputs is the file-scope scratch array below, which
 // every GPU that loads the library holds until the process exits.
 //
-// The scratch holds the job descriptors, the zonal weight table, the per-tile
-// partial sums and the device status word.  Every call shares it and it keeps
+// The scratch holds the job descriptors (the table and its class-ordered
+// copy that the kernels read), the zonal weight table, the per-tile partial
+// sums and the device status word.  Every call shares it and it keeps
 // the last call's contents; each call rewrites the descriptors, clears the
 // status word and writes every partial it later reads.  Calls that overlap on
 // the GPU (different streams, or several host threads) race on it.
@@ -32,7 +33,7 @@ constexpr long long kNoAllocMaxTiles = 1 << 17;  // 131072 tiles of 16 x 128 pix
 
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 constexpr size_t kOffJobs = 0;
-constexpr size_t kOffStatus = align256(kOffJobs + sizeof(ImageJob) * kNoAllocMaxImages);
+constexpr size_t kOffStatus = align256(kOffJobs + 2 * sizeof(ImageJob) * kNoAllocMaxImages);
 constexpr size_t kOffWtab = align256(kOffStatus + sizeof(int));
 constexpr size_t kOffTiles = align256(kOffWtab + sizeof(float2) * kZonalTableEntries);
 constexpr size_t kScratchBytes = align256(kOffTiles + sizeof(float) * kNoAllocMaxTiles);  // ~1.03 MiB
@@ -45,10 +46,12 @@ struct JobPack {
   ImageJob jobs[kNoAllocMaxImages];
 };
 
-__global__ void noalloc_stage_jobs(const __grid_constant__ JobPack pack, int n, unsigned char* scratch) {
-  ImageJob* jobs = reinterpret_cast<ImageJob*>(scratch + kOffJobs);
+// Copies n descriptors to slot `first` of the scratch's table; the first of
+// a call's two copies also clears the status word.
+__global__ void noalloc_stage_jobs(const __grid_constant__ JobPack pack, int n, int first, unsigned char* scratch) {
+  ImageJob* jobs = reinterpret_cast<ImageJob*>(scratch + kOffJobs) + first;
   for (int i = threadIdx.x; i < n; i += blockDim.x) jobs[i] = pack.jobs[i];
-  if (threadIdx.x == 0) *reinterpret_cast<int*>(scratch + kOffStatus) = kDevOk;
+  if (threadIdx.x == 0 && first == 0) *reinterpret_cast<int*>(scratch + kOffStatus) = kDevOk;
 }
 
 // Fills the zonal weight table (kw, dw) for every r in 0..256 from the
@@ -73,6 +76,7 @@ struct DeviceSetup {
   std::atomic<bool> ready{false};
   unsigned char* ptr = nullptr;
   int grid = 0;
+  int sms = 0;
 };
 constexpr int kMaxDevices = 64;
 DeviceSetup g_setup[kMaxDevices];
@@ -103,6 +107,7 @@ atdct16_status setup_device(int dev, cudaStream_t stream, DeviceSetup** out) {
       if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(stream) != cudaSuccess) return ATDCT16_ECUDA;
       s.ptr = static_cast<unsigned char*>(p);
       s.grid = sms * zonal_ctas_per_sm();
+      s.sms = sms;
       s.ready.store(true, std::memory_order_release);
     }
   }
@@ -162,13 +167,21 @@ extern "C" atdct16_status atdct16_compress_zonal_noalloc(const atdct16_image* h_
   atdct16_status st = setup_device(dev, stream, &s);
   if (st != ATDCT16_OK) return st;
   unsigned char* p = s->ptr;
-  noalloc_stage_jobs<<<1, 64, 0, stream>>>(pack, n, p);
+  JobPack ordered;
+  std::memset(&ordered, 0, sizeof(ordered));
+  ZonalSplit split;
+  zonal_order(pack.jobs, n, ordered.jobs, &split);
+  noalloc_stage_jobs<<<1, 64, 0, stream>>>(pack, n, 0, p);
   cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    noalloc_stage_jobs<<<1, 64, 0, stream>>>(ordered, n, kNoAllocMaxImages, p);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return ATDCT16_ECUDA;
   const ImageJob* jobs = reinterpret_cast<const ImageJob*>(p + kOffJobs);
-  const int grid = (int)std::min<long long>(s->grid, (tiles + kZonalWarps - 1) / kZonalWarps);
-  e = launch_zonal(jobs, n, tiles, reinterpret_cast<const float2*>(p + kOffWtab),
-                   reinterpret_cast<float*>(p + kOffTiles), reinterpret_cast<int*>(p + kOffStatus), grid, stream);
+  e = launch_zonal_ordered(jobs + kNoAllocMaxImages, split, default_zonal_config(), s->grid,
+                           reinterpret_cast<const float2*>(p + kOffWtab), reinterpret_cast<float*>(p + kOffTiles),
+                           reinterpret_cast<int*>(p + kOffStatus), s->sms, stream);
   if (e == cudaSuccess)
     e = launch_psnr_finalize(jobs, n, tiles, reinterpret_cast<const float*>(p + kOffTiles), 255.0, d_psnr, d_sse,
                              stream);

@@ -58,4 +58,28 @@ __device__ __forceinline__ float badd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float bsub(float a, float b) { return __fsub_rn(a, b); }
 #endif
 
+// A value that may be known to be zero.  Where the flag is a compile-time
+// fact (a butterfly unrolled over inputs that are zero by construction), the
+// branches fold away: an addition with a zero operand costs nothing, and a
+// subtraction from zero becomes one negation.  V needs badd, bsub and a
+// value-initialised zero.
+// (After every badd / bsub overload, so that the templates see them.)
+template <class V>
+struct MaybeZero {
+  V v;
+  bool z;
+};
+template <class V>
+ATDCT16_OPS_HD MaybeZero<V> badd(MaybeZero<V> a, MaybeZero<V> b) {
+  if (a.z) return b;
+  if (b.z) return a;
+  return MaybeZero<V>{badd(a.v, b.v), false};
+}
+template <class V>
+ATDCT16_OPS_HD MaybeZero<V> bsub(MaybeZero<V> a, MaybeZero<V> b) {
+  if (b.z) return a;
+  if (a.z) return MaybeZero<V>{bsub(V{}, b.v), false};
+  return MaybeZero<V>{bsub(a.v, b.v), false};
+}
+
 }  // namespace atdct16
