@@ -62,6 +62,7 @@ def parse_args():
                     help="run only the coefficient-pipeline phase (--steps applies) and print its JSON")
     ap.add_argument("--mixed-images", type=int, default=1000)
     ap.add_argument("--serve-rates", default="100,250,500,1000,2000,5000")
+    ap.add_argument("--serve-requests", type=int, default=20000, help="serving requests over the whole rate sweep")
     return ap.parse_args()
 
 
@@ -692,12 +693,21 @@ def mixed_batch_phase(torch, atdct16, synth, dev, n_images, seed=4, cpu_oracle=F
     fin = ~p1.isinf()
     same = same and bool(torch.equal(p1[fin], p2[fin]))
     info = batch.info()
+    tuning = batch.tuning()
     batch.close()
     out = {"images": n_images, "pixels": int(total), "r": r,
            "per_image_launches_gpx_s": total / (ms_a / 1e3) / 1e9,
            "graph_batch_gpx_s": total / (ms_b / 1e3) / 1e9,
            "graph_batch_gbs": 2.0 * total / (ms_b / 1e3) / 1e9,
-           "speedup": ms_a / ms_b, "identical_results": same, "autotune_s": tune_s, "tuned": info}
+           "speedup": ms_a / ms_b, "identical_results": same, "autotune_s": tune_s, "tuned": info,
+           "tuning": {"chosen": tuning["chosen"], "candidates": len(tuning["candidates"]),
+                      "candidate_ms": {"min": min(c["ms"] for c in tuning["candidates"]),
+                                       "median": statistics.median(c["ms"] for c in tuning["candidates"]),
+                                       "max": max(c["ms"] for c in tuning["candidates"])},
+                      # tiles per CTA, staging depth, vector bytes, CTAs per SM (0: max), phase, variant: ms
+                      "table": [[c["tiles_per_cta"], c["staging_depth"], c["vector_bytes"], c["box_ctas"],
+                                 c["phase"], c["variant"], c["general_ctas"], round(c["ms"], 4)]
+                                for c in tuning["candidates"]]}}
     if cpu_oracle:
         # the exact-integer oracle on the first images of the set, up to about 8 Mpx
         import oracle as O
@@ -714,11 +724,30 @@ def mixed_batch_phase(torch, atdct16, synth, dev, n_images, seed=4, cpu_oracle=F
     return out
 
 
-def serving_phase(torch, atdct16, synth, rates, seed=5):
-    """Poisson arrivals at each rate; uint8 requests with sides log-uniform in
-    [64, 8192] (multiples of 16) cut from a seeded 8192x8192 AR(1) field in
-    pinned host memory, r uniform in {6, 16, 36, 64}; 40 GB device arena.
-    Bounded sample: max(200, min(2000, rate x 1 s)) requests per rate."""
+SERVE_STAGES = ("queue", "h2d", "slot_wait", "compute", "d2h", "notice")
+
+
+def serve_counts(rates, total):
+    """Requests per rate: `total` split in proportion to sqrt(rate), so that
+    the low rates keep enough samples for a p99 without running for minutes."""
+    w = [math.sqrt(r) for r in rates]
+    n = [int(round(total * x / sum(w))) for x in w]
+    n[-1] += total - sum(n)
+    return n
+
+
+def serving_phase(torch, atdct16, synth, rates, total, seed=5):
+    """Config 5: `total` requests in all, Poisson arrivals at each rate of the
+    sweep (requests split across the rates by serve_counts); uint8 requests
+    with sides log-uniform in [64, 8192] (multiples of 16) cut from a seeded
+    8192 x 8192 AR(1) field in pinned host memory, r uniform in {6, 16, 36,
+    64}; 40 GB device arena.  Latency runs from each request's scheduled
+    arrival to its completion.  Per request the stages on the server's clock
+    give where the time went: queue (arrival to the start of its upload:
+    admission under the memory budget and the copy engine's backlog), h2d (its
+    upload), slot_wait (upload end to the start of its launch), compute (the
+    fused launch it rode in), d2h (to the end of its download) and notice
+    (until the scheduler saw it complete)."""
     import threading
 
     import numpy as np
@@ -728,13 +757,12 @@ def serving_phase(torch, atdct16, synth, rates, seed=5):
     ring = torch.empty(ring_bytes, dtype=torch.uint8).pin_memory()
     srv = atdct16.Server(memory_budget_bytes=40 << 30, max_batch=64, compute_slots=3)
     results = []
-    for rate in rates:
-        n = int(max(200, min(2000, rate * 1.0)))
+    for rate, n in zip(rates, serve_counts(rates, total)):
         rng = np.random.default_rng(seed + int(rate))
         sizes = synth.mixed_sizes(n, 64, 8192, seed * 31 + int(rate))
         rs = rng.choice((6, 16, 36, 64), size=n)
         arrivals = synth.poisson_arrivals(n, rate, seed * 17 + int(rate))
-        lat = [None] * n
+        tim = [None] * n
         tickets = [None] * n
         done_upto = [0]
         cv = threading.Condition()
@@ -744,8 +772,8 @@ def serving_phase(torch, atdct16, synth, rates, seed=5):
                 with cv:
                     while tickets[i] is None:
                         cv.wait()
-                _, l = srv.wait(tickets[i])
-                lat[i] = l
+                _, t = srv.wait_timing(tickets[i])
+                tim[i] = t
                 with cv:
                     done_upto[0] = i + 1
                     cv.notify_all()
@@ -753,7 +781,7 @@ def serving_phase(torch, atdct16, synth, rates, seed=5):
         th = threading.Thread(target=collector)
         th.start()
         ring_pos, slices = 0, []
-        t_start = time.perf_counter()
+        t0 = atdct16.server_clock() + 0.05
         for i in range(n):
             h, w = sizes[i]
             y0 = int(rng.integers(0, 8192 - h + 1)) // 16 * 16
@@ -769,24 +797,42 @@ def serving_phase(torch, atdct16, synth, rates, seed=5):
             slices.append((ring_pos, ring_pos + h * w, i))
             ring_pos += h * w
             src = field[y0:y0 + h, x0:x0 + w]
-            delay = arrivals[i] - (time.perf_counter() - t_start)
+            t_arr = t0 + float(arrivals[i])
+            delay = t_arr - atdct16.server_clock()
             if delay > 0:
                 time.sleep(delay)
-            t = srv.submit(src, dst, int(rs[i]))
+            t = srv.submit(src, dst, int(rs[i]), arrival=t_arr)
             with cv:
                 tickets[i] = t
                 cv.notify_all()
         th.join()
-        wall = time.perf_counter() - t_start
-        lat_ms = np.array(lat) * 1e3
+        t_end = max(x["done"] for x in tim)
+        lat = np.array([x["done"] - x["arrival"] for x in tim]) * 1e3
+        stages = {
+            "queue": [x["h2d_start"] - x["arrival"] for x in tim],
+            "h2d": [x["h2d_end"] - x["h2d_start"] for x in tim],
+            "slot_wait": [x["compute_start"] - x["h2d_end"] for x in tim],
+            "compute": [x["compute_end"] - x["compute_start"] for x in tim],
+            "d2h": [x["d2h_end"] - x["compute_end"] for x in tim],
+            "notice": [x["done"] - x["d2h_end"] for x in tim],
+        }
+        st_ms = {k: np.array(v) * 1e3 for k, v in stages.items()}
+        tail = lat >= np.percentile(lat, 99)
         px = sum(h * w for h, w in sizes)
-        results.append({"rate": rate, "requests": n, "p50_ms": float(np.percentile(lat_ms, 50)),
-                        "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
-                        "achieved_req_s": n / wall, "gpx_s": px / wall / 1e9, "pixels": int(px)})
+        results.append({
+            "rate": rate, "requests": n, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "achieved_req_s": n / (t_end - t0), "gpx_s": px / (t_end - t0) / 1e9, "pixels": int(px),
+            "stages_p50_ms": {k: float(np.percentile(v, 50)) for k, v in st_ms.items()},
+            "stages_p99_ms": {k: float(np.percentile(v, 99)) for k, v in st_ms.items()},
+            # where the slowest 1 % of requests spent their time (mean per stage)
+            "p99_tail_breakdown_ms": {k: float(v[tail].mean()) for k, v in st_ms.items()},
+            "p99_tail_mean_mpx": float(np.mean([sizes[i][0] * sizes[i][1] for i in np.nonzero(tail)[0]]) / 1e6)})
     st = srv.stats()
     srv.close()
-    return {"rates": results, "launches": st["launches"], "arena_gb": 40,
-            "note": "latency = submission to completion, includes H2D and D2H copies"}
+    return {"rates": results, "requests": sum(r["requests"] for r in results), "launches": st["launches"],
+            "arena_gb": 40, "stages": list(SERVE_STAGES),
+            "note": "latency = scheduled Poisson arrival to completion; H2D and D2H of the request included"}
 
 
 # --------------------------------------------------------------------------
@@ -1000,7 +1046,7 @@ def run_ours(args):
                                                     cpu_oracle=args.cpu_seconds > 0)
             torch.cuda.empty_cache()
             rates = [float(v) for v in args.serve_rates.split(",") if v]
-            line["serving"] = serving_phase(torch, atdct16, synth, rates)
+            line["serving"] = serving_phase(torch, atdct16, synth, rates, args.serve_requests)
         print(json.dumps(line), flush=True)
     plan.close()
     if dist:

@@ -282,6 +282,14 @@ atdct16_status atdct16_psnr(atdct16_dtype dtype, const void* d_a, int64_t pitch_
 #define ATDCT16_BATCH_VARIANT_SHIFT 8
 #define ATDCT16_BATCH_VARIANT_MASK (7u << ATDCT16_BATCH_VARIANT_SHIFT)
 #define ATDCT16_BATCH_VARIANT(v) ((uint32_t)((v) + 1) << ATDCT16_BATCH_VARIANT_SHIFT)
+/* Pin the launch shape of the kernels for r <= 36 instead (not with
+ * ATDCT16_BATCH_AUTOTUNE): tiles per CTA w in {2, 4, 8}, staging depth d in
+ * {1, 2, 3}, input copy width v in {8, 16} bytes (see atdct16_tune_point). */
+#define ATDCT16_BATCH_SHAPE_SHIFT 12
+#define ATDCT16_BATCH_SHAPE_MASK (0x3fu << ATDCT16_BATCH_SHAPE_SHIFT)
+#define ATDCT16_BATCH_SHAPE(w, d, v)                                                           \
+  ((uint32_t)((((w) == 2 ? 1 : (w) == 4 ? 2 : 3) | ((d) << 2) | (((v) == 8 ? 1 : 2) << 4)) \
+              << ATDCT16_BATCH_SHAPE_SHIFT))
 
 /* h_images: n zonal descriptors (device src/dst, r in 0..256).  d_psnr /
  * d_sse: caller-owned device outputs (d_sse may be NULL), written by every
@@ -304,6 +312,35 @@ atdct16_status atdct16_batch_launch(atdct16_batch_t batch, cudaStream_t stream);
  * Any pointer may be NULL. */
 atdct16_status atdct16_batch_info(atdct16_batch_t batch, int32_t* variant, int32_t* warps, int32_t* prefetch,
                                   int32_t* grid, int64_t* tiles, float* tuned_ms);
+/* One launch shape of a batch and its time.  The general kernel (jobs with
+ * r = 0 or r > 36) runs in a variant (as above) with general_ctas CTAs per
+ * SM; the kernels for r <= 36 (kept set inside the 8 x 8 low-frequency
+ * corner) run tiles_per_cta warps per CTA (one 16 x 128 tile each at a
+ * time), with the input rows of staging_depth tiles in flight per warp (1,
+ * 2 or 3), copied vector_bytes (16 or 8) at a time, box_ctas CTAs per SM (0:
+ * as many as fit).  ms: median time of one launch of the batch.  phase: 0
+ * for a candidate of the box-kernel search, 1 of the general-kernel search
+ * (which runs with the box shape found first). */
+typedef struct {
+  int32_t phase;
+  int32_t variant;
+  int32_t general_ctas;
+  int32_t tiles_per_cta;
+  int32_t staging_depth;
+  int32_t vector_bytes;
+  int32_t box_ctas;
+  float ms;
+} atdct16_tune_point;
+/* The batch's launch shape and, after autotuning, every candidate the
+ * autotuner timed (the box kernels' tiles per CTA x staging depth x vector
+ * width x CTAs per SM, then the general kernel's variant x CTAs per SM), each
+ * the median of five timed launches of the whole batch.  chosen may be NULL;
+ * up to max_candidates entries go to candidates, *n_candidates receives
+ * their total count (0 without autotuning or when the shape came from the
+ * tuning cache). */
+atdct16_status atdct16_batch_tuning(atdct16_batch_t batch, atdct16_tune_point* chosen,
+                                    atdct16_tune_point* candidates, int32_t max_candidates,
+                                    int32_t* n_candidates);
 /* Waits for the batch's last launch stream, then frees it. */
 atdct16_status atdct16_batch_destroy(atdct16_batch_t batch);
 
@@ -342,10 +379,30 @@ atdct16_status atdct16_server_create(const atdct16_server_config* cfg, atdct16_s
  * request completes.  ATDCT16_ENOMEM if it can never fit in the arena. */
 atdct16_status atdct16_server_submit(atdct16_server_t server, const atdct16_request* req, uint64_t* ticket);
 /* Wait for a request (timeout_us < 0: no limit; ATDCT16_ETIMEOUT when it
- * expires).  On completion returns its PSNR (Sec. 4) and its latency from
- * submission to completion in seconds, and forgets the ticket. */
+ * expires).  On completion returns its PSNR (Sec. 4) and its latency in
+ * seconds from arrival (submission, unless given to atdct16_server_submit_at)
+ * to completion, and forgets the ticket. */
 atdct16_status atdct16_server_wait(atdct16_server_t server, uint64_t ticket, double* psnr, double* latency_s,
                                    int64_t timeout_us);
+/* Seconds on the server's clock (a steady clock; the timestamps below). */
+double atdct16_server_clock(void);
+/* As atdct16_server_submit, for a request that arrived at arrival_s on the
+ * server's clock (<= now): its latency is measured from arrival_s. */
+atdct16_status atdct16_server_submit_at(atdct16_server_t server, const atdct16_request* req, double arrival_s,
+                                        uint64_t* ticket);
+/* Where a request's time went, in seconds on the server's clock: arrival
+ * (submission time unless given), submission, the start and end of its
+ * upload, the start and end of the fused launch it rode in, the end of its
+ * download, and when the scheduler saw it complete.  The device stage
+ * boundaries come from timing events placed on the host clock through a
+ * reference event recorded when the server was created. */
+typedef struct {
+  double arrival, submit, h2d_start, h2d_end, compute_start, compute_end, d2h_end, done;
+} atdct16_request_timing;
+/* As atdct16_server_wait, returning the request's timing as well (either
+ * output may be NULL). */
+atdct16_status atdct16_server_wait_timing(atdct16_server_t server, uint64_t ticket, double* psnr,
+                                          atdct16_request_timing* timing, int64_t timeout_us);
 /* Completed requests, kernel launches, pixels completed, seconds from the
  * first submission to the last completion, arena bytes in use. */
 atdct16_status atdct16_server_stats(atdct16_server_t server, uint64_t* completed, uint64_t* launches,

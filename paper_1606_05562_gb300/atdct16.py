@@ -67,6 +67,13 @@ class Request(C.Structure):
     ]
 
 
+class RequestTiming(C.Structure):
+    """Mirror of ``atdct16_request_timing`` (seconds on the server clock)."""
+
+    _fields_ = [(k, C.c_double) for k in ("arrival", "submit", "h2d_start", "h2d_end", "compute_start",
+                                          "compute_end", "d2h_end", "done")]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -99,9 +106,13 @@ _SIGS = {
     "atdct16_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_size_t)]),
     "atdct16_server_destroy": (C.c_int, [C.c_void_p]),
+    "atdct16_server_clock": (C.c_double, []),
+    "atdct16_server_submit_at": (C.c_int, [C.c_void_p, C.POINTER(Request), C.c_double, C.POINTER(C.c_uint64)]),
+    "atdct16_server_wait_timing": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_double), C.c_void_p, C.c_int64]),
     "atdct16_ssim_batch": (C.c_int, [C.c_void_p, C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p]),
     "atdct16_compress_zonal_dct": (C.c_int, [C.c_void_p, C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p,
                                             C.c_void_p]),
+    "atdct16_batch_tuning": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     "atdct16_plan_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "atdct16_plan_profile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
 }
@@ -281,6 +292,26 @@ def batch_variant(v):
     return (v + 1) << 8
 
 
+def batch_shape(tiles_per_cta, staging_depth, vector_bytes):
+    """Flag that pins the launch shape of a Batch's kernels for r <= 36."""
+    w = {2: 1, 4: 2, 8: 3}[tiles_per_cta]
+    v = {8: 1, 16: 2}[vector_bytes]
+    return (w | (staging_depth << 2) | (v << 4)) << 12
+
+
+class TunePoint(C.Structure):
+    """``atdct16_tune_point``: one launch shape of a batch and its median time."""
+
+    _fields_ = [("phase", C.c_int32), ("variant", C.c_int32), ("general_ctas", C.c_int32), ("tiles_per_cta", C.c_int32),
+                ("staging_depth", C.c_int32), ("vector_bytes", C.c_int32), ("box_ctas", C.c_int32),
+                ("ms", C.c_float)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["variant"] = ZONAL_VARIANTS[self.variant]
+        return d
+
+
 class Batch:
     """A resident zonal batch (``atdct16_batch_*``): descriptors on the device,
     optional autotuned launch shape and CUDA-graph capture."""
@@ -302,6 +333,15 @@ class Batch:
                                         C.byref(ms)), "batch_info")
         return {"variant": ZONAL_VARIANTS[v.value], "warps": w.value, "prefetch": p.value, "grid": g.value,
                 "tiles": t.value, "tuned_ms": ms.value}
+
+    def tuning(self):
+        """The chosen launch shape and every candidate the autotuner timed."""
+        n = C.c_int32()
+        chosen = TunePoint()
+        _check(lib().atdct16_batch_tuning(self._h, C.byref(chosen), None, 0, C.byref(n)), "batch_tuning")
+        cands = (TunePoint * max(1, n.value))()
+        _check(lib().atdct16_batch_tuning(self._h, None, cands, n.value, C.byref(n)), "batch_tuning")
+        return {"chosen": chosen.as_dict(), "candidates": [cands[i].as_dict() for i in range(n.value)]}
 
     def close(self):
         if self._h:
@@ -330,15 +370,28 @@ class Server:
         cfg = ServerConfig(memory_budget_bytes, max_batch, compute_slots, 0)
         _check(lib().atdct16_server_create(C.byref(cfg), C.byref(self._h)), "server_create")
 
-    def submit(self, src, dst, r):
-        """Queue ``src`` (H, W uint8, host) -> ``dst`` (host); returns a ticket."""
+    def submit(self, src, dst, r, arrival=None):
+        """Queue ``src`` (H, W uint8, host) -> ``dst`` (host); returns a ticket.
+        ``arrival``: the request's arrival time on :func:`server_clock`
+        (latency is measured from it; default: now)."""
         sp, spitch = _host_ptr(src)
         dp, dpitch = _host_ptr(dst)
         h, w = src.shape[-2], src.shape[-1]
         req = Request(sp, dp, spitch, dpitch, w, h, int(r), 0)
         t = C.c_uint64()
-        _check(lib().atdct16_server_submit(self._h, C.byref(req), C.byref(t)), "server_submit")
+        if arrival is None:
+            _check(lib().atdct16_server_submit(self._h, C.byref(req), C.byref(t)), "server_submit")
+        else:
+            _check(lib().atdct16_server_submit_at(self._h, C.byref(req), float(arrival), C.byref(t)),
+                   "server_submit_at")
         return t.value
+
+    def wait_timing(self, ticket, timeout_us=-1):
+        """(PSNR, stage timestamps on the server clock) of a request; forgets the ticket."""
+        p, tm = C.c_double(), RequestTiming()
+        _check(lib().atdct16_server_wait_timing(self._h, ticket, C.byref(p), C.byref(tm), timeout_us),
+               "server_wait_timing")
+        return p.value, {k: getattr(tm, k) for k, _ in RequestTiming._fields_}
 
     def wait(self, ticket, timeout_us=-1):
         """(PSNR, latency in seconds) of a request; forgets the ticket."""
@@ -363,6 +416,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def server_clock() -> float:
+    """Seconds on the server's steady clock."""
+    return float(lib().atdct16_server_clock())
 
 
 def compress_zonal_noalloc(images, psnr, sse=None, stream=None):

@@ -45,6 +45,7 @@ struct atdct16_plan_st {
   struct Tuned {
     ZonalConfig cfg;
     int ctas;
+    BoxConfig box;
     float ms;
   };
   std::map<unsigned long long, Tuned> tuned;
@@ -174,16 +175,19 @@ namespace atdct16 {
 const float2* plan_zonal_table(const atdct16_plan_st* plan) { return plan->d_wtab; }
 int plan_num_sms(const atdct16_plan_st* plan) { return plan->num_sms; }
 int plan_device(const atdct16_plan_st* plan) { return plan->device; }
-bool plan_tune_lookup(atdct16_plan_st* plan, unsigned long long key, ZonalConfig* cfg, int* ctas, float* ms) {
+bool plan_tune_lookup(atdct16_plan_st* plan, unsigned long long key, ZonalConfig* cfg, int* ctas, BoxConfig* box,
+                      float* ms) {
   auto it = plan->tuned.find(key);
   if (it == plan->tuned.end()) return false;
   *cfg = it->second.cfg;
   *ctas = it->second.ctas;
+  *box = it->second.box;
   *ms = it->second.ms;
   return true;
 }
-void plan_tune_store(atdct16_plan_st* plan, unsigned long long key, const ZonalConfig& cfg, int ctas, float ms) {
-  plan->tuned[key] = atdct16_plan_st::Tuned{cfg, ctas, ms};
+void plan_tune_store(atdct16_plan_st* plan, unsigned long long key, const ZonalConfig& cfg, int ctas,
+                     const BoxConfig& box, float ms) {
+  plan->tuned[key] = atdct16_plan_st::Tuned{cfg, ctas, box, ms};
 }
 }  // namespace atdct16
 
@@ -370,7 +374,8 @@ atdct16_status atdct16_compress_zonal(atdct16_plan_t plan, const atdct16_image* 
   if (s != ATDCT16_OK) return s;
   const int pk = prof_begin(plan, stream);
   cudaError_t e = launch_zonal_ordered(plan->d_jobs + n, split, default_zonal_config(), plan->zonal_grid,
-                                       plan->d_wtab, plan->d_tile_sse, plan->d_status, plan->num_sms, stream);
+                                       default_box_config(), plan->d_wtab, plan->d_tile_sse, plan->d_status,
+                                       plan->num_sms, stream);
   prof_end(plan, pk, stream);
   if (e == cudaSuccess)
     e = launch_psnr_finalize(plan->d_jobs, n, ntiles, plan->d_tile_sse, 255.0, d_psnr, d_sse, stream);

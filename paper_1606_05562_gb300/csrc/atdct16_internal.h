@@ -108,11 +108,21 @@ int zonal_class_of(int r);
 // tile_begin, and level_base = the job's tile_begin in `jobs` (where the
 // kernels write its per-tile partials, which the PSNR finalize reads).
 void zonal_order(const ImageJob* jobs, int n, ImageJob* ordered, ZonalSplit* split);
+// Launch shape of the box kernels (the batch autotuner's knobs).
+struct BoxConfig {
+  int warps;        // warps per CTA, i.e. tiles per CTA in flight: 2, 4 or 8
+  int depth;        // staging depth, tiles whose input rows are in flight per warp: 1, 2 or 3 (extent 8)
+  int vec;          // bytes per input copy: 16 (one block row) or 8
+  int ctas_per_sm;  // 0: as many as fit
+};
+bool box_config_supported(const BoxConfig& bc);
+BoxConfig default_box_config();
+int box_config_max_ctas_per_sm(const BoxConfig& bc);
 // One launch per non-empty class on `stream`; `general` and `general_grid`
-// shape the general kernel's launch.
+// shape the general kernel's launch, `box` the box kernels'.
 cudaError_t launch_zonal_ordered(const ImageJob* d_ordered, const ZonalSplit& split, const ZonalConfig& general,
-                                 int general_grid, const float2* d_wtab, float* d_tile_sse, int* d_status,
-                                 int num_sms, cudaStream_t stream);
+                                 int general_grid, const BoxConfig& box, const float2* d_wtab, float* d_tile_sse,
+                                 int* d_status, int num_sms, cudaStream_t stream);
 
 }  // namespace atdct16
 
@@ -122,8 +132,10 @@ namespace atdct16 {
 const float2* plan_zonal_table(const atdct16_plan_st* plan);
 int plan_num_sms(const atdct16_plan_st* plan);
 int plan_device(const atdct16_plan_st* plan);
-bool plan_tune_lookup(atdct16_plan_st* plan, unsigned long long key, ZonalConfig* cfg, int* ctas, float* ms);
-void plan_tune_store(atdct16_plan_st* plan, unsigned long long key, const ZonalConfig& cfg, int ctas, float ms);
+bool plan_tune_lookup(atdct16_plan_st* plan, unsigned long long key, ZonalConfig* cfg, int* ctas, BoxConfig* box,
+                      float* ms);
+void plan_tune_store(atdct16_plan_st* plan, unsigned long long key, const ZonalConfig& cfg, int ctas,
+                     const BoxConfig& box, float ms);
 int quant_ctas_per_sm();
 
 }  // namespace atdct16

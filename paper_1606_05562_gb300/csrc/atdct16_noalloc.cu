@@ -179,7 +179,7 @@ extern "C" atdct16_status atdct16_compress_zonal_noalloc(const atdct16_image* h_
   }
   if (e != cudaSuccess) return ATDCT16_ECUDA;
   const ImageJob* jobs = reinterpret_cast<const ImageJob*>(p + kOffJobs);
-  e = launch_zonal_ordered(jobs + kNoAllocMaxImages, split, default_zonal_config(), s->grid,
+  e = launch_zonal_ordered(jobs + kNoAllocMaxImages, split, default_zonal_config(), s->grid, default_box_config(),
                            reinterpret_cast<const float2*>(p + kOffWtab), reinterpret_cast<float*>(p + kOffTiles),
                            reinterpret_cast<int*>(p + kOffStatus), s->sms, stream);
   if (e == cudaSuccess)

@@ -30,7 +30,10 @@ double now_s() {
 struct Req {
   uint64_t id;
   atdct16_request r;
-  double t_submit = 0, t_done = 0;
+  double t_arrival = 0, t_submit = 0, t_done = 0;
+  cudaEvent_t ev_h2d_start = nullptr, ev_h2d_end = nullptr;  // timing events on the H2D stream
+  int slot = -1;                                              // compute slot of its launch
+  atdct16_request_timing timing{};
   size_t off = 0, bytes = 0;  // arena slice: src then dst
   double psnr = 0;
   bool done = false;
@@ -41,6 +44,7 @@ struct Slot {
   atdct16_plan_t plan = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t computed = nullptr, downloaded = nullptr;
+  cudaEvent_t started = nullptr;  // timing event before the launch
   double* d_psnr = nullptr;
   double* h_psnr = nullptr;  // pinned
   std::vector<Req*> reqs;
@@ -63,6 +67,9 @@ struct atdct16_server_st {
   std::vector<std::pair<Req*, cudaEvent_t>> uploading;  // admitted, upload in flight
   std::unordered_map<uint64_t, Req*> all;
   std::vector<cudaEvent_t> event_pool;
+  std::vector<cudaEvent_t> timing_pool;  // timing-enabled events for the request stage boundaries
+  cudaEvent_t ev_ref = nullptr;          // reference event: recorded at creation, at host time host_ref
+  double host_ref = 0;
   uint64_t next_id = 1;
   std::atomic<bool> stop{false};
   std::thread worker;
@@ -85,7 +92,35 @@ cudaEvent_t get_event(atdct16_server_st* s) {
   return e;
 }
 
+cudaEvent_t get_timing_event(atdct16_server_st* s) {
+  if (!s->timing_pool.empty()) {
+    cudaEvent_t e = s->timing_pool.back();
+    s->timing_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Host time of a completed timing event: the reference's host time plus the
+// device time elapsed since the reference.
+double event_time(const atdct16_server_st* s, cudaEvent_t e) {
+  float ms = 0.f;
+  if (!e || cudaEventElapsedTime(&ms, s->ev_ref, e) != cudaSuccess) return 0.0;
+  return s->host_ref + 1e-3 * ms;
+}
+
 size_t req_bytes(const atdct16_request& r) { return 2 * (size_t)r.width * (size_t)r.height; }
+
+// h rows of w bytes: one linear copy when both sides are contiguous (the
+// copy engine moves pitched 2-D copies row by row, far below the link rate
+// for short rows), else a pitched copy.
+cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t w, size_t h,
+                      cudaMemcpyKind kind, cudaStream_t stream) {
+  if (dpitch == w && spitch == w) return cudaMemcpyAsync(dst, src, w * h, kind, stream);
+  return cudaMemcpy2DAsync(dst, dpitch, src, spitch, w, h, kind, stream);
+}
 
 // One pass of the scheduler: completions, admissions, launches.
 bool scheduler_pass(atdct16_server_st* s) {
@@ -104,10 +139,24 @@ bool scheduler_pass(atdct16_server_st* s) {
     if (q == cudaErrorNotReady) continue;
     const double t = now_s();
     std::lock_guard<std::mutex> lk(s->mu);
+    const double t_start = event_time(s, sl.started), t_comp = event_time(s, sl.computed),
+                 t_down = event_time(s, sl.downloaded);
     for (size_t i = 0; i < sl.reqs.size(); ++i) {
       Req* rq = sl.reqs[i];
       rq->psnr = sl.h_psnr[i];
       rq->t_done = t;
+      atdct16_request_timing& tm = rq->timing;
+      tm.arrival = rq->t_arrival;
+      tm.submit = rq->t_submit;
+      tm.h2d_start = event_time(s, rq->ev_h2d_start);
+      tm.h2d_end = event_time(s, rq->ev_h2d_end);
+      tm.compute_start = t_start;
+      tm.compute_end = t_comp;
+      tm.d2h_end = t_down;
+      tm.done = t;
+      s->timing_pool.push_back(rq->ev_h2d_start);
+      s->timing_pool.push_back(rq->ev_h2d_end);
+      rq->ev_h2d_start = rq->ev_h2d_end = nullptr;
       rq->status = q == cudaSuccess ? ATDCT16_OK : ATDCT16_ECUDA;
       rq->done = true;
       s->arena.release(rq->off, rq->bytes);
@@ -129,7 +178,11 @@ bool scheduler_pass(atdct16_server_st* s) {
     rq->off = off;
     unsigned char* d_src = s->arena_base + off;
     const size_t w = rq->r.width, h = rq->r.height;
-    cudaError_t e = cudaMemcpy2DAsync(d_src, w, rq->r.h_src, rq->r.src_pitch, w, h, cudaMemcpyHostToDevice, s->h2d);
+    rq->ev_h2d_start = get_timing_event(s);
+    rq->ev_h2d_end = get_timing_event(s);
+    cudaError_t e = cudaEventRecord(rq->ev_h2d_start, s->h2d);
+    if (e == cudaSuccess) e = copy_rows(d_src, w, rq->r.h_src, rq->r.src_pitch, w, h, cudaMemcpyHostToDevice, s->h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(rq->ev_h2d_end, s->h2d);
     cudaEvent_t ev = get_event(s);
     if (e == cudaSuccess) e = cudaEventRecord(ev, s->h2d);
     if (e != cudaSuccess) s->sticky_error = ATDCT16_ECUDA;
@@ -170,6 +223,7 @@ bool scheduler_pass(atdct16_server_st* s) {
         s->event_pool.push_back(s->uploading[i].second);
       }
       s->uploading.erase(s->uploading.begin(), s->uploading.begin() + take);
+      cudaEventRecord(free_slot->started, free_slot->stream);
       atdct16_status st =
           atdct16_compress_zonal(free_slot->plan, ims.data(), (int32_t)ims.size(), free_slot->d_psnr, nullptr,
                                  free_slot->stream);
@@ -179,8 +233,8 @@ bool scheduler_pass(atdct16_server_st* s) {
       for (size_t i = 0; e == cudaSuccess && i < free_slot->reqs.size(); ++i) {
         Req* rq = free_slot->reqs[i];
         const size_t w = rq->r.width, h = rq->r.height;
-        e = cudaMemcpy2DAsync(rq->r.h_dst, rq->r.dst_pitch, s->arena_base + rq->off + w * h, w, w, h,
-                              cudaMemcpyDeviceToHost, s->d2h);
+        e = copy_rows(rq->r.h_dst, rq->r.dst_pitch, s->arena_base + rq->off + w * h, w, w, h,
+                      cudaMemcpyDeviceToHost, s->d2h);
       }
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(free_slot->h_psnr, free_slot->d_psnr, sizeof(double) * free_slot->reqs.size(),
@@ -223,6 +277,7 @@ void destroy_server(atdct16_server_st* s) {
     if (sl.plan) atdct16_plan_destroy(sl.plan);
     if (sl.stream) cudaStreamDestroy(sl.stream);
     if (sl.computed) cudaEventDestroy(sl.computed);
+    if (sl.started) cudaEventDestroy(sl.started);
     if (sl.downloaded) cudaEventDestroy(sl.downloaded);
     cudaFree(sl.d_psnr);
     cudaFreeHost(sl.h_psnr);
@@ -237,6 +292,12 @@ void destroy_server(atdct16_server_st* s) {
   }
   for (auto& kv : s->uploading) cudaEventDestroy(kv.second);
   for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : s->timing_pool) cudaEventDestroy(e);
+  for (auto& kv : s->all) {
+    if (kv.second->ev_h2d_start) cudaEventDestroy(kv.second->ev_h2d_start);
+    if (kv.second->ev_h2d_end) cudaEventDestroy(kv.second->ev_h2d_end);
+  }
+  if (s->ev_ref) cudaEventDestroy(s->ev_ref);
   for (auto& kv : s->all) delete kv.second;
   cudaFree(s->arena_base);
   delete s;
@@ -271,11 +332,17 @@ atdct16_status atdct16_server_create(const atdct16_server_config* cfg, atdct16_s
     if (e != cudaSuccess) break;
     if (atdct16_plan_create(&sl.plan, ATDCT16_U8, cfg->max_batch, 0, 0) != ATDCT16_OK) e = cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.computed, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.downloaded, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&sl.computed);
+    if (e == cudaSuccess) e = cudaEventCreate(&sl.downloaded);
+    if (e == cudaSuccess) e = cudaEventCreate(&sl.started);
     if (e == cudaSuccess) e = cudaMalloc(&sl.d_psnr, sizeof(double) * cfg->max_batch);
     if (e == cudaSuccess) e = cudaHostAlloc(&sl.h_psnr, sizeof(double) * cfg->max_batch, cudaHostAllocDefault);
   }
+  // the reference event that places device timestamps on the host clock
+  if (e == cudaSuccess) e = cudaEventCreate(&s->ev_ref);
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_ref, s->h2d);
+  if (e == cudaSuccess) e = cudaEventSynchronize(s->ev_ref);
+  s->host_ref = now_s();
   if (e != cudaSuccess) {
     destroy_server(s);
     return ATDCT16_ECUDA;
@@ -285,7 +352,14 @@ atdct16_status atdct16_server_create(const atdct16_server_config* cfg, atdct16_s
   return ATDCT16_OK;
 }
 
+double atdct16_server_clock(void) { return now_s(); }
+
 atdct16_status atdct16_server_submit(atdct16_server_t s, const atdct16_request* r, uint64_t* ticket) {
+  return atdct16_server_submit_at(s, r, -1.0, ticket);
+}
+
+atdct16_status atdct16_server_submit_at(atdct16_server_t s, const atdct16_request* r, double arrival_s,
+                                        uint64_t* ticket) {
   if (!s || !r || !ticket || !r->h_src || !r->h_dst || r->width <= 0 || r->height <= 0 || (r->width & 15) ||
       (r->height & 15) || r->src_pitch < r->width || r->dst_pitch < r->width || r->r < 0 || r->r > 256 ||
       r->reserved != 0)
@@ -297,6 +371,7 @@ atdct16_status atdct16_server_submit(atdct16_server_t s, const atdct16_request* 
   rq->r = *r;
   rq->bytes = req_bytes(*r);
   rq->t_submit = now_s();
+  rq->t_arrival = arrival_s >= 0.0 && arrival_s <= rq->t_submit ? arrival_s : rq->t_submit;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     rq->id = s->next_id++;
@@ -322,7 +397,27 @@ atdct16_status atdct16_server_wait(atdct16_server_t s, uint64_t ticket, double* 
   else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), pred))
     return ATDCT16_ETIMEOUT;
   if (psnr) *psnr = rq->psnr;
-  if (latency_s) *latency_s = rq->t_done - rq->t_submit;
+  if (latency_s) *latency_s = rq->t_done - rq->t_arrival;
+  const int st = rq->status;
+  s->all.erase(it);
+  delete rq;
+  return (atdct16_status)st;
+}
+
+atdct16_status atdct16_server_wait_timing(atdct16_server_t s, uint64_t ticket, double* psnr,
+                                          atdct16_request_timing* timing, int64_t timeout_us) {
+  if (!s) return ATDCT16_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return ATDCT16_EINVAL;
+  Req* rq = it->second;
+  const auto pred = [&] { return rq->done; };
+  if (timeout_us < 0)
+    s->cv_done.wait(lk, pred);
+  else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), pred))
+    return ATDCT16_ETIMEOUT;
+  if (psnr) *psnr = rq->psnr;
+  if (timing) *timing = rq->timing;
   const int st = rq->status;
   s->all.erase(it);
   delete rq;

@@ -61,9 +61,9 @@ using ZF2 = MaybeZero<float2>;
 
 constexpr int kBoxT1Words = 168;  // forward transpose: words per block pair (8 columns x 20, padded)
 constexpr int kBoxT2Units = 148;  // back-transpose: float2 units per block pair (8 columns x 18, padded)
-constexpr int kBoxStageUnits = 2 * 4 * 32;  // two tiles of input rows, 4 x 16 bytes per lane
-constexpr int kBoxWarpSmemBytes = 4 * 4 * kBoxT1Words + 8 * 4 * kBoxT2Units + 16 * kBoxStageUnits;  // 11520
-constexpr int kBoxWarps = 4;
+constexpr int kBoxFixedBytes = 4 * 4 * kBoxT1Words + 8 * 4 * kBoxT2Units;  // both transposes, 7424 bytes
+constexpr int kBoxSlotBytes = 4 * 32 * 16;  // one staging slot: a tile's input rows, 4 x 16 bytes per lane
+__host__ __device__ constexpr int box_warp_smem(int depth) { return kBoxFixedBytes + depth * kBoxSlotBytes; }
 
 // Largest r whose kept zig-zag prefix lies in the K x K corner: the scan
 // walks the anti-diagonals s = u + v in order, so the prefix stays inside
@@ -79,24 +79,28 @@ struct BoxTile {
   int r;
 };
 
-template <int K>
-__global__ void __launch_bounds__(32 * kBoxWarps, 4)
+// Launch shape (chosen by the batch autotuner): K the extent, D the staging
+// depth (tiles whose input rows are in flight, D slots per warp), the warps
+// per CTA (tiles per CTA, from the block size) and the width in bytes of the
+// input copies (vec: 16, one block row per copy, or 8).
+template <int K, int D>
+__global__ void __launch_bounds__(256, 2)
 zonal_box_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll,
                  const float2* __restrict__ wtab, float* __restrict__ tile_sse, int* __restrict__ status,
-                 int pdl_early) {
-  static_assert(K >= 1 && K <= 8, "box extent");
+                 int pdl_early, int vec) {
+  static_assert(K >= 1 && K <= 8 && D >= 1 && D <= 3, "box extent and staging depth");
   extern __shared__ __align__(16) unsigned char bsmem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, cta_warps = blockDim.x >> 5;
   const int p = lane & 3, j = lane >> 2;
-  unsigned char* const wbase = bsmem + warp * kBoxWarpSmemBytes;
+  unsigned char* const wbase = bsmem + warp * box_warp_smem(D);
   unsigned* const t1 = reinterpret_cast<unsigned*>(wbase);
   float2* const t2 = reinterpret_cast<float2*>(wbase + 4 * 4 * kBoxT1Words);
-  uint4* const stg = reinterpret_cast<uint4*>(wbase + 4 * 4 * kBoxT1Words + 8 * 4 * kBoxT2Units) + lane;
+  uint4* const stg = reinterpret_cast<uint4*>(wbase + kBoxFixedBytes) + lane;  // slot s: + 128 s
   const int ntiles = (int)ntiles_ll;  // the launcher checks ntiles < 2^30
 
-  const int nwarps = gridDim.x * kBoxWarps;
+  const int nwarps = gridDim.x * cta_warps;
   const int per_warp = (ntiles + nwarps - 1) / nwarps;
-  const int t_first = (blockIdx.x * kBoxWarps + warp) * per_warp;
+  const int t_first = (blockIdx.x * cta_warps + warp) * per_warp;
   const int t_stop = min(ntiles, t_first + per_warp);
   if (pdl_early) pdl_launch_dependents();  // the next class's kernel may be scheduled
   if (t_first >= t_stop) {
@@ -159,10 +163,22 @@ zonal_box_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     const int na = p < z.nb ? 16 : 0, nb4 = p + 4 < z.nb ? 16 : 0;
     const uint8_t* sa = na ? z.src : z.src - 16 * p;
     const uint8_t* sb = nb4 ? z.src + 64 : sa;
-    cp_async16_zfill(d, sa, na);
-    cp_async16_zfill(d + 32, sa + (na ? z.src_pitch : 0), na);
-    cp_async16_zfill(d + 64, sb, nb4);
-    cp_async16_zfill(d + 96, sb + (nb4 ? z.src_pitch : 0), nb4);
+    if (vec == 16) {
+      cp_async16_zfill(d, sa, na);
+      cp_async16_zfill(d + 32, sa + (na ? z.src_pitch : 0), na);
+      cp_async16_zfill(d + 64, sb, nb4);
+      cp_async16_zfill(d + 96, sb + (nb4 ? z.src_pitch : 0), nb4);
+    } else {  // two 8-byte copies per block row
+      unsigned char* const d8 = reinterpret_cast<unsigned char*>(d);
+      cp_async8_zfill(d8, sa, na >> 1);
+      cp_async8_zfill(d8 + 8, sa + (na ? 8 : 0), na >> 1);
+      cp_async8_zfill(d8 + 512, sa + (na ? z.src_pitch : 0), na >> 1);
+      cp_async8_zfill(d8 + 520, sa + (na ? z.src_pitch + 8 : 0), na >> 1);
+      cp_async8_zfill(d8 + 1024, sb, nb4 >> 1);
+      cp_async8_zfill(d8 + 1032, sb + (nb4 ? 8 : 0), nb4 >> 1);
+      cp_async8_zfill(d8 + 1536, sb + (nb4 ? z.src_pitch : 0), nb4 >> 1);
+      cp_async8_zfill(d8 + 1544, sb + (nb4 ? z.src_pitch + 8 : 0), nb4 >> 1);
+    }
     cp_async_commit();
   };
 
@@ -212,21 +228,29 @@ zonal_box_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     return e;
   };
 
-  BoxTile cur, nxt;
-  take(cur);
+  // the warp's next D tiles: q[0] is the current one, its input rows in slot
+  // st; q[i] in slot (st + i) mod D
+  BoxTile q[D];
+  bool hq[D];
+  take(q[0]);
   ok = advance();
-  issue(cur, 0);
-  bool have_nxt = ok && c_t < t_stop;
-  if (have_nxt) {
-    take(nxt);
-    ok = advance();
-    issue(nxt, 1);
-  } else {
-    cp_async_commit();
+  issue(q[0], 0);
+  hq[0] = true;
+#pragma unroll
+  for (int i = 1; i < D; ++i) {
+    hq[i] = hq[i - 1] && ok && c_t < t_stop;
+    if (hq[i]) {
+      take(q[i]);
+      ok = advance();
+      issue(q[i], i);
+    } else {
+      cp_async_commit();
+    }
   }
   int st = 0;
   while (true) {
-    cp_async_wait<1>();
+    BoxTile& cur = q[0];
+    cp_async_wait<D - 1>();  // the current tile's copies (the oldest group in flight)
     uint4 X[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) X[k] = stg[128 * st + 32 * k];
@@ -258,9 +282,9 @@ zonal_box_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     }
     __syncwarp();
 
-    // ---- the input rows of the tile after the next one, into the slot just read
+    // ---- the input rows of the tile D ahead, into the slot just read
     BoxTile fut;
-    const bool have_fut = have_nxt && ok && c_t < t_stop;
+    const bool have_fut = hq[D - 1] && ok && c_t < t_stop;
     if (have_fut) {
       take(fut);
       ok = advance();
@@ -364,31 +388,85 @@ zonal_box_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     if (lane == 0) tile_sse[cur.t] = (float)nume * (1.0f / 2304.0f);
     __syncwarp();  // buffer reads done before the next tile's writes
 
-    if (!have_nxt) break;
-    cur = nxt;
-    nxt = fut;
-    have_nxt = have_fut;
-    st ^= 1;
+    if (!(D > 1 ? hq[D > 1 ? 1 : 0] : have_fut)) break;
+#pragma unroll
+    for (int i = 0; i + 1 < D; ++i) {
+      q[i] = q[i + 1];
+      hq[i] = hq[i + 1];
+    }
+    q[D - 1] = fut;
+    hq[D - 1] = have_fut;
+    st = st + 1 == D ? 0 : st + 1;
   }
   cp_async_wait<0>();
   if (!ok && lane == 0) set_status(status, kDevBadJob);
   pdl_chain_exit();  // the next kernel (or the PSNR finalize) may now take this CTA's place
 }
 
-template <int K>
-static cudaError_t launch_box(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
-                              float* d_tile_sse, int* d_status, int num_sms, cudaStream_t stream, bool dependent,
-                              bool early) {
-  if (ntiles <= 0) return cudaSuccess;
-  if (ntiles >= (1LL << 30)) return cudaErrorInvalidValue;
+template <int K, int D>
+static cudaError_t launch_box_shape(const BoxConfig& bc, const ImageJob* d_jobs, int njobs, long long ntiles,
+                                    const float2* d_wtab, float* d_tile_sse, int* d_status, int num_sms,
+                                    cudaStream_t stream, bool dependent, bool early) {
+  const int threads = 32 * bc.warps, smem = bc.warps * box_warp_smem(D);
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zonal_box_kernel<K>, 32 * kBoxWarps,
-                                                                kBoxWarps * kBoxWarpSmemBytes);
+  cudaError_t e = cudaFuncSetAttribute(zonal_box_kernel<K, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zonal_box_kernel<K, D>, threads, smem);
   if (e != cudaSuccess) return e;
-  const long long need = (ntiles + kBoxWarps - 1) / kBoxWarps;
-  const int grid = (int)std::max<long long>(1, std::min<long long>((long long)num_sms * std::max(1, per_sm), need));
-  return launch_chained(zonal_box_kernel<K>, grid, 32 * kBoxWarps, kBoxWarps * kBoxWarpSmemBytes, stream, dependent,
-                        d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, early ? 1 : 0);
+  per_sm = std::max(1, per_sm);
+  const int ctas = bc.ctas_per_sm > 0 ? std::min(bc.ctas_per_sm, per_sm) : per_sm;
+  const long long need = (ntiles + bc.warps - 1) / bc.warps;
+  const int grid = (int)std::max<long long>(1, std::min<long long>((long long)num_sms * ctas, need));
+  return launch_chained(zonal_box_kernel<K, D>, grid, threads, smem, stream, dependent, d_jobs, njobs, ntiles, d_wtab,
+                        d_tile_sse, d_status, early ? 1 : 0, bc.vec);
+}
+
+bool box_config_supported(const BoxConfig& bc) {
+  return (bc.warps == 2 || bc.warps == 4 || bc.warps == 8) && (bc.depth >= 1 && bc.depth <= 3) &&
+         (bc.vec == 8 || bc.vec == 16) && bc.ctas_per_sm >= 0;
+}
+
+BoxConfig default_box_config() { return BoxConfig{4, 2, 16, 0}; }
+
+int box_config_max_ctas_per_sm(const BoxConfig& bc) {
+  int n = 0;
+  const int threads = 32 * bc.warps, smem = bc.warps * box_warp_smem(bc.depth);
+  cudaError_t e = cudaSuccess;
+  switch (bc.depth) {
+    case 1:
+      e = cudaFuncSetAttribute(zonal_box_kernel<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_box_kernel<8, 1>, threads, smem);
+      break;
+    case 3:
+      e = cudaFuncSetAttribute(zonal_box_kernel<8, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_box_kernel<8, 3>, threads, smem);
+      break;
+    default:
+      e = cudaFuncSetAttribute(zonal_box_kernel<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zonal_box_kernel<8, 2>, threads, smem);
+  }
+  return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
+// The box kernel of extent K in shape bc.  The staging depth is a tuning
+// knob of the K = 8 kernel (the extent of r <= 36, config-4-like batches);
+// the other extents run with depth 2.
+template <int K>
+static cudaError_t launch_box(const BoxConfig& bc, const ImageJob* d_jobs, int njobs, long long ntiles,
+                              const float2* d_wtab, float* d_tile_sse, int* d_status, int num_sms,
+                              cudaStream_t stream, bool dependent, bool early) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (ntiles >= (1LL << 30) || !box_config_supported(bc)) return cudaErrorInvalidValue;
+  if constexpr (K == 8) {
+    if (bc.depth == 1)
+      return launch_box_shape<K, 1>(bc, d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, num_sms, stream,
+                                    dependent, early);
+    if (bc.depth == 3)
+      return launch_box_shape<K, 3>(bc, d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, num_sms, stream,
+                                    dependent, early);
+  }
+  return launch_box_shape<K, 2>(bc, d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, num_sms, stream,
+                                dependent, early);
 }
 
 // --------------------------------------------------------------------------
@@ -422,8 +500,8 @@ void zonal_order(const ImageJob* jobs, int n, ImageJob* ordered, ZonalSplit* spl
 }
 
 cudaError_t launch_zonal_ordered(const ImageJob* d_ordered, const ZonalSplit& split, const ZonalConfig& general,
-                                 int general_grid, const float2* d_wtab, float* d_tile_sse, int* d_status,
-                                 int num_sms, cudaStream_t stream) {
+                                 int general_grid, const BoxConfig& box, const float2* d_wtab, float* d_tile_sse,
+                                 int* d_status, int num_sms, cudaStream_t stream) {
   // The general class first (the longest), then the box classes from the
   // largest extent down; every launch after the first is a programmatic
   // dependent launch whose CTAs take the places of its predecessor's as they
@@ -443,10 +521,10 @@ cudaError_t launch_zonal_ordered(const ImageJob* d_ordered, const ZonalSplit& sp
     const long long nt = split.ntiles[c];
     const bool early = k != last;
     switch (c) {
-      case 0: e = launch_box<1>(jobs, nj, nt, d_wtab, d_tile_sse, d_status, num_sms, stream, dependent, early); break;
-      case 1: e = launch_box<3>(jobs, nj, nt, d_wtab, d_tile_sse, d_status, num_sms, stream, dependent, early); break;
-      case 2: e = launch_box<6>(jobs, nj, nt, d_wtab, d_tile_sse, d_status, num_sms, stream, dependent, early); break;
-      case 3: e = launch_box<8>(jobs, nj, nt, d_wtab, d_tile_sse, d_status, num_sms, stream, dependent, early); break;
+      case 0: e = launch_box<1>(box, jobs, nj, nt, d_wtab, d_tile_sse, d_status, num_sms, stream, dependent, early); break;
+      case 1: e = launch_box<3>(box, jobs, nj, nt, d_wtab, d_tile_sse, d_status, num_sms, stream, dependent, early); break;
+      case 2: e = launch_box<6>(box, jobs, nj, nt, d_wtab, d_tile_sse, d_status, num_sms, stream, dependent, early); break;
+      case 3: e = launch_box<8>(box, jobs, nj, nt, d_wtab, d_tile_sse, d_status, num_sms, stream, dependent, early); break;
       default: {
         const long long need = (nt + general.warps - 1) / general.warps;
         const int grid = (int)std::max<long long>(1, std::min<long long>(general_grid, need));

@@ -139,3 +139,67 @@ def test_every_kernel_variant_matches_oracle(torch, plan, variant):
         else:
             assert p == pytest.approx(ref["psnr"], rel=1e-5, abs=1e-5)
     b.close()
+
+
+BOX_SHAPES = [(w, d, v) for w in (2, 4, 8) for d in (1, 2, 3) for v in (16, 8)]
+
+
+@pytest.mark.parametrize("shape", BOX_SHAPES, ids=[f"w{w}-d{d}-v{v}" for w, d, v in BOX_SHAPES])
+def test_every_box_shape_matches_oracle(torch, plan, shape):
+    """Each launch shape the autotuner may pick for the kernels of r <= 36
+    (tiles per CTA x staging depth x copy width), pinned: bit-exact pixels,
+    PSNR within tolerance, for every extent class (and a general job)."""
+    rs = [1, 2, 6, 7, 16, 21, 22, 36, 64, 1, 36, 6]
+    imgs = _mixed(13, n=len(rs), lo=16, hi=300)[0][:len(rs)]
+    src, dst = _dev(torch, imgs)
+    descs = [atdct16.image(s, d, r) for s, d, r in zip(src, dst, rs)]
+    psnr = torch.empty(len(imgs), dtype=torch.float64, device="cuda")
+    b = atdct16.Batch(plan, descs, psnr, flags=atdct16.BATCH_GRAPH | atdct16.batch_shape(*shape))
+    chosen = b.tuning()["chosen"]
+    assert (chosen["tiles_per_cta"], chosen["staging_depth"], chosen["vector_bytes"]) == shape
+    b.launch()
+    torch.cuda.synchronize()
+    for im, r, d, p in zip(imgs, rs, dst, psnr.cpu().tolist()):
+        ref = O.compress_zonal_exact(im, r)
+        assert np.array_equal(d.cpu().numpy(), ref["recon_u8"]), (shape, r)
+        assert p == pytest.approx(ref["psnr"], rel=1e-5, abs=1e-5)
+    b.close()
+
+
+def test_autotune_times_every_candidate(torch):
+    # r <= 36 and r > 36 jobs: the box shapes first, then the general variants
+    imgs, _ = _mixed(14, n=24, lo=64, hi=512)
+    rs = [(16, 36, 100)[i % 3] for i in range(len(imgs))]
+    src, dst = _dev(torch, imgs)
+    descs = [atdct16.image(s, d, r) for s, d, r in zip(src, dst, rs)]
+    psnr = torch.empty(len(imgs), dtype=torch.float64, device="cuda")
+    p = atdct16.Plan(atdct16.U8, max_images=64)
+    b = atdct16.Batch(p, descs, psnr, flags=atdct16.BATCH_AUTOTUNE)
+    t = b.tuning()
+    cands = t["candidates"]
+    shapes = {(c["tiles_per_cta"], c["staging_depth"], c["vector_bytes"]) for c in cands}
+    assert set(BOX_SHAPES) <= shapes
+    assert {c["variant"] for c in cands} == set(atdct16.ZONAL_VARIANTS)
+    assert all(c["ms"] > 0 for c in cands)
+    ch = t["chosen"]
+    # the box phase comes first (general shape at its default) and the chosen
+    # box shape is its fastest candidate; the general phase ran with that box
+    # shape and the chosen variant is its fastest
+    key = lambda c: (c["tiles_per_cta"], c["staging_depth"], c["vector_bytes"], c["box_ctas"])
+    box_phase = [c for c in cands if c["phase"] == 0]
+    gen_phase = [c for c in cands if c["phase"] == 1]
+    assert cands == box_phase + gen_phase
+    assert {(c["tiles_per_cta"], c["staging_depth"], c["vector_bytes"]) for c in box_phase} == set(BOX_SHAPES)
+    assert key(ch) == key(min(box_phase, key=lambda c: c["ms"]))
+    assert gen_phase and all(key(c) == key(ch) for c in gen_phase)
+    best_gen = min(gen_phase, key=lambda c: c["ms"])
+    assert (ch["variant"], ch["general_ctas"]) == (best_gen["variant"], best_gen["general_ctas"])
+    assert ch["ms"] == pytest.approx(best_gen["ms"])
+    b.launch()
+    torch.cuda.synchronize()
+    for im, r, d, pv in zip(imgs, rs, dst, psnr.cpu().tolist()):
+        ref = O.compress_zonal_exact(im, r)
+        assert np.array_equal(d.cpu().numpy(), ref["recon_u8"])
+        assert pv == pytest.approx(ref["psnr"], rel=1e-5, abs=1e-5)
+    b.close()
+    p.close()

@@ -155,7 +155,7 @@ def _small_images():
     return imgs
 
 
-@pytest.mark.parametrize("r", [0, 1, 2, 6, 16, 36, 64, 100, 136, 150, 255, 256])
+@pytest.mark.parametrize("r", [0, 1, 2, 6, 7, 16, 21, 22, 36, 37, 64, 100, 136, 150, 255, 256])
 def test_zonal_small_images_exact(torch, plan, r):
     imgs = _small_images()
     outs, psnr, sse = run_zonal(torch, plan, imgs, [r] * len(imgs))
@@ -169,6 +169,20 @@ def test_zonal_mixed_r_in_one_call_and_pitch(torch, plan):
     outs, psnr, sse = run_zonal(torch, plan, imgs, rs, pitch_extra=48)
     for img, r, out, p, s in zip(imgs, rs, outs, psnr, sse):
         check_zonal(img, r, out, p, s)
+
+
+def test_zonal_class_boundaries_in_one_call(torch, plan):
+    # every class of the split (kept set inside the 1x1, 3x3, 6x6 or 8x8 corner,
+    # or the general kernel) at the r where one class ends and the next begins,
+    # all in one call with pitched images
+    imgs = _small_images()
+    rs = [0, 1, 2, 3, 6, 7, 10, 15, 16, 21, 22, 28, 35, 36, 37, 66, 256]
+    allimgs = [im for _ in rs for im in imgs]
+    allrs = [r for r in rs for _ in imgs]
+    outs, psnr, sse = run_zonal(torch, plan, allimgs, allrs, pitch_extra=32)
+    for img, r, out, p, s in zip(allimgs, allrs, outs, psnr, sse):
+        check_zonal(img, r, out, p, s)
+    assert plan.last_device_status() == atdct16.OK
 
 
 def test_zonal_random_sizes(torch, plan):

@@ -71,3 +71,32 @@ def test_admission_under_a_small_budget(torch):
         srv.submit(big, torch.zeros_like(big), 16)
     assert e.value.status == atdct16.ENOMEM
     srv.close()
+
+
+def test_request_timing_stages_in_order(torch):
+    # requests with scheduled arrival times: every stage boundary on the
+    # server clock lies between the previous one and completion, the results
+    # stay exact, and wait() measures latency from the arrival
+    imgs, rs = _requests(12, 23, lo=64, hi=600)
+    srcs = [_pinned(torch, im) for im in imgs]
+    outs = [torch.zeros_like(s).pin_memory() for s in srcs]
+    srv = atdct16.Server(memory_budget_bytes=256 << 20, max_batch=4, compute_slots=2)
+    t0 = atdct16.server_clock()
+    tickets = [srv.submit(s, d, r, arrival=t0 - 0.001 * (len(imgs) - i)) for i, (s, d, r) in
+               enumerate(zip(srcs, outs, rs))]
+    eps = 2e-3  # device timestamps are placed on the host clock through one reference event
+    for i, (im, r, d, t) in enumerate(zip(imgs, rs, outs, tickets)):
+        p, tm = srv.wait_timing(t)
+        assert tm["arrival"] == pytest.approx(t0 - 0.001 * (len(imgs) - i), abs=1e-9)
+        order = [tm[k] for k in ("arrival", "submit", "h2d_start", "h2d_end", "compute_start", "compute_end",
+                                 "d2h_end", "done")]
+        assert all(b >= a - eps for a, b in zip(order, order[1:])), tm
+        assert tm["h2d_end"] >= tm["h2d_start"] and tm["compute_end"] >= tm["compute_start"]
+        ref = O.compress_zonal_exact(im, r)
+        assert np.array_equal(d.numpy(), ref["recon_u8"])
+        assert p == pytest.approx(ref["psnr"], rel=1e-5, abs=1e-5)
+    s2 = _pinned(torch, imgs[0])
+    arr = atdct16.server_clock() - 0.05
+    _, lat = srv.wait(srv.submit(s2, torch.zeros_like(s2).pin_memory(), 16, arrival=arr))
+    assert lat >= 0.05
+    srv.close()
