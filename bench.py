@@ -58,6 +58,8 @@ def parse_args():
                     help="run only the exact-DCT baseline phase (--steps applies) and print its JSON")
     ap.add_argument("--ssim-only", action="store_true",
                     help="run only the SSIM phase on one compressed step (--steps applies) and print its JSON")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving phase (config 5) and print its JSON")
     ap.add_argument("--coef-only", action="store_true",
                     help="run only the coefficient-pipeline phase (--steps applies) and print its JSON")
     ap.add_argument("--mixed-images", type=int, default=1000)
@@ -1141,6 +1143,20 @@ def run_ssim_only(args):
     return 0
 
 
+def run_serve_only(args):
+    """The serving phase alone, on one GPU."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1606_05562_gb300 import atdct16, synth
+    from paper_1606_05562_gb300 import build as b
+
+    b.build()
+    rates = [float(v) for v in args.serve_rates.split(",") if v]
+    print(json.dumps({"serving": serving_phase(torch, atdct16, synth, rates, args.serve_requests)}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -1149,6 +1165,8 @@ def main():
         return run_quant_only(args)
     if args.coef_only:
         return run_coef_only(args)
+    if args.serve_only:
+        return run_serve_only(args)
     if args.ssim_only:
         return run_ssim_only(args)
     if args.dct_only:
