@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--images", type=int, default=N_IMAGES,
+                    help="images per step (default: the 64-image workload; smaller for profiling captures)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-extras", action="store_true", help="skip the quantisation, mixed-batch and serving phases")
@@ -164,9 +166,9 @@ def kernel_source_sha256():
 
 
 def recorded_traffic():
-    """DRAM bytes per launch of the zonal kernel from the committed ncu
+    """DRAM bytes per call of the fused zonal kernels from the committed ncu
     summary, if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "zonal_kernel_64x512x512.md")
+    p = os.path.join(ROOT, "profiles", "zonal_kernels_64x512x512.md")
     try:
         text = open(p).read()
     except OSError:
@@ -856,9 +858,10 @@ def run_ours(args):
     from paper_1606_05562_gb300 import build as b
 
     b.build()
-    batch = synth.image_batch_512(N_IMAGES * world, SIDE, first_seed=100, indices=rank_images(world, rank))
+    n_img = args.images
+    batch = synth.image_batch_512(n_img * world, SIDE, first_seed=100, indices=rank_images(world, rank, n_per_rank=n_img))
     nr = len(R_SWEEP)
-    jobs = nr * N_IMAGES
+    jobs = nr * n_img
     px_step = jobs * SIDE * SIDE
 
     # rotating sets of inputs (one copy per r) and outputs, > 4 x L2 in total
@@ -868,7 +871,7 @@ def run_ours(args):
         src = base.unsqueeze(0).repeat(nr, 1, 1, 1).contiguous()
         dst = torch.empty_like(src)
         descs = atdct16.descriptors(
-            [atdct16.image(src[k, i], dst[k, i], r) for k, r in enumerate(R_SWEEP) for i in range(N_IMAGES)])
+            [atdct16.image(src[k, i], dst[k, i], r) for k, r in enumerate(R_SWEEP) for i in range(n_img)])
         sets.append((src, dst, descs))
     plan = atdct16.Plan(atdct16.U8, max_images=jobs)
     psnr = torch.empty(jobs, dtype=torch.float64, device=dev)
@@ -952,12 +955,12 @@ def run_ours(args):
     # stream) and a PSNR-only readback are reported beside it.
     h_src = torch.from_numpy(batch).pin_memory()
     d_src2 = [torch.empty_like(base) for _ in range(2)]
-    d_dst2 = [torch.empty((nr, N_IMAGES, SIDE, SIDE), dtype=torch.uint8, device=dev) for _ in range(2)]
+    d_dst2 = [torch.empty((nr, n_img, SIDE, SIDE), dtype=torch.uint8, device=dev) for _ in range(2)]
     h_dst2 = [torch.empty(d_dst2[0].shape, dtype=torch.uint8).pin_memory() for _ in range(2)]
     psnr2 = [torch.empty(jobs, dtype=torch.float64, device=dev) for _ in range(2)]
     h_psnr2 = [torch.empty(jobs, dtype=torch.float64).pin_memory() for _ in range(2)]
     descs2 = [atdct16.descriptors([atdct16.image(d_src2[b][i], d_dst2[b][k, i], r)
-                                   for k, r in enumerate(R_SWEEP) for i in range(N_IMAGES)]) for b in range(2)]
+                                   for k, r in enumerate(R_SWEEP) for i in range(n_img)]) for b in range(2)]
     s_in, s_cmp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_cmp = [torch.cuda.Event() for _ in range(2)]
@@ -1021,7 +1024,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "images": N_IMAGES, "side": SIDE, "r_sweep": list(R_SWEEP),
+            "config": {"workload": WORKLOAD.replace("64x", f"{n_img}x", 1), "images": n_img, "side": SIDE, "r_sweep": list(R_SWEEP),
                        "jobs_per_step": jobs, "pixels_per_step": px_step, "parallelism": f"dp{world} (image shards)",
                        "l2": f"{N_SETS} rotating input/output sets of {2 * px_step / 1e6:.0f} MB (> 4 x L2)"},
             "roofline": roof,
