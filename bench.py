@@ -839,6 +839,20 @@ def serving_phase(torch, atdct16, synth, rates, total, seed=5):
             "note": "latency = scheduled Poisson arrival to completion; H2D and D2H of the request included"}
 
 
+def serving_in_own_process(args):
+    """The serving phase in a fresh process (`--serve-only`), as a server runs:
+    its pinned buffers and device arena are allocated in a process that has not
+    run the other phases."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--serve-only", "--serve-rates", args.serve_rates,
+           "--serve-requests", str(args.serve_requests)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("serving phase failed: " + r.stderr[-2000:])
+    res = json.loads(r.stdout.strip().splitlines()[-1])["serving"]
+    res["process"] = "own process (bench.py --serve-only)"
+    return res
+
+
 # --------------------------------------------------------------------------
 def run_ours(args):
     import torch
@@ -1050,8 +1064,7 @@ def run_ours(args):
             line["mixed_batch"] = mixed_batch_phase(torch, atdct16, synth, dev, args.mixed_images,
                                                     cpu_oracle=args.cpu_seconds > 0)
             torch.cuda.empty_cache()
-            rates = [float(v) for v in args.serve_rates.split(",") if v]
-            line["serving"] = serving_phase(torch, atdct16, synth, rates, args.serve_requests)
+            line["serving"] = serving_in_own_process(args)
         print(json.dumps(line), flush=True)
     plan.close()
     if dist:
