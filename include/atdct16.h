@@ -276,9 +276,10 @@ atdct16_status atdct16_psnr(atdct16_dtype dtype, const void* d_a, int64_t pitch_
 #define ATDCT16_BATCH_GRAPH 2u    /* capture the launches into a CUDA graph */
 /* Pin the kernel variant instead (not with ATDCT16_BATCH_AUTOTUNE):
  * flags |= ATDCT16_BATCH_VARIANT(v), v = 0 (integer row pass, FP32 column
- * pass), 1 (forward transform in int16 SWAR, the default) or 2 (forward
- * transform on the tensor cores).  All variants give the same stored pixels;
- * PSNR agrees to FP32 summation order. */
+ * pass), 1 (forward transform in int16 SWAR, the default), 2 (forward
+ * transform as mma.sync tensor-core products) or 3 (forward transform as
+ * tcgen05 products with the accumulators in tensor memory).  All variants
+ * give the same stored pixels; PSNR agrees to FP32 summation order. */
 #define ATDCT16_BATCH_VARIANT_SHIFT 8
 #define ATDCT16_BATCH_VARIANT_MASK (7u << ATDCT16_BATCH_VARIANT_SHIFT)
 #define ATDCT16_BATCH_VARIANT(v) ((uint32_t)((v) + 1) << ATDCT16_BATCH_VARIANT_SHIFT)
@@ -305,10 +306,10 @@ atdct16_status atdct16_batch_create(atdct16_plan_t plan, const atdct16_image* h_
 /* Re-run the batch on `stream` (asynchronous). */
 atdct16_status atdct16_batch_launch(atdct16_batch_t batch, cudaStream_t stream);
 /* Chosen launch shape: variant (0: integer row pass + FP32 column pass,
- * 1: forward transform in int16 SWAR, 2: forward transform on the tensor
- * cores), warps per CTA, prefetch (always 1: input rows are staged two tiles
- * ahead), grid size, tile count and the tuned time per launch in ms (0 if
- * untuned).
+ * 1: forward transform in int16 SWAR, 2: forward transform as mma.sync
+ * products, 3: forward transform as tcgen05 products), warps per CTA,
+ * prefetch (always 1: input rows are staged ahead), grid size, tile count
+ * and the tuned time per launch in ms (0 if untuned).
  * Any pointer may be NULL. */
 atdct16_status atdct16_batch_info(atdct16_batch_t batch, int32_t* variant, int32_t* warps, int32_t* prefetch,
                                   int32_t* grid, int64_t* tiles, float* tuned_ms);

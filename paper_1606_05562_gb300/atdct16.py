@@ -284,11 +284,11 @@ class Plan:
 
 
 BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2
-ZONAL_VARIANTS = ("f32", "swar", "mma")
+ZONAL_VARIANTS = ("f32", "swar", "mma", "tc")
 
 
 def batch_variant(v):
-    """Flag that pins the zonal kernel variant of a Batch (0, 1 or 2)."""
+    """Flag that pins the zonal kernel variant of a Batch (0, 1, 2 or 3)."""
     return (v + 1) << 8
 
 

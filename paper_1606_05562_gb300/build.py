@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_NAME = "libatdct16.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
-SOURCES = ["atdct16_kernels.cu", "atdct16_zonal_box.cu", "atdct16_coef.cu", "atdct16_api.cu", "atdct16_batch.cu", "atdct16_noalloc.cu", "atdct16_server.cu"]
+SOURCES = ["atdct16_kernels.cu", "atdct16_zonal_box.cu", "atdct16_zonal_tc.cu", "atdct16_coef.cu", "atdct16_api.cu", "atdct16_batch.cu", "atdct16_noalloc.cu", "atdct16_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -224,7 +224,7 @@ atdct16_status autotune(atdct16_batch_st* b, int sms, cudaStream_t stream) {
         }
   }
   if (has_general && st == ATDCT16_OK) {
-    const ZonalConfig gens[] = {{kZonalSwar, 4, 1}, {kZonalF32, 4, 1}, {kZonalMma, 4, 1}};
+    const ZonalConfig gens[] = {{kZonalSwar, 4, 1}, {kZonalF32, 4, 1}, {kZonalMma, 4, 1}, {kZonalTc, 4, 1}};
     best = 1e30f;
     for (const ZonalConfig& c : gens) {
       const int maxc = zonal_config_max_ctas_per_sm(c);

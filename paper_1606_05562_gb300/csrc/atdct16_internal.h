@@ -46,9 +46,10 @@ constexpr int kDevTimeout = 2;  // a bounded wait on an asynchronous copy expire
 // Launch shapes of the fused zonal kernel (chosen by the batch autotuner).
 constexpr int kZonalF32 = 0;   // integer row pass, FP32 column pass and inverse
 constexpr int kZonalSwar = 1;  // whole forward transform on the integer pipe (int16 SWAR)
-constexpr int kZonalMma = 2;   // forward transform as f16 tensor-core products (exact)
+constexpr int kZonalMma = 2;   // forward transform as f16 tensor-core products (exact), mma.sync
+constexpr int kZonalTc = 3;    // forward transform as tcgen05 products with TMEM accumulators (exact)
 struct ZonalConfig {
-  int variant;   // kZonalF32, kZonalSwar or kZonalMma
+  int variant;   // kZonalF32, kZonalSwar, kZonalMma or kZonalTc
   int warps;     // warps per CTA: 2, 4 or 8 (SWAR: 4)
   int prefetch;  // 1: load the next tile while computing the current one
 };
@@ -60,6 +61,11 @@ int zonal_config_max_ctas_per_sm(const ZonalConfig& c);
 cudaError_t launch_zonal_config(const ZonalConfig& cfg, const ImageJob* d_jobs, int njobs, long long ntiles,
                                 const float2* d_wtab, float* d_tile_sse, int* d_status, int grid,
                                 cudaStream_t stream, bool dependent = false, bool early = false);
+// The tcgen05 variant (atdct16_zonal_tc.cu): one warpgroup per CTA.
+cudaError_t launch_zonal_tc(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
+                            float* d_tile_sse, int* d_status, int grid, cudaStream_t stream, bool dependent,
+                            bool early);
+int zonal_tc_max_ctas_per_sm();
 // d_levels (optional, 16-byte aligned): int16 levels per block, row-major
 // in (u, v) or, with zigzag, in zig-zag order.
 cudaError_t launch_quant(const ImageJob* d_jobs, int njobs, long long ntiles, const float4* d_qtab,

@@ -1639,7 +1639,11 @@ static cudaError_t occupancy_with_smem(int* n, K kernel, int threads, int smem) 
 
 static int config_index(const ZonalConfig& c) {
   if (!c.prefetch || c.warps != 4) return -1;
-  return c.variant == kZonalSwar ? 0 : (c.variant == kZonalF32 ? 1 : (c.variant == kZonalMma ? 2 : -1));
+  return c.variant == kZonalSwar ? 0
+         : c.variant == kZonalF32 ? 1
+         : c.variant == kZonalMma ? 2
+         : c.variant == kZonalTc  ? 3
+                                  : -1;
 }
 
 bool zonal_config_supported(const ZonalConfig& c) { return config_index(c) >= 0; }
@@ -1661,6 +1665,8 @@ cudaError_t launch_zonal_config(const ZonalConfig& cfg, const ImageJob* d_jobs, 
     case 2:
       return launch_chained(zonal_mma_kernel<4>, grid, threads, 4 * kZonalMmaWarpSmemBytes, stream, dependent,
                             d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, pe);
+    case 3:
+      return launch_zonal_tc(d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, grid, stream, dependent, early);
   }
   return cudaErrorInvalidValue;
 }
@@ -1673,6 +1679,7 @@ int zonal_config_max_ctas_per_sm(const ZonalConfig& cfg) {
     case 0: e = occupancy_with_smem(&n, zonal_f32_kernel<4, true>, 128, 4 * zs); break;
     case 1: e = occupancy_with_smem(&n, zonal_f32_kernel<4, false>, 128, 4 * zs); break;
     case 2: e = occupancy_with_smem(&n, zonal_mma_kernel<4>, 128, 4 * kZonalMmaWarpSmemBytes); break;
+    case 3: return zonal_tc_max_ctas_per_sm();
   }
   return (e == cudaSuccess && n > 0) ? n : 1;
 }

@@ -118,7 +118,7 @@ def test_autotune_rejects_in_place(torch, plan):
     b.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_every_kernel_variant_matches_oracle(torch, plan, variant):
     """Each zonal kernel variant, pinned: bit-exact pixels against the exact
     oracle, PSNR within the FP tolerance (r spans every mask extent)."""
@@ -139,6 +139,45 @@ def test_every_kernel_variant_matches_oracle(torch, plan, variant):
         else:
             assert p == pytest.approx(ref["psnr"], rel=1e-5, abs=1e-5)
     b.close()
+
+
+def test_tc_variant_long_pipeline_matches_oracle(torch, plan):
+    """The tcgen05 variant with every CTA walking several tile pairs (its
+    software pipeline in steady state), pairs that straddle images of
+    different sizes and r, ragged tiles: pixels bit-identical to the
+    integer-pipe variant's on every image and to the exact oracle on a
+    sample; PSNR within the FP tolerance."""
+    rng = np.random.default_rng(21)
+    imgs = [synth.ar1_image(512, 512, 0.95, 300 + i) for i in range(48)]
+    imgs += _mixed(22, n=12, lo=16, hi=400)[0]
+    order = rng.permutation(len(imgs))
+    imgs = [imgs[i] for i in order]
+    rs = [int(v) for v in rng.choice([0, 37, 64, 100, 150, 200, 255, 256], size=len(imgs))]
+    out = {}
+    for v in (1, 3):
+        src, dst = _dev(torch, imgs)
+        descs = [atdct16.image(s, d, r) for s, d, r in zip(src, dst, rs)]
+        psnr = torch.empty(len(imgs), dtype=torch.float64, device="cuda")
+        b = atdct16.Batch(plan, descs, psnr, flags=atdct16.BATCH_GRAPH | atdct16.batch_variant(v))
+        info = b.info()
+        assert info["variant"] == atdct16.ZONAL_VARIANTS[v]
+        if v == 3:
+            assert info["tiles"] >= 8 * info["grid"]  # several pairs per CTA
+        b.launch()
+        b.launch()
+        torch.cuda.synchronize()
+        out[v] = ([d.cpu().numpy() for d in dst], psnr.cpu().tolist())
+        b.close()
+    for a, c in zip(out[1][0], out[3][0]):
+        assert np.array_equal(a, c)
+    assert out[3][1] == pytest.approx(out[1][1], rel=1e-5, abs=1e-5)
+    for k in [0, 1] + [i for i in range(len(imgs)) if imgs[i].shape[1] % 128][:2]:
+        ref = O.compress_zonal_exact(imgs[k], rs[k])
+        assert np.array_equal(out[3][0][k], ref["recon_u8"]), rs[k]
+        if math.isinf(ref["psnr"]):
+            assert math.isinf(out[3][1][k])
+        else:
+            assert out[3][1][k] == pytest.approx(ref["psnr"], rel=1e-5, abs=1e-5)
 
 
 BOX_SHAPES = [(w, d, v) for w in (2, 4, 8) for d in (1, 2, 3) for v in (16, 8)]
