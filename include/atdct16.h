@@ -100,12 +100,20 @@ const char* atdct16_status_string(atdct16_status s);
  *                  atdct16_inverse announces 16 bytes more than its bulk
  *                  copies deliver, so its bounded waits expire (about 2 s per
  *                  call) and atdct16_last_device_status reports
+ *                  ATDCT16_ETIMEOUT; the context stays usable.
+ *                  ATDCT16_PLAN_TEST_STALL_MMA (failure-path test hook): a
+ *                  batch on this plan that runs the tcgen05 kernel variant
+ *                  issues no tensor-core product, so every CTA's bounded wait
+ *                  on the first one expires (about half a second), the CTA
+ *                  frees its tensor memory and returns, results are left
+ *                  undefined and atdct16_batch_last_device_status reports
  *                  ATDCT16_ETIMEOUT; the context stays usable.  Other bits:
  *                  ATDCT16_EINVAL.
  * Allocates the plan's workspace (device tables, descriptor ring, partials)
  * with cudaMalloc and pinned host staging with cudaHostAlloc. */
 #define ATDCT16_PLAN_ZIGZAG 1u
 #define ATDCT16_PLAN_TEST_STALL_COPIES 0x80000000u
+#define ATDCT16_PLAN_TEST_STALL_MMA 0x40000000u
 atdct16_status atdct16_plan_create(atdct16_plan_t* plan, atdct16_dtype dtype, int32_t max_images,
                                    size_t workspace_budget_bytes, uint32_t flags);
 
@@ -311,6 +319,11 @@ atdct16_status atdct16_batch_launch(atdct16_batch_t batch, cudaStream_t stream);
  * prefetch (always 1: input rows are staged ahead), grid size, tile count
  * and the tuned time per launch in ms (0 if untuned).
  * Any pointer may be NULL. */
+/* Device-side status of the batch's launches so far (sticky, first error
+ * wins): waits for the last launch's stream, then ATDCT16_OK,
+ * ATDCT16_ETIMEOUT (a bounded wait of a kernel expired; that launch's results
+ * are undefined) or ATDCT16_EDEVICE (a kernel's own checks failed). */
+atdct16_status atdct16_batch_last_device_status(atdct16_batch_t batch);
 atdct16_status atdct16_batch_info(atdct16_batch_t batch, int32_t* variant, int32_t* warps, int32_t* prefetch,
                                   int32_t* grid, int64_t* tiles, float* tuned_ms);
 /* One launch shape of a batch and its time.  The general kernel (jobs with

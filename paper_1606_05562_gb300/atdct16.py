@@ -17,6 +17,7 @@ from . import build as _build
 U8, I16 = 0, 1
 PLAN_ZIGZAG = 1  # ATDCT16_PLAN_ZIGZAG
 PLAN_TEST_STALL_COPIES = 0x80000000  # ATDCT16_PLAN_TEST_STALL_COPIES (failure-path test hook)
+PLAN_TEST_STALL_MMA = 0x40000000  # ATDCT16_PLAN_TEST_STALL_MMA (failure-path test hook)
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EDEVICE = range(7)
 
 
@@ -96,6 +97,7 @@ _SIGS = {
     "atdct16_batch_create": (C.c_int, [C.c_void_p, C.POINTER(Image), C.c_int32, C.c_void_p, C.c_void_p, C.c_uint32,
                                        C.c_void_p, C.POINTER(C.c_void_p)]),
     "atdct16_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "atdct16_batch_last_device_status": (C.c_int, [C.c_void_p]),
     "atdct16_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                      C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_float)]),
     "atdct16_batch_destroy": (C.c_int, [C.c_void_p]),
@@ -325,6 +327,10 @@ class Batch:
 
     def launch(self, stream=None):
         _check(lib().atdct16_batch_launch(self._h, _stream(stream)), "batch_launch")
+
+    def last_device_status(self) -> int:
+        """Sticky device status of this batch's launches (waits for the last one)."""
+        return lib().atdct16_batch_last_device_status(self._h)
 
     def info(self):
         v, w, p, g = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()

@@ -19,6 +19,7 @@ struct atdct16_plan_st {
   atdct16_dtype dtype = ATDCT16_U8;
   bool zigzag = false;                  // ATDCT16_PLAN_ZIGZAG: block coefficients / levels in zig-zag order
   bool stall_copies = false;            // ATDCT16_PLAN_TEST_STALL_COPIES (failure-path test hook)
+  bool stall_mma = false;               // ATDCT16_PLAN_TEST_STALL_MMA (failure-path test hook)
   int max_images = 0;
   long long max_tiles = 0;
   int num_sms = 0;
@@ -175,6 +176,7 @@ namespace atdct16 {
 const float2* plan_zonal_table(const atdct16_plan_st* plan) { return plan->d_wtab; }
 int plan_num_sms(const atdct16_plan_st* plan) { return plan->num_sms; }
 int plan_device(const atdct16_plan_st* plan) { return plan->device; }
+bool plan_test_stall_mma(const atdct16_plan_st* plan) { return plan->stall_mma; }
 bool plan_tune_lookup(atdct16_plan_st* plan, unsigned long long key, ZonalConfig* cfg, int* ctas, BoxConfig* box,
                       float* ms) {
   auto it = plan->tuned.find(key);
@@ -240,7 +242,7 @@ atdct16_status atdct16_plan_destroy(atdct16_plan_t plan) {
 
 atdct16_status atdct16_plan_create(atdct16_plan_t* out, atdct16_dtype dtype, int32_t max_images,
                                    size_t workspace_budget_bytes, uint32_t flags) {
-  if (!out || max_images < 1 || (flags & ~(ATDCT16_PLAN_ZIGZAG | ATDCT16_PLAN_TEST_STALL_COPIES)) != 0 || (dtype != ATDCT16_U8 && dtype != ATDCT16_I16))
+  if (!out || max_images < 1 || (flags & ~(ATDCT16_PLAN_ZIGZAG | ATDCT16_PLAN_TEST_STALL_COPIES | ATDCT16_PLAN_TEST_STALL_MMA)) != 0 || (dtype != ATDCT16_U8 && dtype != ATDCT16_I16))
     return ATDCT16_EINVAL;
   *out = nullptr;
   atdct16_plan_st* plan = new (std::nothrow) atdct16_plan_st();
@@ -248,6 +250,7 @@ atdct16_status atdct16_plan_create(atdct16_plan_t* out, atdct16_dtype dtype, int
   plan->dtype = dtype;
   plan->zigzag = (flags & ATDCT16_PLAN_ZIGZAG) != 0;
   plan->stall_copies = (flags & ATDCT16_PLAN_TEST_STALL_COPIES) != 0;
+  plan->stall_mma = (flags & ATDCT16_PLAN_TEST_STALL_MMA) != 0;
   plan->max_images = max_images;
   if (cudaGetDevice(&plan->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device) != cudaSuccess) {

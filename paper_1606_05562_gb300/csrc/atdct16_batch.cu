@@ -360,6 +360,7 @@ atdct16_status atdct16_batch_create(atdct16_plan_t plan, const atdct16_image* h_
     }
   }
   b->grid = grid_for(b->cfg, b->ctas, sms, tiles);
+  b->cfg.test_stall = plan_test_stall_mma(plan) ? 1 : 0;
 
   if (flags & ATDCT16_BATCH_GRAPH) {
     // Capture on a private stream so that the caller's stream is untouched.
@@ -393,6 +394,14 @@ atdct16_status atdct16_batch_launch(atdct16_batch_t b, cudaStream_t stream) {
   b->last_stream = stream;
   cudaError_t e = b->exec ? cudaGraphLaunch(b->exec, stream) : launch_batch_once(b, b->cfg, b->grid, b->box, stream);
   return e == cudaSuccess ? ATDCT16_OK : ATDCT16_ECUDA;
+}
+
+atdct16_status atdct16_batch_last_device_status(atdct16_batch_t b) {
+  if (!b) return ATDCT16_EINVAL;
+  if (b->last_stream && cudaStreamSynchronize(b->last_stream) != cudaSuccess) return ATDCT16_ECUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, b->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return ATDCT16_ECUDA;
+  return v == kDevOk ? ATDCT16_OK : (v == kDevTimeout ? ATDCT16_ETIMEOUT : ATDCT16_EDEVICE);
 }
 
 atdct16_status atdct16_batch_info(atdct16_batch_t b, int32_t* variant, int32_t* warps, int32_t* prefetch,

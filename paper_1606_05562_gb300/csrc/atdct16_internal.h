@@ -52,6 +52,7 @@ struct ZonalConfig {
   int variant;   // kZonalF32, kZonalSwar, kZonalMma or kZonalTc
   int warps;     // warps per CTA: 2, 4 or 8 (SWAR: 4)
   int prefetch;  // 1: load the next tile while computing the current one
+  int test_stall = 0;  // failure-path test hook: the tcgen05 variant issues no MMA, so its bounded waits expire
 };
 bool zonal_config_supported(const ZonalConfig& c);
 ZonalConfig default_zonal_config();
@@ -64,7 +65,7 @@ cudaError_t launch_zonal_config(const ZonalConfig& cfg, const ImageJob* d_jobs, 
 // The tcgen05 variant (atdct16_zonal_tc.cu): one warpgroup per CTA.
 cudaError_t launch_zonal_tc(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
                             float* d_tile_sse, int* d_status, int grid, cudaStream_t stream, bool dependent,
-                            bool early);
+                            bool early, bool stall = false);
 int zonal_tc_max_ctas_per_sm();
 // d_levels (optional, 16-byte aligned): int16 levels per block, row-major
 // in (u, v) or, with zigzag, in zig-zag order.
@@ -138,6 +139,7 @@ namespace atdct16 {
 const float2* plan_zonal_table(const atdct16_plan_st* plan);
 int plan_num_sms(const atdct16_plan_st* plan);
 int plan_device(const atdct16_plan_st* plan);
+bool plan_test_stall_mma(const atdct16_plan_st* plan);
 bool plan_tune_lookup(atdct16_plan_st* plan, unsigned long long key, ZonalConfig* cfg, int* ctas, BoxConfig* box,
                       float* ms);
 void plan_tune_store(atdct16_plan_st* plan, unsigned long long key, const ZonalConfig& cfg, int ctas,

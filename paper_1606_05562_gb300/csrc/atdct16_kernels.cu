@@ -1666,7 +1666,8 @@ cudaError_t launch_zonal_config(const ZonalConfig& cfg, const ImageJob* d_jobs, 
       return launch_chained(zonal_mma_kernel<4>, grid, threads, 4 * kZonalMmaWarpSmemBytes, stream, dependent,
                             d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, pe);
     case 3:
-      return launch_zonal_tc(d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, grid, stream, dependent, early);
+      return launch_zonal_tc(d_jobs, njobs, ntiles, d_wtab, d_tile_sse, d_status, grid, stream, dependent, early,
+                             cfg.test_stall != 0);
   }
   return cudaErrorInvalidValue;
 }

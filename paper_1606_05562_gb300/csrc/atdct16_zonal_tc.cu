@@ -93,7 +93,7 @@ __device__ __forceinline__ void store_row_f16(unsigned char* a, const uint4& x) 
 
 __global__ void __launch_bounds__(128, 4)
 zonal_tc_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_ll, const float2* __restrict__ wtab,
-                float* __restrict__ tile_sse, int* __restrict__ status, int pdl_early) {
+                float* __restrict__ tile_sse, int* __restrict__ status, int pdl_early, int stall) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tau = warp >> 1;                   // tile of the pair
@@ -279,7 +279,7 @@ zonal_tc_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_l
   to_a1(0);
   tc::fence_proxy_async();
   __syncthreads();
-  if (tid == 0) issue_mma1();
+  if (tid == 0 && !stall) issue_mma1();  // stall: the failure-path test hook, no product ever arrives
   bad = !tc::mbar_wait(bar1, 0, kTcWaitCycles);
   tc::fence_after_sync();
   to_a2();
@@ -413,9 +413,9 @@ int zonal_tc_smem_bytes() { return kTcSmemBytes; }
 
 cudaError_t launch_zonal_tc(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
                             float* d_tile_sse, int* d_status, int grid, cudaStream_t stream, bool dependent,
-                            bool early) {
+                            bool early, bool stall) {
   return launch_chained(zonal_tc_kernel, grid, 128, kTcSmemBytes, stream, dependent, d_jobs, njobs, ntiles, d_wtab,
-                        d_tile_sse, d_status, early ? 1 : 0);
+                        d_tile_sse, d_status, early ? 1 : 0, stall ? 1 : 0);
 }
 
 // CTAs of the kernel that fit on one SM.  The occupancy calculator answers 1

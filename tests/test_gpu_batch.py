@@ -180,6 +180,34 @@ def test_tc_variant_long_pipeline_matches_oracle(torch, plan):
             assert out[3][1][k] == pytest.approx(ref["psnr"], rel=1e-5, abs=1e-5)
 
 
+def test_tc_variant_tensor_wait_times_out_cleanly(torch):
+    """With the MMA stall test hook the tcgen05 kernel issues no product: every
+    CTA's bounded wait on the tensor core expires, it frees its tensor memory
+    and returns, the batch's device status reads ETIMEOUT, and the context
+    keeps working (a following tcgen05 batch matches the oracle)."""
+    imgs = [synth.ar1_image(64, 256, 0.9, 40 + i) for i in range(3)]
+    rs = [64, 150, 256]
+    stall = atdct16.Plan(atdct16.U8, max_images=8, flags=atdct16.PLAN_TEST_STALL_MMA)
+    src, dst = _dev(torch, imgs)
+    psnr = torch.empty(len(imgs), dtype=torch.float64, device="cuda")
+    b = atdct16.Batch(stall, [atdct16.image(s, d, r) for s, d, r in zip(src, dst, rs)], psnr,
+                      flags=atdct16.batch_variant(3))
+    b.launch()
+    assert b.last_device_status() == atdct16.ETIMEOUT
+    b.close()
+    stall.close()
+    ok = atdct16.Plan(atdct16.U8, max_images=8)
+    src, dst = _dev(torch, imgs)
+    b = atdct16.Batch(ok, [atdct16.image(s, d, r) for s, d, r in zip(src, dst, rs)], psnr,
+                      flags=atdct16.batch_variant(3))
+    b.launch()
+    assert b.last_device_status() == atdct16.OK
+    for im, r, d in zip(imgs, rs, dst):
+        assert np.array_equal(d.cpu().numpy(), O.compress_zonal_exact(im, r)["recon_u8"]), r
+    b.close()
+    ok.close()
+
+
 BOX_SHAPES = [(w, d, v) for w in (2, 4, 8) for d in (1, 2, 3) for v in (16, 8)]
 
 

@@ -288,5 +288,5 @@ def test_inverse_copy_wait_times_out_cleanly(torch):
 
 def test_unknown_plan_flags_rejected(torch):
     with pytest.raises(atdct16.Atdct16Error) as e:
-        atdct16.Plan(atdct16.U8, max_images=1, flags=0x40000000)
+        atdct16.Plan(atdct16.U8, max_images=1, flags=0x20000000)
     assert e.value.status == atdct16.EINVAL
