@@ -458,6 +458,48 @@ def quant_phase(torch, atdct16, synth, dev, n_frames, chunk, steps, warmup, peak
 
 
 # --------------------------------------------------------------------------
+def general_variants_phase(torch, atdct16, batch, dev, reps=100):
+    """The general zonal kernel's variants on the r > 36 half of the bench
+    workload (the 64 images x r in {64, 100, 150, 256}: 256 jobs, 32768
+    tiles, 134 MB moved per launch), each pinned through the batch API:
+    integer-pipe forward (int16 SWAR, the default), FP32 column pass, the
+    forward as mma.sync f16 products, and as tcgen05 products with TMEM
+    accumulators.  Time per launch of the batch (kernel + PSNR finalize),
+    and whether every variant stored the same pixels as the default."""
+    R = (64, 100, 150, 256)
+    base = torch.from_numpy(batch).to(dev)
+    src = base.unsqueeze(0).repeat(len(R), 1, 1, 1).contiguous()
+    dst = torch.empty_like(src)
+    ref = None
+    plan = atdct16.Plan(atdct16.U8, max_images=len(R) * base.shape[0])
+    psnr = torch.empty(len(R) * base.shape[0], dtype=torch.float64, device=dev)
+    descs = [atdct16.image(src[k, i], dst[k, i], r) for k, r in enumerate(R) for i in range(base.shape[0])]
+    out = {"r": list(R), "tiles": None, "us_per_launch": {}, "identical_pixels": True}
+    for v in (1, 0, 2, 3):
+        dst.fill_(7)
+        b = atdct16.Batch(plan, descs, psnr, flags=atdct16.batch_variant(v))
+        out["tiles"] = b.info()["tiles"]
+        for _ in range(5):
+            b.launch()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        out["us_per_launch"][atdct16.ZONAL_VARIANTS[v]] = e0.elapsed_time(e1) / reps * 1e3
+        if b.last_device_status() != atdct16.OK:
+            raise RuntimeError(f"zonal variant {v}: device status {b.last_device_status()}")
+        b.close()
+        if ref is None:
+            ref = dst.clone()
+        elif not torch.equal(dst, ref):
+            out["identical_pixels"] = False
+    plan.close()
+    return out
+
+
 def coef_phase(torch, atdct16, batch, dev, peak_gbs, reps=50):
     """The standalone coefficient pipeline on one 4096 x 8192 u8 image (the
     64 bench images tiled 8 x 8, beside its mirror image; 33.5 Mpx): 2-D
@@ -1054,6 +1096,7 @@ def run_ours(args):
             line["config1"] = config1_phase(torch, atdct16, synth, dev)
             line["psnr_u8_by_r"] = psnr_u8_by_r(torch, atdct16, sets[0][0], sets[0][1])
             line["coefficients"] = coef_phase(torch, atdct16, batch, dev, peak)
+            line["general_variants"] = general_variants_phase(torch, atdct16, batch, dev)
             line["ssim"] = ssim_phase(torch, atdct16, plan, sets[0][2], jobs, px_step)
             line["dct_baseline"] = dct_baseline_phase(torch, atdct16, plan, sets, jobs, px_step, None)
             del sets
