@@ -10,7 +10,8 @@
 //     columns and computes K outputs (46 of the 60 additions of Sec. 2 for
 //     K = 8, fewer for smaller K; the unused outputs are dead code);
 //   * the inverse has only K non-zero inputs in each direction (38 of 60
-//     additions for K = 8, none at all for K = 1);
+//     additions for K = 8, none at all for K = 1: there the kernel sums
+//     each block with dp4a and stores the rounded constant 9 Y[0][0] / 2304);
 //   * the squared error needs no dropped coefficient: with the orthonormal
 //     C_hat, SSE = ||X - X_hat||^2 = ||X||^2 - ||B'||^2, and both terms are
 //     exact integers here.  With pixels centred at 128 (which changes only
@@ -69,6 +70,12 @@ __host__ __device__ constexpr int box_warp_smem(int depth) { return kBoxFixedByt
 // walks the anti-diagonals s = u + v in order, so the prefix stays inside
 // while it covers only s < K, i.e. its first K (K + 1) / 2 coefficients.
 __host__ __device__ constexpr int box_max_r(int k) { return k * (k + 1) / 2; }
+
+// rne(z / 2304) of one exact integer z as raw denormal bits: the products of
+// rne_denormal(f2mul(., kInv2304)) for one lane.
+__device__ __forceinline__ unsigned round_dc(float z) {
+  return __float_as_uint(__fmul_rn(__fmul_rn(z, kInv2304), __uint_as_float(1u)));
+}
 
 struct BoxTile {
   const uint8_t* src;  // row 2j of block p of this lane
@@ -271,8 +278,65 @@ zonal_box_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     }
     const bool va = p < cur.nb, vb = p + 4 < cur.nb;
 
-    // ---- pixel energy (dp4a over the 64 input bytes) and the row pass
-    const unsigned ex = pixel_energy(X);
+    const unsigned ex = pixel_energy(X);  // dp4a over the 64 input bytes
+    unsigned long long ke = 0ull;
+    long long dc_term = 0;
+    BoxTile fut;
+    bool have_fut;
+    if constexpr (K == 1) {
+      // ---- DC only (r = 1).  The kept coefficient is the block sum Y[0][0]
+      // (row 0 of T is all ones), and the inverse of a lone DC is the
+      // constant W_0^2 Y[0][0] = 9 Y_c[0][0] + 2304 * 128 at every pixel, an
+      // integer below 2^24: the value the pruned passes form, rounded by the
+      // same two multiplies.  Each lane sums its two rows of blocks p and
+      // p + 4 (dp4a against ones, each partial < 2^13), the 8 lanes of a block
+      // pair add them up as two 16-bit halves of one word (totals < 2^16).
+      unsigned s2 = 0u;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        s2 = __dp4a(X[k].x, 0x01010101u, s2);
+        s2 = __dp4a(X[k].y, 0x01010101u, s2);
+        s2 = __dp4a(X[k].z, 0x01010101u, s2);
+        s2 = __dp4a(X[k].w, 0x01010101u, s2);
+      }
+      unsigned sb = 0u;
+#pragma unroll
+      for (int k = 2; k < 4; ++k) {
+        sb = __dp4a(X[k].x, 0x01010101u, sb);
+        sb = __dp4a(X[k].y, 0x01010101u, sb);
+        sb = __dp4a(X[k].z, 0x01010101u, sb);
+        sb = __dp4a(X[k].w, 0x01010101u, sb);
+      }
+      s2 |= sb << 16;
+      s2 += __shfl_xor_sync(0xffffffffu, s2, 4);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, 8);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, 16);
+      const int ya = (int)(s2 & 0xffffu) - 32768, yb = (int)(s2 >> 16) - 32768;  // Y_c[0][0], blocks p, p + 4
+
+      have_fut = hq[D - 1] && ok && c_t < t_stop;  // the input rows of the tile D ahead
+      if (have_fut) {
+        take(fut);
+        ok = advance();
+        issue(fut, st);
+      } else {
+        cp_async_commit();
+      }
+
+      const unsigned qa = round_dc(__fmaf_rn((float)ya, 9.0f, 294912.0f));
+      const unsigned qb = round_dc(__fmaf_rn((float)yb, 9.0f, 294912.0f));
+      const unsigned wa = pack_u8(qa, qa, pack_u8(qa, qa, 0u)), wb = pack_u8(qb, qb, pack_u8(qb, qb, 0u));
+#pragma unroll
+      for (int tr = 0; tr < 2; ++tr) {
+        uint8_t* d = cur.dst + tr * cur.dst_pitch;
+        if (va) __stcs(reinterpret_cast<uint4*>(d), make_uint4(wa, wa, wa, wa));
+        if (vb) __stcs(reinterpret_cast<uint4*>(d + 64), make_uint4(wb, wb, wb, wb));
+      }
+      if (j == 0) {  // the kept energy W_0^2 Y_c^2, once per block pair
+        ke = (unsigned long long)(unsigned)(ya * ya) * 9ull + (unsigned long long)(unsigned)(yb * yb) * 9ull;
+        dc_term = (long long)ya + yb;
+      }
+    } else {
+    // ---- the row pass
     {
       Swar16 rv[2][16];
       row_pass(X, rv);
@@ -283,8 +347,7 @@ zonal_box_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
     __syncwarp();
 
     // ---- the input rows of the tile D ahead, into the slot just read
-    BoxTile fut;
-    const bool have_fut = hq[D - 1] && ok && c_t < t_stop;
+    have_fut = hq[D - 1] && ok && c_t < t_stop;
     if (have_fut) {
       take(fut);
       ok = advance();
@@ -295,8 +358,6 @@ zonal_box_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
 
     // ---- column pass on column c = j, exact scaled coefficients, kept
     // energy, inverse column pass into the back-transpose (columns c < K)
-    unsigned long long ke = 0ull;
-    long long dc_term = 0;
     {
       ZF2 y[16];
       Swar16 cw[16], yw[16];
@@ -376,6 +437,8 @@ zonal_box_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_
         if (vb) __stcs(reinterpret_cast<uint4*>(d + 64), make_uint4(ob[0], ob[1], ob[2], ob[3]));
       }
     }
+
+    }  // K > 1
 
     // ---- the tile's exact 2304 SSE: 2304 sum (x - 128)^2 - kept energy.  Per
     // block sum (x - 128)^2 = sum x^2 - 256 Y_c[0][0] - 4194304; lane (p, 0)
