@@ -6,9 +6,10 @@ keep W_u W_v Y_c as one FMA on the float 2^23 + field (plus 2304 * 128 on the
 DC of column 0), the FP32 inverse over MaybeZero inputs (inputs at or above
 K known to be zero), the rounding fl(fl(Z fl(1/2304)) 2^-149), and the exact
 squared error 2304 SSE = 2304 sum (x - 128)^2 - sum_kept W_u W_v Y_c^2 from
-the byte energy and the DC coefficient.  Stored pixels must equal the
-oracle's exact reconstruction and 2304 SSE its exact integer, for every r
-of each class.  No GPU needed."""
+the byte energy and the DC coefficient; for K = 1 the DC-only body (block
+sums, the constant 9 Y_c + 2304 * 128 rounded the same way).  Stored pixels
+must equal the oracle's exact reconstruction and 2304 SSE its exact integer,
+for every r of each class.  No GPU needed."""
 
 import os
 import shutil
@@ -62,7 +63,27 @@ int main() {
     for (int i = 0; i < 2; ++i)
       for (int m = 0; m < 16; ++m)
         for (int n = 0; n < 16; ++n) ex += (unsigned)(blk[i][m][n] * blk[i][m][n]);
-    // row pass (outputs c < K used), DC centred by -2048
+    if (K == 1) {
+      // the DC-only kernel: block sums, the constant 9 Y_c + 2304 * 128, rounded
+      long long kept = 0, dcs = 0;
+      for (int b = 0; b < 2; ++b) {
+        int s = 0;
+        for (int m = 0; m < 16; ++m)
+          for (int n = 0; n < 16; ++n) s += blk[b][m][n];
+        const int yc = s - 32768;
+        const float z = std::fmaf((float)yc, 9.0f, 294912.0f);
+        const float t = z * inv2304;
+        int q = (int)bits(t * tiny);
+        q = q < 0 ? 0 : (q > 255 ? 255 : q);
+        for (int k = 0; k < 256; ++k) std::printf("%d ", q);
+        std::printf("\n");
+        kept += 9LL * yc * yc;
+        dcs += yc;
+      }
+      std::printf("%lld\n", 2304LL * ((long long)ex - 256 * dcs - 2 * 4194304LL) - kept);
+      continue;
+    }
+    // K > 1: row pass (outputs c < K used), DC centred by -2048
     Swar16 rows[16][16];
     for (int m = 0; m < 16; ++m) {
       Swar16 x[16], o[16];
