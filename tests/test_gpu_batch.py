@@ -180,6 +180,34 @@ def test_tc_variant_long_pipeline_matches_oracle(torch, plan):
             assert out[3][1][k] == pytest.approx(ref["psnr"], rel=1e-5, abs=1e-5)
 
 
+# batch shapes that give the tcgen05 variant's CTAs 1, 2, 3 and 4 tile pairs
+# (its prologue and loop guards differ for each): grid = min(4 per SM, tiles / 4),
+# tiles per CTA = 2 ceil(tiles / (2 grid))
+TC_DEPTHS = [("1-pair", [(16, 128)]), ("2-pairs", [(512, 512)]), ("3-pairs", [(512, 512)] * 24),
+             ("4-pairs", [(512, 512)] * 31)]
+
+
+@pytest.mark.parametrize("shapes", [s for _, s in TC_DEPTHS], ids=[i for i, _ in TC_DEPTHS])
+def test_tc_variant_pipeline_depths(torch, plan, shapes):
+    imgs = [synth.ar1_image(h, w, 0.9, 70 + i) for i, (h, w) in enumerate(shapes)]
+    rs = [(0, 64, 100, 150, 256)[i % 5] for i in range(len(imgs))]
+    got = {}
+    for v in (1, 3):
+        src, dst = _dev(torch, imgs)
+        psnr = torch.empty(len(imgs), dtype=torch.float64, device="cuda")
+        b = atdct16.Batch(plan, [atdct16.image(s, d, r) for s, d, r in zip(src, dst, rs)], psnr,
+                          flags=atdct16.batch_variant(v))
+        b.launch()
+        assert b.last_device_status() == atdct16.OK
+        got[v] = ([d.cpu().numpy() for d in dst], psnr.cpu().tolist())
+        b.close()
+    for a, c in zip(got[1][0], got[3][0]):
+        assert np.array_equal(a, c)
+    assert got[3][1] == pytest.approx(got[1][1], rel=1e-5, abs=1e-5)
+    ref = O.compress_zonal_exact(imgs[0], rs[0])
+    assert np.array_equal(got[3][0][0], ref["recon_u8"])
+
+
 def test_tc_variant_tensor_wait_times_out_cleanly(torch):
     """With the MMA stall test hook the tcgen05 kernel issues no product: every
     CTA's bounded wait on the tensor core expires, it frees its tensor memory
