@@ -76,22 +76,9 @@ __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence
 // tensor core's (async-proxy) reads.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// 16 consecutive 32-bit columns of this thread's TMEM lane (shape 32x32b:
+// 32 consecutive 32-bit columns of this thread's TMEM lane (shape 32x32b:
 // warp w of the warpgroup reads lanes 32 (w & 3) .. + 31; taddr carries the
-// warp's first lane in bits 16-31), then the wait for it.
-__device__ __forceinline__ void ld16(unsigned taddr, float (&v)[16]) {
-  unsigned r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-// 32 consecutive 32-bit columns of this thread's TMEM lane (as ld16).
+// warp's first lane in bits 16-31); ld_wait waits for it.
 __device__ __forceinline__ void ld32(unsigned taddr, float (&v)[32]) {
   unsigned r[32];
   asm volatile(

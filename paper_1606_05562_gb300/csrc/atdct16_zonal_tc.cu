@@ -409,8 +409,6 @@ zonal_tc_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_l
   pdl_chain_exit();
 }
 
-int zonal_tc_smem_bytes() { return kTcSmemBytes; }
-
 cudaError_t launch_zonal_tc(const ImageJob* d_jobs, int njobs, long long ntiles, const float2* d_wtab,
                             float* d_tile_sse, int* d_status, int grid, cudaStream_t stream, bool dependent,
                             bool early, bool stall) {
