@@ -899,7 +899,7 @@ def serving_in_own_process(args):
     run the other phases."""
     cmd = [sys.executable, os.path.abspath(__file__), "--serve-only", "--serve-rates", args.serve_rates,
            "--serve-requests", str(args.serve_requests)]
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
     if r.returncode != 0:
         raise RuntimeError("serving phase failed: " + r.stderr[-2000:])
     res = json.loads(r.stdout.strip().splitlines()[-1])["serving"]
@@ -1105,21 +1105,28 @@ def run_ours(args):
         if args.cpu_seconds > 0:
             line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(batch)
         if not args.no_extras:
-            line["config1"] = config1_phase(torch, atdct16, synth, dev)
-            line["psnr_u8_by_r"] = psnr_u8_by_r(torch, atdct16, sets[0][0], sets[0][1])
-            line["coefficients"] = coef_phase(torch, atdct16, batch, dev, peak)
-            line["general_variants"] = general_variants_phase(torch, atdct16, batch, dev)
-            line["ssim"] = ssim_phase(torch, atdct16, plan, sets[0][2], jobs, px_step)
-            line["dct_baseline"] = dct_baseline_phase(torch, atdct16, plan, sets, jobs, px_step, None)
+            # the extra phases never take the headline with them: a phase that
+            # fails records its error in its own key
+            def phase(key, fn):
+                try:
+                    line[key] = fn()
+                except Exception as e:  # noqa: BLE001 - reported in the line
+                    line[key] = {"error": f"{type(e).__name__}: {e}"[:500]}
+                torch.cuda.empty_cache()
+
+            phase("config1", lambda: config1_phase(torch, atdct16, synth, dev))
+            phase("psnr_u8_by_r", lambda: psnr_u8_by_r(torch, atdct16, sets[0][0], sets[0][1]))
+            phase("coefficients", lambda: coef_phase(torch, atdct16, batch, dev, peak))
+            phase("general_variants", lambda: general_variants_phase(torch, atdct16, batch, dev))
+            phase("ssim", lambda: ssim_phase(torch, atdct16, plan, sets[0][2], jobs, px_step))
+            phase("dct_baseline", lambda: dct_baseline_phase(torch, atdct16, plan, sets, jobs, px_step, None))
             del sets
             torch.cuda.empty_cache()
-            line["quant"] = quant_phase(torch, atdct16, synth, dev, args.quant_frames, args.quant_chunk, 5, 1,
-                                        peak, cpu_oracle=args.cpu_seconds > 0)
-            torch.cuda.empty_cache()
-            line["mixed_batch"] = mixed_batch_phase(torch, atdct16, synth, dev, args.mixed_images,
-                                                    cpu_oracle=args.cpu_seconds > 0)
-            torch.cuda.empty_cache()
-            line["serving"] = serving_in_own_process(args)
+            phase("quant", lambda: quant_phase(torch, atdct16, synth, dev, args.quant_frames, args.quant_chunk, 5, 1,
+                                               peak, cpu_oracle=args.cpu_seconds > 0))
+            phase("mixed_batch", lambda: mixed_batch_phase(torch, atdct16, synth, dev, args.mixed_images,
+                                                           cpu_oracle=args.cpu_seconds > 0))
+            phase("serving", lambda: serving_in_own_process(args))
         print(json.dumps(line), flush=True)
     plan.close()
     if dist:
