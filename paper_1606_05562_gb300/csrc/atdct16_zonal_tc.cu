@@ -39,8 +39,9 @@
 //   copy the rows of k+3 into the staging slot; Y(k) -> registers; one CTA
 //   barrier; thread 0 issues MMA2(k+1) and MMA1(k+2); then the CUDA-core work
 //   of pair k runs while the tensor core computes the next products.  Each
-//   thread keeps the output pointer, tile index, r and block count of the
-//   pairs in flight in a four-entry ring of its own in shared memory.
+//   warp keeps the output row, pitch, tile index, r and block count of its
+//   tiles in flight in a four-entry ring in shared memory, and its tile's
+//   S^2 weights in a padded shared copy refreshed when r changes.
 // Every wait on the tensor core is bounded (the kernel then records a device
 // timeout, stops issuing, frees its TMEM and returns).
 #include <cuda_runtime.h>
@@ -64,11 +65,12 @@ constexpr int kTcA2 = 8192;       // pass-2 operand: 128 x 32 f16, MN-major
 constexpr int kTcB = 16384;       // B1 and B2: 32 x 32 f16, K-major, 2048 each
 constexpr int kTcStage = 20480;   // input rows: 2 slots x (block p, block p + 4) x 128 threads x 16 bytes
 constexpr int kTcTr = 28672;      // back-transpose: per warp 2 x 16 x 18 float2 (4608 bytes)
-constexpr int kTcRing = 47104;    // per thread 4 x 16 bytes: the pairs in flight
-constexpr int kTcPart = 55296;    // tile-energy partials of the second warp of each tile, [2 slots][2 tiles]
-constexpr int kTcBar = 55312;     // mbarriers: MMA1 and MMA2 completion
-constexpr int kTcSlot = 55328;    // the TMEM address written by tcgen05.alloc
-constexpr int kTcSmemBytes = 55344;
+constexpr int kTcRing = 47104;    // per warp 4 x 32 bytes: the tiles of the pairs in flight
+constexpr int kTcPart = 47616;    // tile-energy partials of the second warp of each tile, [2 slots][2 tiles]
+constexpr int kTcBar = 47632;     // mbarriers: MMA1 and MMA2 completion
+constexpr int kTcSlot = 47648;    // the TMEM address written by tcgen05.alloc
+constexpr int kTcW = 47664;       // per warp: its tile's weights, 16 columns at 9-unit strides (2304 bytes)
+constexpr int kTcSmemBytes = 56880;
 constexpr unsigned kTcCols = 64;  // TMEM columns: P (32 f32), Y (32 f32)
 constexpr long long kTcWaitCycles = 1LL << 30;  // about 0.5 s per wait on the tensor core
 
@@ -115,7 +117,7 @@ zonal_tc_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_l
   unsigned* const tslot = reinterpret_cast<unsigned*>(tsm + kTcSlot);
   const unsigned bar1 = tc::smem_u32(tsm + kTcBar), bar2 = bar1 + 8;
   float* const part = reinterpret_cast<float*>(tsm + kTcPart);
-  uint4* const ring = reinterpret_cast<uint4*>(tsm + kTcRing) + tid;  // entry s at + 128 s
+  uint4* const ring = reinterpret_cast<uint4*>(tsm + kTcRing) + 8 * warp;  // entry e: units 2 e, 2 e + 1
 
   // ---- set-up: TMEM, mbarriers, the constant B operands
   if (warp == 0) {
@@ -204,9 +206,10 @@ zonal_tc_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_l
   bool have = c_first + tau < c_stop;  // the cursor is on a tile of this warp
   if (have && !enter(c_first + tau)) ok = have = false;
   // The cursor's tile: its rows i16 of blocks p and p + 4 into staging slot
-  // st (zeros for blocks past the image edge, read from nowhere), its output
-  // row, tile index, r and block count into ring entry e; then the cursor
-  // moves two tiles on.  A warp without a tile stages zeros, t = -1.
+  // st (zeros for blocks past the image edge, read from nowhere); lane 0's
+  // output row, the pitch, tile index, r and block count into the warp's ring
+  // entry e; then the cursor moves two tiles on.  A warp without a tile
+  // stages zeros, t = -1.
   auto take = [&](int e, int st) {
     unsigned char* d = tsm + kTcStage + st * 4096 + tid * 16;
     const uint8_t* dummy = reinterpret_cast<const uint8_t*>(jobs);
@@ -217,15 +220,21 @@ zonal_tc_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_l
       const int na = p < nb ? 16 : 0, nb4 = p + 4 < nb ? 16 : 0;
       cp_async16_zfill(d, na ? src : dummy, na);
       cp_async16_zfill(d + 2048, nb4 ? src + 64 : dummy, nb4);
-      ring[128 * e] = make_uint4((unsigned)dst, (unsigned)(dst >> 32), (unsigned)(c_t + t_shift),
+      if (lane == 0) {
+        ring[2 * e] = make_uint4((unsigned)dst, (unsigned)(dst >> 32), (unsigned)(c_t + t_shift),
                                  ((unsigned)r_job << 8) | (unsigned)nb);
+        ring[2 * e + 1] = make_uint4((unsigned)dst_pitch, 0u, 0u, 0u);
+      }
       ok = step() && ok;
       ok = step() && ok;
       have = ok && c_t < t_stop;
     } else {
       cp_async16_zfill(d, dummy, 0);
       cp_async16_zfill(d + 2048, dummy, 0);
-      ring[128 * e] = make_uint4(0u, 0u, 0xFFFFFFFFu, 0u);
+      if (lane == 0) {
+        ring[2 * e] = make_uint4(0u, 0u, 0xFFFFFFFFu, 0u);
+        ring[2 * e + 1] = make_uint4(0u, 0u, 0u, 0u);
+      }
     }
     cp_async_commit();
   };
@@ -300,6 +309,8 @@ zonal_tc_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_l
   // the first warp of each tile finishes the tile's partial after the next barrier
   float own = 0.f;
   int own_t = -1;
+  int wr = -1;  // r whose weights this warp holds
+  float4* const wsm = reinterpret_cast<float4*>(tsm + kTcW) + warp * 144;
   for (int k = 0; k < npairs && !bad; ++k) {
     // ---- MMA2(k) and MMA1(k+1) complete: next operands, this pair's Y
     bool fail = !tc::mbar_wait(bar2, k & 1, kTcWaitCycles);
@@ -330,18 +341,30 @@ zonal_tc_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_l
       tile_sse[own_t] = (own + part[2 * ((k - 1) & 1) + tau]) * (1.0f / (256.0f * 2304.0f));
 
     // ---- pair k on the CUDA cores: column v = i16 of blocks p, p + 4
-    const uint4 md = ring[128 * (k & 3)];
+    const uint4 md = ring[2 * (k & 3)];  // written by lane 0 three pairs ago (barriers since)
+    const int cur_pitch = (int)ring[2 * (k & 3) + 1].x;
     const int cur_r = (int)(md.w >> 8), cur_nb = (int)(md.w & 255u);
     float2 y[16];
 #pragma unroll
     for (int u = 0; u < 16; ++u) y[u] = make_float2(yv[2 * u], yv[2 * u + 1]);
     if (i16 == 0) y[0] = badd(y[0], make_float2(8388608.0f, 8388608.0f));  // 256 Y_c -> 256 Y at (0, 0)
     float2 acc = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+    if (cur_r != wr) {  // warp-uniform (one tile per warp): refresh the warp's weight copy
+      __syncwarp();
+      const float4* const src = reinterpret_cast<const float4*>(wtab) + (long long)cur_r * 128;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int g = lane * 4 + q;
+        wsm[9 * (g >> 3) + (g & 7)] = __ldg(src + g);  // (kw, dw) of rows 2h, 2h + 1 of column g >> 3
+      }
+      __syncwarp();
+      wr = cur_r;
+    }
     {
-      const float4* const wcol = reinterpret_cast<const float4*>(wtab) + (long long)cur_r * 128 + i16 * 8;
+      const float4* const wcol = wsm + 9 * i16;
 #pragma unroll
       for (int h = 0; h < 8; ++h) {
-        const float4 w = __ldg(wcol + h);  // (kw, dw) of rows 2h, 2h + 1 of column v
+        const float4 w = wcol[h];  // (kw, dw) of rows 2h, 2h + 1 of column v
         acc = __ffma2_rn(f2mul(y[2 * h], w.y), y[2 * h], acc);
         acc1 = __ffma2_rn(f2mul(y[2 * h + 1], w.w), y[2 * h + 1], acc1);
         y[2 * h] = f2mul(y[2 * h], w.x);
@@ -379,7 +402,9 @@ zonal_tc_kernel(const ImageJob* __restrict__ jobs, int njobs, long long ntiles_l
         oa[g] = pack_u8(qa[1], qa[0], pack_u8(qa[3], qa[2], 0u));
         ob[g] = pack_u8(qb[1], qb[0], pack_u8(qb[3], qb[2], 0u));
       }
-      uint8_t* const dst = reinterpret_cast<uint8_t*>((unsigned long long)md.x | ((unsigned long long)md.y << 32));
+      // lane 0 holds row 0 of block pair 2 (warp & 1); this lane row i16 of pair p
+      uint8_t* const dst = reinterpret_cast<uint8_t*>((unsigned long long)md.x | ((unsigned long long)md.y << 32)) +
+                           (long long)i16 * cur_pitch + 16 * (lane >> 4);
       const bool va = p < cur_nb, vb = p + 4 < cur_nb;
       if (va) __stcs(reinterpret_cast<uint4*>(dst), make_uint4(oa[0], oa[1], oa[2], oa[3]));
       if (vb) __stcs(reinterpret_cast<uint4*>(dst + 64), make_uint4(ob[0], ob[1], ob[2], ob[3]));
